@@ -1,0 +1,48 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds no arithmetic of the method: it only draws numbers (numpy
+PCG64 streams keyed by an integer seed) in the shapes of the paper's runs.
+
+* theta: float64 (Ntau, L, L, 2), indexed [tau, y, x, c]; c = 0 the bond
+  (x,y)->(x+1,y), c = 1 the bond (x,y)->(x,y+1).  "Hot start": i.i.d. uniform
+  in [-pi, pi) on every spatial bond (temporal links are fixed to zero and not
+  stored).
+* vectors: complex128 (Ntau, L, L), indexed [tau, y, x].
+* R ~ CN(0, 1): real and imaginary parts i.i.d. N(0, 1/2) (density e^{-|R|^2}).
+* p ~ N(0, 1/2) per bond (density e^{-p^2}, the kinetic term sum p^2 of H).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def theta_hot(L: int, Ntau: int, seed: int) -> np.ndarray:
+    return rng(seed).uniform(-np.pi, np.pi, size=(Ntau, L, L, 2))
+
+
+def theta_zero(L: int, Ntau: int) -> np.ndarray:
+    return np.zeros((Ntau, L, L, 2))
+
+
+def theta_pi_flux(L: int, Ntau: int) -> np.ndarray:
+    """theta_y(x, y) = pi * (x mod 2), theta_x = 0: flux pi through every plaquette."""
+    th = np.zeros((Ntau, L, L, 2))
+    th[:, :, 1::2, 1] = np.pi
+    return th
+
+
+def complex_gaussian(L: int, Ntau: int, seed: int) -> np.ndarray:
+    g = rng(seed).standard_normal(size=(2, Ntau, L, L))
+    return (g[0] + 1j * g[1]) * np.sqrt(0.5)
+
+
+def momenta(L: int, Ntau: int, seed: int) -> np.ndarray:
+    return rng(seed).standard_normal(size=(Ntau, L, L, 2)) * np.sqrt(0.5)
+
+
+def uniform01(seed: int) -> float:
+    return float(rng(seed).uniform(0.0, 1.0))
