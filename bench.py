@@ -1,0 +1,326 @@
+"""Benchmark of the HQMC hot path: HMC trajectories per second on one GB300.
+
+A step is one HMC trajectory of the whole path (Philox draws, phi = M^dagger R,
+N_lf + 1 CG solves of (M^dagger M) X = phi, forces, leapfrog, Metropolis) on a
+seeded synthetic gauge field; the chain continues from step to step.
+
+Default workload (plain FP64 GPU HMC): L = 24, Ntau = 240 (138,240 sites),
+dtau = 0.1, t = 1, J = 1, compact action, hot start theta ~ U[-pi, pi), CG to a
+true FP64 residual of 1e-8, 20 leapfrog steps of dt = 0.01.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line on rank 0.  Under torchrun every rank runs an independent
+chain (replicas; the path has no exchange between chains).  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M†M apply GB/s vs HBM peak; HMC traj/s learned+FP32 vs plain FP64 at 1e-8"
+
+WORKLOADS = {
+    # plain FP64 HMC at L = 24, Ntau = 240
+    "hmc_fp64_L24_Nt240": dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.01, tol=1e-8,
+                               solver="cg64", seed=1),
+    # plain FP64 HMC at L = 8, Ntau = 40 (oracle-sized)
+    "hmc_fp64_L8_Nt40": dict(L=8, Ntau=40, dtau=0.1, t=1.0, J=1.0, nsteps=10, dt=0.02, tol=1e-10,
+                             solver="cg64", seed=1),
+    # mixed precision at L = 48, Ntau = 480
+    "hmc_mixed_L48_Nt480": dict(L=48, Ntau=480, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.01, tol=1e-8,
+                                solver="mixed", seed=1),
+}
+DEFAULT_WORKLOAD = "hmc_fp64_L24_Nt240"
+
+# Algorithmic work of one launch of the fused M^dagger M kernel in CG mode, per site:
+#   flops: 2 sweeps x 7 factor passes x 8 flops + 22 (direction update, combination, <p, Op>)
+#   bytes (FP64): links 32 + r 16 + p_old 16 + p_new 16 + q 16
+MDAGM_FLOPS_PER_SITE = 134
+MDAGM_BYTES_PER_SITE = {"cg64": 96, "mixed": 48}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10):
+    """Times the FP64 CPU oracle on a bounded sample of one trajectory: max_iters CG
+    iterations and one force evaluation at the workload's size, scaled to one
+    trajectory with its_per_traj CG iterations and nsteps + 1 forces."""
+    import oracle
+
+    lat = oracle.Lattice(wl["L"], wl["Ntau"], dtau=wl["dtau"], t=wl["t"], J=wl["J"])
+    t0 = time.perf_counter()
+    X, it, _, _ = oracle.cg(lat, theta, phi, tol=1e-30, maxit=max_iters)
+    t1 = time.perf_counter()
+    oracle.fermion_dS(lat, theta, X)
+    oracle.bosonic_dS(lat, theta)
+    t2 = time.perf_counter()
+    t_iter = (t1 - t0) / (it + 2)  # it iterations plus the initial and final residual applications
+    t_force = t2 - t1
+    t_traj = its_per_traj * t_iter + (wl["nsteps"] + 1) * t_force
+    return {"traj_s": t_traj, "t_iter_s": t_iter, "t_force_s": t_force, "cores": oracle.num_threads(),
+            "sample": f"{it} oracle CG iterations + 1 force at L={wl['L']}, Ntau={wl['Ntau']}, "
+                      f"scaled to {its_per_traj:.0f} CG iterations and {wl['nsteps'] + 1} forces per trajectory"}
+
+
+# CG iterations per trajectory used to scale oracle samples when no GPU run is
+# available (the reference arm); measured on the GPU with the same algorithm.
+ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 40000.0, "hmc_fp64_L8_Nt40": 11000.0, "hmc_mixed_L48_Nt480": 80000.0}
+
+
+def run_reference(args, wl_name, wl, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2508_16298_gb300 import inputs
+
+    lat = oracle.Lattice(wl["L"], wl["Ntau"], dtau=wl["dtau"], t=wl["t"], J=wl["J"])
+    theta = inputs.theta_hot(wl["L"], wl["Ntau"], wl["seed"])
+    R = inputs.complex_gaussian(wl["L"], wl["Ntau"], wl["seed"] + 1)
+    phi = oracle.apply_M(lat, theta, R, dagger=True)
+    its = ITS_PER_TRAJ_HINT[wl_name]
+    for _ in range(args.warmup):
+        oracle_sample(wl, its, theta, phi, max_iters=2)
+    samples = [oracle_sample(wl, its, theta, phi) for _ in range(args.steps)]
+    t = statistics.median(s["traj_s"] for s in samples)
+    value = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl_name, wl),
+            "cpu_baseline": {"value": value, "unit": "traj/s", "cores": samples[0]["cores"], "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": value, "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl_name, wl):
+    return {"workload": wl_name, "L": wl["L"], "Ntau": wl["Ntau"], "sites": wl["L"] * wl["L"] * wl["Ntau"],
+            "dtau": wl["dtau"], "t": wl["t"], "J": wl["J"], "action": "compact", "start": "hot (theta ~ U[-pi, pi))",
+            "n_leapfrog": wl["nsteps"], "dt": wl["dt"], "cg_tol": wl["tol"], "solver": wl["solver"],
+            "l2": "flushed between timed steps (512 MiB write; step times exclude the flush)"}
+
+
+def run_ours(args, wl_name, wl, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_16298_gb300 import hqmc, inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    L, N = wl["L"], wl["Ntau"]
+    cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"])
+    seed = wl["seed"] + 1000 * rank
+    theta = torch.from_numpy(inputs.theta_hot(L, N, seed)).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver=wl["solver"])
+
+    for k in range(args.warmup):
+        hqmc.trajectory(cfg, theta, seed=seed, traj_counter=k, **kw)
+    fp64_tflops = hqmc.probe_fp64_rate(cfg) if rank == 0 else None
+
+    # ---- device-resident timed region --------------------------------------
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    gpu_id = None
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else str(local_rank)
+    except Exception:
+        gpu_id = str(local_rank)
+    clocks = ClockSampler(gpu_id)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    hqmc.set_timing(cfg, True)
+    launches0 = cfg.launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        infos.append(hqmc.trajectory(cfg, theta, seed=seed, traj_counter=args.warmup + k, **kw))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = cfg.launch_count() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    n_md, md_ms = hqmc.get_timing(cfg, hqmc.TIMER_MDAGM)
+    hqmc.set_timing(cfg, False)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----------------
+    theta_h = theta.cpu().pin_memory()
+    bytes_theta = theta_h.numel() * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        th_dev = theta_h.to(dev, non_blocking=True)
+        info = hqmc.trajectory(cfg, th_dev, seed=seed, traj_counter=args.warmup + args.steps + k, **kw)
+        theta_h.copy_(th_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps / e2e_s
+
+    if rank != 0:
+        return
+    its = [i["cg_iterations"] for i in infos]
+    its_per_traj = statistics.mean(its)
+    md_avg_ms = md_ms / max(n_md, 1)
+    sites = L * L * N
+    achieved_tflops = MDAGM_FLOPS_PER_SITE * sites / (md_avg_ms * 1e-3) / 1e12
+    achieved_gbs = MDAGM_BYTES_PER_SITE[wl["solver"]] * sites / (md_avg_ms * 1e-3) / 1e9
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"kernel": "mdagm_kernel<double, CG direction>", "bound": "alu", "achieved": achieved_tflops,
+                "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_tflops,
+                "traffic": None,
+                "peak_note": "FP64 FMA rate measured on this GPU by hqmc_probe_fp64_rate",
+                "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / hbm,
+                "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms}
+
+    # ---- oracle on the host cores: bounded sample --------------------------
+    import oracle
+    lat = oracle.Lattice(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"])
+    th_np = inputs.theta_hot(L, N, wl["seed"])
+    phi_np = oracle.apply_M(lat, th_np, inputs.complex_gaussian(L, N, wl["seed"] + 1), dagger=True)
+    cb = oracle_sample(wl, its_per_traj, th_np, phi_np)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl_name, wl),
+        "e2e": {"value": e2e_value, "unit": "traj/s", "h2d_bytes_per_step": bytes_theta,
+                "d2h_bytes_per_step": bytes_theta},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": {"value": 1.0 / cb["traj_s"], "unit": "traj/s", "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "clocks": clk,
+        "acceptance": statistics.mean(i["accepted"] for i in infos),
+        "cg_iterations_per_traj": its_per_traj,
+        "dH": [round(i["dH"], 6) for i in infos],
+        "max_true_residual": max(i["max_true_residual"] for i in infos),
+        "step_ms": [round(s, 3) for s in step_ms],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        run_reference(args, args.workload, wl, rank, world)
+    else:
+        run_ours(args, args.workload, wl, rank, world, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

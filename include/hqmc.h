@@ -1,0 +1,229 @@
+/*
+ * hqmc.h - C ABI of the GB300 hybrid quantum Monte Carlo hot path.
+ *
+ * The library applies the fermion matrix of a compact (or non-compact) U(1)
+ * gauge field theta on the spatial bonds of an L x L x Ntau lattice coupled to
+ * fermions, solves (M^dagger M) X = phi by conjugate gradients, computes the
+ * pseudofermion force and runs leapfrog / Metropolis HMC trajectories, all in
+ * CUDA kernels for sm_103a (arXiv 2508.16298, Methods and Supplement SI).
+ *
+ * Layouts (all arrays contiguous, caller-owned DEVICE memory unless stated):
+ *   theta, p, F : double[Ntau][L][L][2]; index [tau][y][x][c], c = 0 the bond
+ *                 (x,y)->(x+1,y), c = 1 the bond (x,y)->(x,y+1); periodic in x, y.
+ *   vectors     : complex[Ntau][L][L], interleaved (re, im); complex double
+ *                 (16 B) for HQMC_FP64, complex float (8 B) for HQMC_FP32.
+ *   0-based slices: slice tau carries the paper's B_{tau+1}.
+ * Every pointer must be 16-byte aligned.  Arrays must not overlap unless a
+ * function says otherwise.  Scalars returned through *_info structs are host
+ * memory owned by the caller.
+ *
+ * Stream semantics: every call is ordered on `stream` (a cudaStream_t passed
+ * as void*; NULL is the legacy default stream).  Functions that return
+ * host-side results (solve and trajectory info) synchronise that stream
+ * before returning; the others only enqueue work.
+ *
+ * Errors: every function returns an hqmc_status.  No C++ exception crosses
+ * the ABI.  After HQMC_ECUDA the CUDA error text is in hqmc_last_error(cfg).
+ * The config is single-threaded: calls on one config must not run
+ * concurrently from several host threads.
+ */
+#ifndef HQMC_H
+#define HQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HQMC_API __attribute__((visibility("default")))
+#else
+#define HQMC_API
+#endif
+
+typedef enum {
+    HQMC_OK = 0,
+    HQMC_EINVAL = 1,       /* bad parameter: odd or too large L, Ntau < 2, NULL or misaligned pointer */
+    HQMC_ENOTCONV = 2,     /* CG used up maxit; x holds the last iterate, info the true residual */
+    HQMC_EBREAKDOWN = 3,   /* CG met <d, O d> <= 0 */
+    HQMC_ENONFINITE = 4,   /* a NaN or Inf reached a CG reduction or the Hamiltonian */
+    HQMC_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    HQMC_ECUDA = 6,        /* a CUDA runtime call failed (text in hqmc_last_error) */
+    HQMC_ENOMEM = 7,       /* workspace allocation failed in hqmc_make_config */
+    HQMC_EUNSUPPORTED = 8  /* option not available for these sizes or this device */
+} hqmc_status;
+
+enum { HQMC_FP64 = 0, HQMC_FP32 = 1 };
+enum { HQMC_ACTION_COMPACT = 0, HQMC_ACTION_NONCOMPACT = 1 };
+
+/* Solver selection for hqmc_cg_solve / hqmc_leapfrog / hqmc_trajectory. */
+enum {
+    HQMC_SOLVER_CG64 = 0,  /* plain CG, every vector and reduction in FP64 */
+    HQMC_SOLVER_MIXED = 1  /* CG with M^dagger M in FP32 (complex float) and FP64 reliable
+                              residual updates every params.reliable_interval iterations */
+};
+
+/* Model and lattice (Results "Model"; Methods "Model and partition function"). */
+typedef struct hqmc_params {
+    int L;                 /* spatial extent: even, 4 <= L <= 68 (FP64 path limit) */
+    int Ntau;              /* number of imaginary-time slices, >= 2 */
+    double dtau;           /* Trotter step Delta tau (> 0); the paper uses 0.1 */
+    double t;              /* hopping amplitude (the paper's energy unit, 1) */
+    double J;              /* gauge coupling (> 0) */
+    double K;              /* plaquette coupling (0 in the compact runs here) */
+    int action;            /* HQMC_ACTION_COMPACT or HQMC_ACTION_NONCOMPACT */
+    int reliable_interval; /* mixed solver: FP64 residual update period; <= 0 means 50 */
+} hqmc_params;
+
+/* Opaque configuration: geometry, launch shapes and the device workspace
+ * (CG vectors, link tables, reduction partials).  It is bound to the device
+ * that was current in hqmc_make_config; use it only with that device current. */
+typedef struct hqmc_config hqmc_config;
+
+typedef struct hqmc_solve_info {
+    int status;                /* hqmc_status of the solve */
+    int iterations;            /* applications of M^dagger M to a search direction */
+    int restarts;              /* FP64 solver: restarts from the true residual */
+    int reliable_updates;      /* mixed solver: FP64 residual recomputations */
+    double true_residual;      /* ||phi - (M^dagger M) x|| / ||phi||, computed in FP64 */
+    double recursive_residual; /* the recurrence's estimate at exit */
+} hqmc_solve_info;
+
+typedef struct hqmc_traj_info {
+    int status;            /* worst hqmc_status of the solves in the trajectory */
+    int accepted;          /* 1 if the Metropolis test accepted the end point */
+    int cg_solves;         /* number of CG solves (nsteps + 1) */
+    int cg_iterations;     /* total CG iterations */
+    double H0, H1, dH;     /* Hamiltonian at start and end, dH = H1 - H0 */
+    double u;              /* the uniform number used by the Metropolis test */
+    double max_true_residual;
+} hqmc_traj_info;
+
+/* ---- configuration ----------------------------------------------------- */
+
+/* Validates *p, chooses launch shapes for the current device and allocates
+ * the workspace (this is the only call that allocates device memory).
+ * *out receives the config; free it with hqmc_free_config.
+ * Errors: HQMC_EINVAL (parameters), HQMC_EUNSUPPORTED (device is not
+ * compute capability 10.x or 11.x-class with clusters), HQMC_ENOMEM, HQMC_ECUDA. */
+HQMC_API int hqmc_make_config(const hqmc_params* p, hqmc_config** out);
+
+/* Releases the workspace.  NULL is accepted.  Waits for the device. */
+HQMC_API int hqmc_free_config(hqmc_config* cfg);
+
+/* Static description of a status code. */
+HQMC_API const char* hqmc_strerror(int status);
+
+/* Detail text of the last error on this config ("" if none). */
+HQMC_API const char* hqmc_last_error(const hqmc_config* cfg);
+
+/* Number of lattice sites Ntau*L*L of the config (host query, no device work). */
+HQMC_API long long hqmc_num_sites(const hqmc_config* cfg);
+
+/* Number of CUDA kernels this config has enqueued since it was made (host
+ * counter; no device work).  Differences around a region count its launches. */
+HQMC_API long long hqmc_launch_count(const hqmc_config* cfg);
+
+/* ---- operators (Methods, Eq. (M_alpha) and the checkerboard Eq. (eq24)) -- */
+
+/* y = M x (dagger = 0) or y = M^dagger x (dagger = 1), where
+ * (M x)_tau = x_tau - B_{tau-1} x_{tau-1} for tau >= 1 and
+ * (M x)_0 = x_0 + B_{Ntau-1} x_{Ntau-1}, and B_tau is the symmetric checkerboard
+ * product e^{V4/2} e^{V3/2} e^{V2/2} e^{V1} e^{V2/2} e^{V3/2} e^{V4/2} of 2x2 bond
+ * exponentials [[cosh a, e^{i theta} sinh a], [e^{-i theta} sinh a, cosh a]] with
+ * a = dtau*t (halved for families 2-4).  precision: HQMC_FP64 (x, y complex
+ * double) or HQMC_FP32 (complex float).  theta is always double.  x and y
+ * must not overlap. */
+HQMC_API int hqmc_apply_M(hqmc_config* cfg, const double* theta, const void* x, void* y,
+                 int dagger, int precision, void* stream);
+
+/* y = (M^dagger M) x in one fused kernel (Methods, "Matrix-free representation
+ * of M^dagger M v"):  y_tau = x_tau + B_tau^2 x_tau - s_tau B_{tau-1} x_{tau-1}
+ * - s'_tau B_tau x_{tau+1} with s_0 = -1, s'_{Ntau-1} = -1, else +1. */
+HQMC_API int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void* y,
+                     int precision, void* stream);
+
+/* ---- solver (Methods, "CG method and preconditioner", Eq. (pCG)) ------- */
+
+/* Solves (M^dagger M) x = phi.  phi and x are complex double.  x holds the
+ * initial guess on entry (zeros for the paper's X_0 = 0) and the solution on
+ * exit.  Stops when ||r|| <= tol ||phi|| for the FP64 true residual
+ * r = phi - (M^dagger M) x; HQMC_SOLVER_CG64 restarts from the true residual if
+ * the recursive one has drifted.  maxit bounds the iterations.  *info (host,
+ * may be NULL) is filled.  Synchronises the stream.  Returns HQMC_ENOTCONV,
+ * HQMC_EBREAKDOWN or HQMC_ENONFINITE on failure with x holding the last iterate. */
+HQMC_API int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* x,
+                  double tol, int maxit, int solver, hqmc_solve_info* info, void* stream);
+
+/* ---- force (Supplement SI, Eqs. (force&CG) and (fermion_force)) -------- */
+
+/* Given X = (M^dagger M)^{-1} phi (complex double), writes the total force
+ * F = -dS_B/dtheta - dS_f/dtheta with S_f = phi^dagger (M^dagger M)^{-1} phi and
+ * S_B the bosonic action (compact: (1/(J dtau)) sum[1 - cos(theta_{tau+1} -
+ * theta_tau)], non-compact: (1/(J dtau)) sum (theta_{tau+1} - theta_tau)^2, plus
+ * K dtau sum_plaquettes cos(curl theta)).  dSf (nullable) receives dS_f/dtheta
+ * alone.  F and dSf are double[Ntau][L][L][2] and may not alias theta. */
+HQMC_API int hqmc_force(hqmc_config* cfg, const double* theta, const void* X, double* F,
+               double* dSf, void* stream);
+
+/* Hamiltonian terms of Eq. (H_hmc) at (theta, p) with fermion part phi^dagger X:
+ * out_host[0] = S_B(theta), out_host[1] = sum p^2, out_host[2] = Re phi^dagger X.
+ * p, phi or X may be NULL (the term is then 0).  Synchronises the stream. */
+HQMC_API int hqmc_action_terms(hqmc_config* cfg, const double* theta, const double* p,
+                      const void* phi, const void* X, double* out_host, void* stream);
+
+/* ---- HMC (Methods, "HQMC algorithm": steps (i)-(iv), Eq. (leapfrog)) ---- */
+
+/* Gaussian draws of step (i) from the counter-based Philox4x32-10 generator
+ * (key = seed, counter = (element, stream, traj_counter)): p ~ N(0, 1/2) per
+ * bond and R ~ CN(0, 1) per site (complex double).  Either output may be NULL.
+ * *u_host (nullable) receives the Metropolis uniform of that trajectory. */
+HQMC_API int hqmc_draw(hqmc_config* cfg, uint64_t seed, uint64_t traj_counter, double* p, void* R,
+              double* u_host, void* stream);
+
+/* nsteps leapfrog steps of size dt on (theta, p) in place:
+ * p += F dt/2; theta += 2 p dt; solve; p += F dt/2, with F the total force.
+ * X (complex double, in/out) is the CG initial guess on entry and
+ * (M^dagger M)^{-1} phi at the final theta on exit.  Every solve uses tol,
+ * maxit and solver as in hqmc_cg_solve.  *info (nullable): cg_solves,
+ * cg_iterations, status, max_true_residual.  Synchronises the stream. */
+HQMC_API int hqmc_leapfrog(hqmc_config* cfg, double* theta, double* p, const void* phi, void* X,
+                  int nsteps, double dt, double tol, int maxit, int solver,
+                  hqmc_traj_info* info, void* stream);
+
+/* One HQMC update from theta (in/out).  Draws p and R with hqmc_draw(seed,
+ * traj_counter) unless p_in (double, device) / R_in (complex double, device) /
+ * u_in (host) are given; phi = M^dagger R; H0 = S_B + sum p^2 + R^dagger R;
+ * nsteps leapfrog steps; H1 = S_B + sum p^2 + phi^dagger X; accepts iff
+ * u < exp(H0 - H1), else restores theta.  Synchronises the stream. */
+HQMC_API int hqmc_trajectory(hqmc_config* cfg, double* theta, uint64_t seed, uint64_t traj_counter,
+                    const double* p_in, const void* R_in, const double* u_in, int nsteps,
+                    double dt, double tol, int maxit, int solver, hqmc_traj_info* info,
+                    void* stream);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+enum { HQMC_TIMER_MDAGM = 0, HQMC_TIMER_CG_UPDATE = 1, HQMC_TIMER_FORCE = 2, HQMC_TIMER_COUNT = 3 };
+
+/* Enables (1) or disables (0) CUDA-event timing of kernel launches and resets
+ * the counters.  Events are recorded on the launching stream around every
+ * launch of the timed kernel classes. */
+HQMC_API int hqmc_set_timing(hqmc_config* cfg, int enable);
+
+/* Synchronises the device and returns, for one kernel class, the number of
+ * timed launches and their summed duration in milliseconds. */
+HQMC_API int hqmc_get_timing(hqmc_config* cfg, int timer, long long* launches, double* total_ms);
+
+/* Measures the device's FP64 fused-multiply-add throughput (TFLOP/s, 2 flops
+ * per FMA) with a short kernel of independent FMA chains on the default
+ * stream; used as the roofline denominator of the FP64 (ALU-bound) kernels.
+ * Synchronises the device. */
+HQMC_API int hqmc_probe_fp64_rate(hqmc_config* cfg, double* tflops_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HQMC_H */

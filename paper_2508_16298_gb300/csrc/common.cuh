@@ -1,0 +1,181 @@
+// Device-side building blocks shared by the HQMC kernels (sm_103a).
+//
+// Storage conventions (see include/hqmc.h): slice-major vectors v[tau][y][x]
+// of interleaved complex numbers; theta[tau][y][x][c]; site s = x + L*y.
+//
+// The checkerboard product of Eq. (eq24) is evaluated in a factored form:
+// every family factor e^{alpha T_f} equals cosh(alpha) * (1 + tanh(alpha) T_f)
+// because T_f^2 = 1 and every site belongs to exactly one bond of each family.
+// Hence B = cB * P with the scalar cB = cosh(a) cosh(a/2)^6 and
+//   P = (1 + t2 T4)(1 + t2 T3)(1 + t2 T2)(1 + t1 T1)(1 + t2 T2)(1 + t2 T3)(1 + t2 T4),
+// t1 = tanh(a), t2 = tanh(a/2), a = dtau*t.  The per-bond link factor
+// U = t_f e^{i theta} ("link table") is computed once per gauge field, so the
+// inner sweep is two complex FMAs per bond endpoint:
+//   v_i <- v_i + U v_j,   v_j <- v_j + conj(U) v_i.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace hqmc {
+
+template <class R> struct CT;
+template <> struct CT<double> { using T = double2; };
+template <> struct CT<float> { using T = float2; };
+template <class R> using C2 = typename CT<R>::T;
+
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+
+// a + u * b
+template <class T> __device__ __forceinline__ T cfma(T a, T u, T b) {
+  return mk(fma(u.x, b.x, fma(-u.y, b.y, a.x)), fma(u.x, b.y, fma(u.y, b.x, a.y)));
+}
+// a + conj(u) * b
+template <class T> __device__ __forceinline__ T cfmac(T a, T u, T b) {
+  return mk(fma(u.x, b.x, fma(u.y, b.y, a.x)), fma(u.x, b.y, fma(-u.y, b.x, a.y)));
+}
+// a + s * b (s real)
+template <class T, class R> __device__ __forceinline__ T caxpy(T a, R s, T b) {
+  return mk(fma(s, b.x, a.x), fma(s, b.y, a.y));
+}
+template <class T, class R> __device__ __forceinline__ T cscale(R s, T b) { return mk(s * b.x, s * b.y); }
+// Re(conj(a) * b)
+template <class T> __device__ __forceinline__ double cdot_re(T a, T b) {
+  return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+}
+
+// Slice geometry.
+struct Geo {
+  int L;      // spatial extent (even)
+  int V;      // L*L
+  int half;   // L/2
+  int Ntau;   // slices
+};
+
+// Bond number b in [0, V/2) of checkerboard family fam (1..4): tail site i,
+// head site j and bond direction c.
+__device__ __forceinline__ void bond_of(const Geo& g, int fam, int b, int& i, int& j, int& c) {
+  if (fam <= 2) {
+    int y = b / g.half;
+    int x = 2 * (b - y * g.half) + (fam - 1);
+    int xp = (x + 1 == g.L) ? 0 : x + 1;
+    i = x + g.L * y;
+    j = xp + g.L * y;
+    c = 0;
+  } else {
+    int k = b / g.L;
+    int x = b - k * g.L;
+    int y = 2 * k + (fam - 3);
+    int yp = (y + 1 == g.L) ? 0 : y + 1;
+    i = x + g.L * y;
+    j = x + g.L * yp;
+    c = 1;
+  }
+}
+
+// Factor order of P as applied to a vector: the rightmost factor first.
+__constant__ static const int kApplyOrder[7] = {4, 3, 2, 1, 2, 3, 4};
+
+// v <- (1 + U T_fam) v on one slice held in shared memory.  U points at the
+// slice's link table (two complex links per site).  Caller synchronises.
+template <class T>
+__device__ __forceinline__ void factor_pass(const Geo& g, int fam, T* v, const T* __restrict__ U) {
+  const int nb = g.V >> 1;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int i, j, c;
+    bond_of(g, fam, b, i, j, c);
+    T u = __ldg(U + 2 * i + c);
+    T vi = v[i], vj = v[j];
+    v[i] = cfma(vi, u, vj);
+    v[j] = cfmac(vj, u, vi);
+  }
+}
+
+// v <- (1 + U T_fam)^{-1} v = (1 - U T_fam) v / (1 - |U|^2); used by the force
+// sweep to step back through the factors without storing every partial product.
+template <class T>
+__device__ __forceinline__ void factor_pass_inverse(const Geo& g, int fam, T* v, const T* __restrict__ U) {
+  const int nb = g.V >> 1;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int i, j, c;
+    bond_of(g, fam, b, i, j, c);
+    T u = __ldg(U + 2 * i + c);
+    auto nrm = u.x * u.x + u.y * u.y;
+    auto inv = 1 / (1 - nrm);
+    T mu = mk(-u.x, -u.y);
+    T vi = v[i], vj = v[j];
+    T ni = cfma(vi, mu, vj);
+    T nj = cfmac(vj, mu, vi);
+    v[i] = cscale(inv, ni);
+    v[j] = cscale(inv, nj);
+  }
+}
+
+// v <- P v: seven factor passes with a block barrier after each.
+template <class T>
+__device__ __forceinline__ void apply_P(const Geo& g, T* v, const T* __restrict__ U) {
+#pragma unroll 1
+  for (int k = 0; k < 7; ++k) {
+    factor_pass(g, kApplyOrder[6 - k], v, U);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: a fixed tree per block and a fixed order over the
+// per-block partials, so that every block of a consumer kernel that sums the
+// same partials gets bit-identical totals.
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of v; the result is valid in thread 0.  `scratch` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = (lane < nw) ? scratch[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// Sum of n partials by one warp in a fixed order; every lane returns the total.
+__device__ __forceinline__ double warp_sum_partials(const double* p, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) s += p[k];
+  s = warp_sum(s);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Device-resident CG state.  Every field is written by exactly one kernel
+// launch and read by later launches, or written by block 0 into a slot that
+// the other blocks of the same launch do not read.
+struct CgState {
+  double rr[2];      // <r, r> of the current and previous iteration (index k & 1)
+  double bb;         // <phi, phi>
+  double tol2bb;     // tol^2 <phi, phi>
+  double pq_last;    // last <p, O p>
+  double alpha_last; // last step length
+  int k;             // iterations completed; read by the direction kernel
+  int k2;            // copy of k for the update kernel
+  int seg_start;     // first iteration of the current recurrence segment
+  int maxit;
+  int done;          // 0 running; 1 recursive residual below tol; 2 maxit; 3 breakdown; 4 non-finite
+  int pad[3];
+};
+
+enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4 };
+
+}  // namespace hqmc

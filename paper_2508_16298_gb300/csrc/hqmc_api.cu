@@ -1,0 +1,724 @@
+// C ABI of the HQMC library: configuration, workspace, argument checking and
+// the host-side orchestration of the kernels (CG loop, force, leapfrog,
+// trajectory).  Declarations and contracts are in include/hqmc.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "hqmc.h"
+#include "kernels.h"
+
+using namespace hqmc;
+
+namespace {
+
+constexpr int kMaxL = 68;             // 3 complex-double slices must fit in 227 KB of shared memory
+constexpr int kChunk = 32;            // CG iterations enqueued between host checks
+constexpr int kDefaultReliable = 50;  // mixed solver residual-update period
+
+struct TimerClass {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+  size_t used = 0;
+};
+
+}  // namespace
+
+struct hqmc_config {
+  hqmc_params p{};
+  int device = 0;
+  Geo g{};
+  long long n = 0;  // sites
+  double a = 0, t1 = 0, t2 = 0, cB = 0;
+  BosonParams bp{};
+  SliceLaunch sl{};   // fused M^dagger M
+  SliceLaunch sl1{};  // apply_M and force (one CTA per slice, no cluster)
+  int ew_grid = 0;    // CG update grid (= number of <r,r> partials)
+  int act_grid = 0;
+  int reliable = kDefaultReliable;
+
+  // device workspace
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  double2 *r64 = nullptr, *p64[2] = {nullptr, nullptr}, *q64 = nullptr;
+  float2 *r32 = nullptr, *p32[2] = {nullptr, nullptr}, *q32 = nullptr, *xh32 = nullptr;
+  double2 *eta = nullptr, *Xw = nullptr, *Rw = nullptr, *vscratch = nullptr;
+  double *dSf = nullptr, *F = nullptr, *th0 = nullptr, *pm = nullptr;
+  double *part_mdagm = nullptr, *part_ew = nullptr, *part_resid = nullptr, *part_act = nullptr;
+  double *terms = nullptr, *report = nullptr;
+  CgState* st = nullptr;
+  // pinned host mirrors
+  CgState* st_h = nullptr;
+  double* terms_h = nullptr;
+  double* report_h = nullptr;
+
+  int timing = 0;
+  long long launches = 0;  // kernels enqueued by this config
+  TimerClass timers[HQMC_TIMER_COUNT];
+  std::vector<void*> allocs;
+  char err[512] = {0};
+};
+
+namespace {
+
+int fail(hqmc_config* cfg, int code, const char* fmt, ...) {
+  if (cfg) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(cfg->err, sizeof(cfg->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(cfg, HQMC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                        \
+  } while (0)
+
+#define RET(call)                 \
+  do {                            \
+    int rc_ = (call);             \
+    if (rc_ != HQMC_OK) return rc_; \
+  } while (0)
+
+// Kernel launches are made through LK so that the config can report how many
+// of its kernels it enqueued (launch_action_terms enqueues two).
+#define LK(n, call)           \
+  do {                        \
+    cfg->launches += (n);     \
+    CK(call);                 \
+  } while (0)
+
+bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+template <class T>
+int dalloc(hqmc_config* cfg, T** ptr, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(cfg, HQMC_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  cfg->allocs.push_back(p);
+  *ptr = (T*)p;
+  return HQMC_OK;
+}
+
+void release(hqmc_config* cfg) {
+  for (void* p : cfg->allocs) cudaFree(p);
+  cfg->allocs.clear();
+  if (cfg->st_h) cudaFreeHost(cfg->st_h);
+  if (cfg->terms_h) cudaFreeHost(cfg->terms_h);
+  if (cfg->report_h) cudaFreeHost(cfg->report_h);
+  for (auto& tc : cfg->timers)
+    for (auto& pr : tc.pairs) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+}
+
+// Event timing around launches of one kernel class.
+int timer_begin(hqmc_config* cfg, int cls, cudaStream_t s, int* slot) {
+  *slot = -1;
+  if (!cfg->timing) return HQMC_OK;
+  TimerClass& tc = cfg->timers[cls];
+  if (tc.used == tc.pairs.size()) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    tc.pairs.emplace_back(a, b);
+  }
+  *slot = (int)tc.used++;
+  CK(cudaEventRecord(tc.pairs[*slot].first, s));
+  return HQMC_OK;
+}
+
+int timer_end(hqmc_config* cfg, int cls, cudaStream_t s, int slot) {
+  if (slot < 0) return HQMC_OK;
+  CK(cudaEventRecord(cfg->timers[cls].pairs[slot].second, s));
+  return HQMC_OK;
+}
+
+int check_device(hqmc_config* cfg) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != cfg->device)
+    return fail(cfg, HQMC_EINVAL, "config belongs to device %d but device %d is current", cfg->device, dev);
+  return HQMC_OK;
+}
+
+int links(hqmc_config* cfg, const double* theta, bool need64, bool need32, cudaStream_t s) {
+  LK(1, launch_links(cfg->g, theta, cfg->t1, cfg->t2, need64 ? cfg->U64 : nullptr, need32 ? cfg->U32 : nullptr, s));
+  return HQMC_OK;
+}
+
+template <class R, int MODE>
+MdagmArgs<R> mdagm_args(hqmc_config* cfg) {
+  MdagmArgs<R> a{};
+  a.g = cfg->g;
+  a.cB = (R)cfg->cB;
+  return a;
+}
+
+// r_out = b - O x (FP64) with partials; then the state bookkeeping.
+int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, bool r_fp32, int fin_mode,
+             double tol, int maxit, cudaStream_t s) {
+  MdagmArgs<double> a = mdagm_args<double, MODE_RESID>(cfg);
+  a.U = cfg->U64;
+  a.x = x;
+  a.b = b;
+  a.r_out = r_out;
+  a.r_out_fp32 = r_fp32 ? 1 : 0;
+  a.part_out = cfg->part_resid;
+  int slot;
+  RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
+  LK(1, (launch_mdagm<double, MODE_RESID>(cfg->sl, a, s)));
+  RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
+  LK(1, launch_resid_finalize(cfg->part_resid, cfg->sl.grid, fin_mode, tol, maxit, cfg->part_ew, cfg->ew_grid,
+                           cfg->st, cfg->report, s));
+  return HQMC_OK;
+}
+
+template <class R>
+int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, const C2<R>* U, void* x,
+                 bool x_double, cudaStream_t s) {
+  MdagmArgs<R> a = mdagm_args<R, MODE_CGDIR>(cfg);
+  a.U = U;
+  a.y = q;
+  a.r = r;
+  a.pbuf[0] = pbuf[0];
+  a.pbuf[1] = pbuf[1];
+  a.part_in = cfg->part_ew;
+  a.n_part_in = cfg->ew_grid;
+  a.part_out = cfg->part_mdagm;
+  a.st = cfg->st;
+  int slot;
+  RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
+  LK(1, (launch_mdagm<R, MODE_CGDIR>(cfg->sl, a, s)));
+  RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
+  RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
+  LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, cfg->sl.grid,
+                         cfg->part_ew, cfg->st, s));
+  RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
+  return HQMC_OK;
+}
+
+int read_state(hqmc_config* cfg, cudaStream_t s) {
+  CK(cudaMemcpyAsync(cfg->st_h, cfg->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cfg->report_h, cfg->report, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return HQMC_OK;
+}
+
+// CG on (M^dagger M) x = phi with the link tables already built for theta.
+int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
+          hqmc_solve_info* info, cudaStream_t s) {
+  const bool mixed = solver == HQMC_SOLVER_MIXED;
+  hqmc_solve_info inf{};
+  RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, s));
+  if (mixed) CK(cudaMemsetAsync(cfg->xh32, 0, sizeof(float2) * cfg->n, s));
+  bool after_resid = true;
+  int status = HQMC_OK;
+  for (;;) {
+    RET(read_state(cfg, s));
+    const CgState& st = *cfg->st_h;
+    if (st.bb == 0.0) {  // phi = 0: the solution is zero whatever the guess
+      CK(cudaMemsetAsync(x, 0, sizeof(double2) * cfg->n, s));
+      cfg->report_h[0] = 0.0;
+      break;
+    }
+    if (st.done == CG_RUNNING && !(mixed && !after_resid)) {
+      const int chunk = mixed ? cfg->reliable : kChunk;
+      for (int c = 0; c < chunk; ++c) {
+        if (mixed)
+          RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, s));
+        else
+          RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, s));
+      }
+      after_resid = false;
+      continue;
+    }
+    if ((st.done == CG_CONVERGED || st.done == CG_RUNNING) && after_resid) break;  // true residual below tol
+    if (st.done == CG_CONVERGED || st.done == CG_RUNNING) {
+      if (mixed) {
+        LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, s));
+        RET(residual(cfg, phi, x, cfg->r32, true, FIN_RELIABLE, tol, maxit, s));
+        inf.reliable_updates++;
+      } else {
+        RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, tol, maxit, s));
+        inf.restarts++;
+      }
+      after_resid = true;
+      continue;
+    }
+    // MAXIT, BREAKDOWN or NONFINITE: report the true residual of the last iterate
+    status = st.done == CG_MAXIT ? HQMC_ENOTCONV : st.done == CG_BREAKDOWN ? HQMC_EBREAKDOWN : HQMC_ENONFINITE;
+    if (mixed) LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, s));
+    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, s));
+    RET(read_state(cfg, s));
+    break;
+  }
+  const CgState& st = *cfg->st_h;
+  if (!mixed && inf.restarts > 0 && status == HQMC_OK) inf.restarts--;  // the final check is not a restart
+  inf.status = status;
+  inf.iterations = st.k;
+  inf.true_residual = st.bb > 0 ? std::sqrt(cfg->report_h[0] / st.bb) : 0.0;
+  inf.recursive_residual = st.bb > 0 ? std::sqrt(st.rr[st.k & 1] / st.bb) : 0.0;
+  if (status == HQMC_OK && !(inf.true_residual <= tol)) status = inf.status = HQMC_ENOTCONV;
+  if (info) *info = inf;
+  return status;
+}
+
+int force(hqmc_config* cfg, const double* theta, const double2* X, double* F, double* dSf, cudaStream_t s) {
+  int slot;
+  RET(timer_begin(cfg, HQMC_TIMER_FORCE, s, &slot));
+  LK(1, launch_force(cfg->sl1, cfg->cB, cfg->U64, X, dSf, s));
+  RET(timer_end(cfg, HQMC_TIMER_FORCE, s, slot));
+  LK(1, launch_force_finish(cfg->g, cfg->bp, theta, dSf, F, s));
+  return HQMC_OK;
+}
+
+int merge_status(int a, int b) { return a != HQMC_OK ? a : b; }
+
+int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, double2* X, int nsteps, double dt,
+             double tol, int maxit, int solver, hqmc_traj_info* ti, cudaStream_t s) {
+  const bool mixed = solver == HQMC_SOLVER_MIXED;
+  const long long nb = 2 * cfg->n;
+  hqmc_solve_info si;
+  int status = HQMC_OK;
+  RET(links(cfg, theta, true, mixed, s));
+  int rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
+  if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
+  status = merge_status(status, rc);
+  ti->cg_solves++;
+  ti->cg_iterations += si.iterations;
+  ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+  RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
+  for (int n = 0; n < nsteps; ++n) {
+    LK(1, launch_kick_drift(nb, p, theta, cfg->F, dt / 2, dt, s));
+    RET(links(cfg, theta, true, mixed, s));
+    rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
+    if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
+    status = merge_status(status, rc);
+    ti->cg_solves++;
+    ti->cg_iterations += si.iterations;
+    ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+    RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
+    LK(1, launch_kick(nb, p, cfg->F, dt / 2, s));
+  }
+  ti->status = status;
+  return status;
+}
+
+int check_solver(hqmc_config* cfg, int solver) {
+  if (solver != HQMC_SOLVER_CG64 && solver != HQMC_SOLVER_MIXED)
+    return fail(cfg, HQMC_EINVAL, "unknown solver %d", solver);
+  return HQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hqmc_strerror(int status) {
+  switch (status) {
+    case HQMC_OK: return "success";
+    case HQMC_EINVAL: return "invalid argument";
+    case HQMC_ENOTCONV: return "CG did not converge within maxit";
+    case HQMC_EBREAKDOWN: return "CG breakdown (<d, O d> <= 0)";
+    case HQMC_ENONFINITE: return "non-finite value in a reduction";
+    case HQMC_ETIMEOUT: return "bounded device wait timed out";
+    case HQMC_ECUDA: return "CUDA runtime error";
+    case HQMC_ENOMEM: return "device allocation failed";
+    case HQMC_EUNSUPPORTED: return "unsupported configuration or device";
+    default: return "unknown status";
+  }
+}
+
+const char* hqmc_last_error(const hqmc_config* cfg) { return cfg ? cfg->err : "no config"; }
+
+long long hqmc_num_sites(const hqmc_config* cfg) { return cfg ? cfg->n : 0; }
+
+long long hqmc_launch_count(const hqmc_config* cfg) { return cfg ? cfg->launches : 0; }
+
+int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
+  if (!p || !out) return HQMC_EINVAL;
+  *out = nullptr;
+  if (p->L < 4 || (p->L & 1) || p->L > kMaxL) return HQMC_EINVAL;
+  if (p->Ntau < 2) return HQMC_EINVAL;
+  if (!(p->dtau > 0) || !std::isfinite(p->dtau) || !std::isfinite(p->t) || !(p->J > 0) ||
+      !std::isfinite(p->J) || !std::isfinite(p->K))
+    return HQMC_EINVAL;
+  if (p->action != HQMC_ACTION_COMPACT && p->action != HQMC_ACTION_NONCOMPACT) return HQMC_EINVAL;
+  const long long n = (long long)p->L * p->L * p->Ntau;
+  if (n > (1LL << 31) - 1) return HQMC_EINVAL;
+
+  hqmc_config* cfg = new (std::nothrow) hqmc_config();
+  if (!cfg) return HQMC_ENOMEM;
+  cfg->p = *p;
+  int rc = HQMC_OK;
+  do {
+    cudaError_t e = cudaGetDevice(&cfg->device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, cfg->device);
+    if (e != cudaSuccess) {
+      rc = fail(cfg, HQMC_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (prop.major != 10) {
+      rc = fail(cfg, HQMC_EUNSUPPORTED, "built for sm_103a; device is sm_%d%d", prop.major, prop.minor);
+      break;
+    }
+    const int L = p->L, V = L * L;
+    cfg->g = Geo{L, V, L / 2, p->Ntau};
+    cfg->n = n;
+    cfg->a = p->dtau * p->t;
+    cfg->t1 = std::tanh(cfg->a);
+    cfg->t2 = std::tanh(cfg->a / 2);
+    cfg->cB = std::cosh(cfg->a) * std::pow(std::cosh(cfg->a / 2), 6);
+    cfg->bp.cK = 1.0 / (p->J * p->dtau);
+    cfg->bp.Kdtau = p->K * p->dtau;
+    cfg->bp.noncompact = p->action == HQMC_ACTION_NONCOMPACT;
+    cfg->reliable = p->reliable_interval > 0 ? p->reliable_interval : kDefaultReliable;
+
+    // slice kernels: enough threads for one pass over a family's V/2 bonds
+    const int bonds = V / 2;
+    const int rounds = (bonds + 1023) / 1024;
+    int threads = (bonds + rounds - 1) / rounds;
+    threads = ((threads + 31) / 32) * 32;
+    if (threads < 64) threads = 64;
+    cfg->sl.g = cfg->g;
+    cfg->sl.threads = threads;
+    cfg->sl.cluster = p->Ntau < 8 ? p->Ntau : 8;
+    cfg->sl1 = cfg->sl;
+    cfg->sl1.cluster = 1;
+    cfg->sl1.grid = p->Ntau;
+    // shrink the cluster until the device can co-schedule it
+    for (;;) {
+      cfg->sl.grid = ((p->Ntau + cfg->sl.cluster - 1) / cfg->sl.cluster) * cfg->sl.cluster;
+      if (prepare_mdagm<double, MODE_CGDIR>(cfg->sl) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(cfg, HQMC_EUNSUPPORTED, "cannot configure the M^dagger M kernel for L=%d", L);
+        break;
+      }
+      if (cfg->sl.cluster == 1 || mdagm_max_active_clusters(cfg->sl) > 0) break;
+      cfg->sl.cluster--;
+    }
+    if (rc != HQMC_OK) break;
+    if (prepare_mdagm<double, MODE_APPLY>(cfg->sl) != cudaSuccess ||
+        prepare_mdagm<double, MODE_RESID>(cfg->sl) != cudaSuccess ||
+        prepare_mdagm<float, MODE_APPLY>(cfg->sl) != cudaSuccess ||
+        prepare_mdagm<float, MODE_CGDIR>(cfg->sl) != cudaSuccess || prepare_apply_M<double>(cfg->sl1) != cudaSuccess ||
+        prepare_apply_M<float>(cfg->sl1) != cudaSuccess || prepare_force(cfg->sl1) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(cfg, HQMC_EUNSUPPORTED, "cannot configure slice kernels for L=%d", L);
+      break;
+    }
+    {
+      long long b = (n + 255) / 256;
+      cfg->ew_grid = (int)(b < 1024 ? b : 1024);
+      cfg->act_grid = (int)(b < 512 ? b : 512);
+    }
+    // workspace
+    if ((rc = dalloc(cfg, &cfg->U64, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->U32, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->r64, n))) break;
+    if ((rc = dalloc(cfg, &cfg->p64[0], n))) break;
+    if ((rc = dalloc(cfg, &cfg->p64[1], n))) break;
+    if ((rc = dalloc(cfg, &cfg->q64, n))) break;
+    if ((rc = dalloc(cfg, &cfg->r32, n))) break;
+    if ((rc = dalloc(cfg, &cfg->p32[0], n))) break;
+    if ((rc = dalloc(cfg, &cfg->p32[1], n))) break;
+    if ((rc = dalloc(cfg, &cfg->q32, n))) break;
+    if ((rc = dalloc(cfg, &cfg->xh32, n))) break;
+    if ((rc = dalloc(cfg, &cfg->eta, n))) break;
+    if ((rc = dalloc(cfg, &cfg->Xw, n))) break;
+    if ((rc = dalloc(cfg, &cfg->Rw, n))) break;
+    if ((rc = dalloc(cfg, &cfg->vscratch, n))) break;
+    if ((rc = dalloc(cfg, &cfg->dSf, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->F, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->th0, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->pm, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->part_mdagm, 2 * (size_t)cfg->sl.grid))) break;
+    if ((rc = dalloc(cfg, &cfg->part_resid, 2 * (size_t)cfg->sl.grid))) break;
+    if ((rc = dalloc(cfg, &cfg->part_ew, (size_t)cfg->ew_grid))) break;
+    if ((rc = dalloc(cfg, &cfg->part_act, 4 * (size_t)cfg->act_grid))) break;
+    if ((rc = dalloc(cfg, &cfg->terms, 8))) break;
+    if ((rc = dalloc(cfg, &cfg->report, 2))) break;
+    if ((rc = dalloc(cfg, &cfg->st, 1))) break;
+    if (cudaMallocHost(&cfg->st_h, sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&cfg->terms_h, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&cfg->report_h, 2 * sizeof(double)) != cudaSuccess) {
+      rc = fail(cfg, HQMC_ENOMEM, "pinned host allocation failed");
+      break;
+    }
+    cudaMemset(cfg->st, 0, sizeof(CgState));
+    cudaMemset(cfg->report, 0, 2 * sizeof(double));
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      rc = fail(cfg, HQMC_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
+      break;
+    }
+  } while (0);
+  if (rc != HQMC_OK) {
+    release(cfg);
+    delete cfg;
+    return rc;
+  }
+  *out = cfg;
+  return HQMC_OK;
+}
+
+int hqmc_free_config(hqmc_config* cfg) {
+  if (!cfg) return HQMC_OK;
+  cudaDeviceSynchronize();
+  release(cfg);
+  delete cfg;
+  return HQMC_OK;
+}
+
+int hqmc_apply_M(hqmc_config* cfg, const double* theta, const void* x, void* y, int dagger, int precision,
+                 void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(x) || !aligned16(y)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (precision != HQMC_FP64 && precision != HQMC_FP32) return fail(cfg, HQMC_EINVAL, "bad precision");
+  const size_t vb = cfg->n * (precision == HQMC_FP64 ? sizeof(double2) : sizeof(float2));
+  if (overlap(x, vb, y, vb)) return fail(cfg, HQMC_EINVAL, "x and y overlap");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == HQMC_FP64) {
+    RET(links(cfg, theta, true, false, s));
+    LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, (const double2*)x, (double2*)y, dagger ? 1 : 0, s));
+  } else {
+    RET(links(cfg, theta, false, true, s));
+    LK(1, launch_apply_M<float>(cfg->sl1, (float)cfg->cB, cfg->U32, (const float2*)x, (float2*)y, dagger ? 1 : 0, s));
+  }
+  return HQMC_OK;
+}
+
+int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void* y, int precision, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(x) || !aligned16(y)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (precision != HQMC_FP64 && precision != HQMC_FP32) return fail(cfg, HQMC_EINVAL, "bad precision");
+  const size_t vb = cfg->n * (precision == HQMC_FP64 ? sizeof(double2) : sizeof(float2));
+  if (overlap(x, vb, y, vb)) return fail(cfg, HQMC_EINVAL, "x and y overlap");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  int slot;
+  if (precision == HQMC_FP64) {
+    RET(links(cfg, theta, true, false, s));
+    MdagmArgs<double> a = mdagm_args<double, MODE_APPLY>(cfg);
+    a.U = cfg->U64;
+    a.x = (const double2*)x;
+    a.y = (double2*)y;
+    RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
+    LK(1, (launch_mdagm<double, MODE_APPLY>(cfg->sl, a, s)));
+    RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
+  } else {
+    RET(links(cfg, theta, false, true, s));
+    MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
+    a.U = cfg->U32;
+    a.x = (const float2*)x;
+    a.y = (float2*)y;
+    RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
+    LK(1, (launch_mdagm<float, MODE_APPLY>(cfg->sl, a, s)));
+    RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
+  }
+  return HQMC_OK;
+}
+
+int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* x, double tol, int maxit, int solver,
+                  hqmc_solve_info* info, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(phi) || !aligned16(x)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (!(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "tol must be > 0 and maxit >= 0");
+  if (overlap(phi, cfg->n * 16, x, cfg->n * 16)) return fail(cfg, HQMC_EINVAL, "phi and x overlap");
+  RET(check_solver(cfg, solver));
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  RET(links(cfg, theta, true, solver == HQMC_SOLVER_MIXED, s));
+  return solve(cfg, (const double2*)phi, (double2*)x, tol, maxit, solver, info, s);
+}
+
+int hqmc_force(hqmc_config* cfg, const double* theta, const void* X, double* F, double* dSf, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(X) || !aligned16(F) || (dSf && !aligned16(dSf)))
+    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  const size_t fb = cfg->n * 16;
+  if (overlap(F, fb, theta, fb) || (dSf && (overlap(dSf, fb, theta, fb) || overlap(dSf, fb, F, fb))))
+    return fail(cfg, HQMC_EINVAL, "output overlaps an input");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  RET(links(cfg, theta, true, false, s));
+  return force(cfg, theta, (const double2*)X, F, dSf ? dSf : cfg->dSf, s);
+}
+
+int hqmc_action_terms(hqmc_config* cfg, const double* theta, const double* p, const void* phi, const void* X,
+                      double* out_host, void* stream) {
+  if (!cfg || !out_host) return HQMC_EINVAL;
+  if (!aligned16(theta) || (p && !aligned16(p)) || (phi && !aligned16(phi)) || (X && !aligned16(X)))
+    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool ab = phi && X;
+  LK(2, launch_action_terms(cfg->g, cfg->bp, theta, p, ab ? (const double2*)phi : nullptr,
+                         ab ? (const double2*)X : nullptr, cfg->act_grid, cfg->part_act, cfg->terms, s));
+  CK(cudaMemcpyAsync(cfg->terms_h, cfg->terms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < 3; ++i) out_host[i] = cfg->terms_h[i];
+  return HQMC_OK;
+}
+
+int hqmc_draw(hqmc_config* cfg, uint64_t seed, uint64_t traj_counter, double* p, void* R, double* u_host,
+              void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if ((p && !aligned16(p)) || (R && !aligned16(R))) return fail(cfg, HQMC_EINVAL, "misaligned pointer");
+  RET(check_device(cfg));
+  if (p || R) LK(1, launch_draw(cfg->n, seed, traj_counter, p, (double2*)R, (cudaStream_t)stream));
+  if (u_host) philox_uniform_host(seed, traj_counter, u_host);
+  return HQMC_OK;
+}
+
+int hqmc_leapfrog(hqmc_config* cfg, double* theta, double* p, const void* phi, void* X, int nsteps, double dt,
+                  double tol, int maxit, int solver, hqmc_traj_info* info, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(p) || !aligned16(phi) || !aligned16(X))
+    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (nsteps < 0 || !std::isfinite(dt) || !(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "bad step parameters");
+  RET(check_solver(cfg, solver));
+  RET(check_device(cfg));
+  hqmc_traj_info ti{};
+  const int rc = leapfrog(cfg, theta, p, (const double2*)phi, (double2*)X, nsteps, dt, tol, maxit, solver, &ti,
+                          (cudaStream_t)stream);
+  if (rc == HQMC_OK || rc == HQMC_ENOTCONV) CK(cudaStreamSynchronize((cudaStream_t)stream));
+  ti.status = rc;
+  if (info) *info = ti;
+  return rc;
+}
+
+int hqmc_trajectory(hqmc_config* cfg, double* theta, uint64_t seed, uint64_t traj_counter, const double* p_in,
+                    const void* R_in, const double* u_in, int nsteps, double dt, double tol, int maxit, int solver,
+                    hqmc_traj_info* info, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || (p_in && !aligned16(p_in)) || (R_in && !aligned16(R_in)))
+    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (nsteps < 0 || !std::isfinite(dt) || !(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "bad step parameters");
+  RET(check_solver(cfg, solver));
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = cfg->n;
+  hqmc_traj_info ti{};
+  // (i) momenta and pseudofermion source
+  if (p_in)
+    CK(cudaMemcpyAsync(cfg->pm, p_in, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else
+    LK(1, launch_draw(n, seed, traj_counter, cfg->pm, nullptr, s));
+  if (R_in)
+    CK(cudaMemcpyAsync(cfg->Rw, R_in, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  else
+    LK(1, launch_draw(n, seed, traj_counter, nullptr, cfg->Rw, s));
+  if (u_in)
+    ti.u = *u_in;
+  else
+    philox_uniform_host(seed, traj_counter, &ti.u);
+  RET(links(cfg, theta, true, false, s));
+  LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, cfg->Rw, cfg->eta, 1, s));  // eta = M^dagger R
+  // H0 = S_B + sum p^2 + R^dagger R
+  LK(2, launch_action_terms(cfg->g, cfg->bp, theta, cfg->pm, cfg->Rw, cfg->Rw, cfg->act_grid, cfg->part_act,
+                         cfg->terms, s));
+  CK(cudaMemcpyAsync(cfg->th0, theta, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(cfg->Xw, 0, n * sizeof(double2), s));
+  // (ii) leapfrog
+  int rc = leapfrog(cfg, theta, cfg->pm, cfg->eta, cfg->Xw, nsteps, dt, tol, maxit, solver, &ti, s);
+  if (rc != HQMC_OK && rc != HQMC_ENOTCONV) {
+    CK(cudaMemcpyAsync(theta, cfg->th0, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    ti.status = rc;
+    if (info) *info = ti;
+    return rc;
+  }
+  // H1 = S_B + sum p^2 + eta^dagger X
+  LK(2, launch_action_terms(cfg->g, cfg->bp, theta, cfg->pm, cfg->eta, cfg->Xw, cfg->act_grid, cfg->part_act,
+                         cfg->terms + 3, s));
+  CK(cudaMemcpyAsync(cfg->terms_h, cfg->terms, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double* t = cfg->terms_h;
+  ti.H0 = t[0] + t[1] + t[2];
+  ti.H1 = t[3] + t[4] + t[5];
+  ti.dH = ti.H1 - ti.H0;
+  if (!std::isfinite(ti.dH)) rc = HQMC_ENONFINITE;
+  // (iii) Metropolis: accept iff u < exp(H0 - H1)
+  ti.accepted = (rc == HQMC_OK || rc == HQMC_ENOTCONV) && std::isfinite(ti.dH) && ti.u < std::exp(-ti.dH);
+  if (!ti.accepted) {
+    CK(cudaMemcpyAsync(theta, cfg->th0, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  ti.status = rc;
+  if (info) *info = ti;
+  return rc;
+}
+
+int hqmc_probe_fp64_rate(hqmc_config* cfg, double* tflops_out) {
+  if (!cfg || !tflops_out) return HQMC_EINVAL;
+  RET(check_device(cfg));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device));
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    CK(cudaEventRecord(a, 0));
+    LK(1, launch_fp64_probe(blocks, threads, iters, cfg->report, 0));
+    CK(cudaEventRecord(b, 0));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    if (rep > 0 && ms < best) best = ms;  // the first launch is a warm-up
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const double flops = 16.0 * iters * (double)blocks * threads;
+  *tflops_out = flops / (best * 1e-3) / 1e12;
+  return HQMC_OK;
+}
+
+int hqmc_set_timing(hqmc_config* cfg, int enable) {
+  if (!cfg) return HQMC_EINVAL;
+  CK(cudaDeviceSynchronize());
+  cfg->timing = enable ? 1 : 0;
+  for (auto& tc : cfg->timers) tc.used = 0;
+  return HQMC_OK;
+}
+
+int hqmc_get_timing(hqmc_config* cfg, int timer, long long* launches, double* total_ms) {
+  if (!cfg || timer < 0 || timer >= HQMC_TIMER_COUNT) return HQMC_EINVAL;
+  CK(cudaDeviceSynchronize());
+  const TimerClass& tc = cfg->timers[timer];
+  double sum = 0.0;
+  for (size_t i = 0; i < tc.used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, tc.pairs[i].first, tc.pairs[i].second));
+    sum += ms;
+  }
+  if (launches) *launches = (long long)tc.used;
+  if (total_ms) *total_ms = sum;
+  return HQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Host-side launch interface of the HQMC kernels (internal to libhqmc).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace hqmc {
+
+// Launch shape of the slice kernels: one CTA per imaginary-time slice, grouped
+// into thread-block clusters of `cluster` consecutive slices.
+struct SliceLaunch {
+  Geo g;
+  int threads;   // threads per CTA
+  int cluster;   // CTAs per cluster (consecutive slices)
+  int grid;      // CTAs, a multiple of cluster, >= Ntau
+};
+
+enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_CGDIR = 2 };
+
+template <class R>
+struct MdagmArgs {
+  Geo g;
+  R cB;                    // cosh(a) cosh(a/2)^6
+  const C2<R>* U;          // link table, two complex links per site
+  const C2<R>* x;          // APPLY / RESID input
+  C2<R>* y;                // APPLY output; CGDIR: q = O p
+  const double2* b;        // RESID right-hand side (complex double)
+  void* r_out;             // RESID residual b - O x (complex double, or float if r_out_fp32)
+  int r_out_fp32;
+  const C2<R>* r;          // CGDIR residual
+  C2<R>* pbuf[2];          // CGDIR directions: iteration k reads pbuf[k&1], writes pbuf[(k+1)&1]
+  const double* part_in;   // CGDIR: partials of <r, r> from the update kernel
+  int n_part_in;
+  double* part_out;        // per-CTA partials: CGDIR <p, Op>; RESID <r,r> then <b,b>
+  CgState* st;
+};
+
+// Fused M^dagger M (three modes).
+template <class R, int MODE>
+cudaError_t launch_mdagm(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStream_t s);
+template <class R, int MODE>
+cudaError_t prepare_mdagm(const SliceLaunch& sl);
+// Clusters of sl.cluster CTAs the device can keep resident (<= 0: none / error).
+int mdagm_max_active_clusters(const SliceLaunch& sl);
+
+// y = M x or M^dagger x.
+template <class R>
+cudaError_t launch_apply_M(const SliceLaunch& sl, R cB, const C2<R>* U, const C2<R>* x, C2<R>* y,
+                           int dagger, cudaStream_t s);
+template <class R>
+cudaError_t prepare_apply_M(const SliceLaunch& sl);
+
+// Link tables U = t_f e^{i theta} (double and/or float), theta -> links.
+cudaError_t launch_links(const Geo& g, const double* theta, double t1, double t2, double2* U64,
+                         float2* U32, cudaStream_t s);
+
+// CG update x += alpha p, r -= alpha q, partial <r,r>; MIXED: x is the float
+// correction.  Reads alpha from the partials of <p, Op>.
+// The direction used is pbuf[(k2+1)&1], the one the direction kernel wrote.
+template <class R>
+cudaError_t launch_cg_update(long long n, int grid, void* x, int x_is_double, C2<R>* r,
+                             C2<R>* const pbuf[2], const C2<R>* q, const double* part_pq, int n_pq,
+                             double* part_rr, CgState* st, cudaStream_t s);
+
+enum { FIN_START = 0, FIN_RESTART = 1, FIN_RELIABLE = 2, FIN_REPORT = 3 };
+// Sums the RESID partials into the CG state.
+cudaError_t launch_resid_finalize(const double* part, int n, int mode, double tol, int maxit,
+                                  double* part_rr_out, int n_rr_out, CgState* st, double* report,
+                                  cudaStream_t s);
+
+// x64 += xh32; xh32 = 0.
+cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, cudaStream_t s);
+
+// Fermion force dS_f/dtheta given X (FP64).
+cudaError_t launch_force(const SliceLaunch& sl, double cB, const double2* U, const double2* X,
+                         double* dSf, cudaStream_t s);
+cudaError_t prepare_force(const SliceLaunch& sl);
+
+struct BosonParams {
+  double cK;      // 1/(J dtau)
+  double Kdtau;   // K * dtau
+  int noncompact;
+};
+// F = -dSf - dS_B(theta).
+cudaError_t launch_force_finish(const Geo& g, const BosonParams& bp, const double* theta,
+                                const double* dSf, double* F, cudaStream_t s);
+// p += h F
+cudaError_t launch_kick(long long nb, double* p, const double* F, double h, cudaStream_t s);
+// p += h F; theta += 2 dt p
+cudaError_t launch_kick_drift(long long nb, double* p, double* theta, const double* F, double h,
+                              double dt, cudaStream_t s);
+// terms[0] = S_B, terms[1] = sum p^2, terms[2] = Re <a, b>  (device doubles)
+cudaError_t launch_action_terms(const Geo& g, const BosonParams& bp, const double* theta,
+                                const double* p, const double2* a, const double2* b, int grid,
+                                double* part, double* terms, cudaStream_t s);
+// Philox draws.
+cudaError_t launch_draw(long long n_sites, uint64_t seed, uint64_t counter, double* p, double2* R,
+                        cudaStream_t s);
+void philox_uniform_host(uint64_t seed, uint64_t counter, double* u);
+// FP64 FMA throughput probe (16 flops per thread per iteration).
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
+
+}  // namespace hqmc

@@ -1,0 +1,302 @@
+// Fused application of M^dagger M, M and M^dagger (Methods, "Matrix-free
+// representation of M^dagger M v"; matrix M of Eq. (M_alpha); checkerboard
+// B of Eq. (eq24)).
+//
+// With B_tau = cB P_tau (see common.cuh) and z_tau = P_tau x_tau,
+//   (M^dagger M x)_tau = x_tau - s_tau cB z_{tau-1} + cB P_tau (cB z_tau - s'_tau x_{tau+1}),
+// s_0 = -1, s'_{Ntau-1} = -1, otherwise +1.  Each slice therefore needs two
+// sweeps of P over its own data plus z_{tau-1} of the previous slice.
+//
+// Design: one CTA per slice; consecutive slices form a thread-block cluster.
+// Every CTA computes z_tau in shared memory and publishes it; after a cluster
+// barrier the CTA of slice tau reads z_{tau-1} from its left neighbour through
+// distributed shared memory.  Only the first CTA of each cluster recomputes
+// the halo z_{tau0-1} itself (overlapped with the barrier), so a cluster of C
+// slices does 2C+1 sweeps instead of 3C.  All 7 factor passes of a sweep run
+// on a slice held in shared memory; HBM sees each input once and the output
+// once.
+#include <cooperative_groups.h>
+
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace hqmc {
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+template <class R, int MODE>
+__device__ __forceinline__ C2<R> load_input(const MdagmArgs<R>& a, const C2<R>* p_old, size_t g, R beta,
+                                            bool first) {
+  if (MODE == MODE_CGDIR) {
+    C2<R> rv = a.r[g];
+    if (first) return rv;
+    return caxpy(rv, beta, p_old[g]);
+  }
+  return a.x[g];
+}
+
+template <class R, int MODE>
+__global__ void __launch_bounds__(1024, 1) mdagm_kernel(const MdagmArgs<R> a) {
+  using T = C2<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int V = a.g.V, N = a.g.Ntau;
+  T* Z = reinterpret_cast<T*>(smem_raw);  // z_tau, read by the right neighbour
+  T* W = Z + V;                           // work slice
+  T* Y = W + V;                           // output accumulator
+  __shared__ double red[32];
+  __shared__ int s_flags;                 // bit 0: stop, bit 1: first iteration of a segment
+  __shared__ R s_beta;
+  __shared__ int s_k;
+
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
+  const int tau = blockIdx.x;
+  const bool active = tau < N;
+
+  if (MODE == MODE_CGDIR) {
+    // Direction step of CG: beta = <r_k, r_k> / <r_{k-1}, r_{k-1}> from the
+    // update kernel's partials; every CTA reaches the same decision.
+    if (threadIdx.x < 32) {
+      CgState* st = a.st;
+      const int lane = threadIdx.x;
+      const int done = *(volatile int*)&st->done;
+      const int k = *(volatile int*)&st->k;
+      const int seg = st->seg_start;
+      int flags = 0;
+      double beta = 0.0;
+      int new_done = CG_RUNNING;
+      if (done != CG_RUNNING) {
+        flags = 1;
+      } else if (k >= st->maxit) {
+        flags = 1;
+        new_done = CG_MAXIT;
+      } else if (k == seg) {
+        flags = 2;
+      } else {
+        const double rr = warp_sum_partials(a.part_in, a.n_part_in);
+        if (!isfinite(rr)) {
+          flags = 1;
+          new_done = CG_NONFINITE;
+        } else if (rr <= st->tol2bb) {
+          flags = 1;
+          new_done = CG_CONVERGED;
+        } else {
+          beta = rr / st->rr[(k - 1) & 1];
+        }
+        if (blockIdx.x == 0 && lane == 0) st->rr[k & 1] = rr;
+      }
+      if (blockIdx.x == 0 && lane == 0) {
+        if (new_done != CG_RUNNING) st->done = new_done;
+        if (!(flags & 1)) st->k2 = k;
+      }
+      if (lane == 0) {
+        s_flags = flags;
+        s_beta = (R)beta;
+        s_k = k;
+      }
+    }
+    __syncthreads();
+    if (s_flags & 1) return;  // uniform over the whole grid: no cluster barrier is pending
+  }
+  const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);
+  const R beta = (MODE == MODE_CGDIR) ? s_beta : R(0);
+  const C2<R>* p_old = nullptr;
+  C2<R>* p_new = nullptr;
+  if (MODE == MODE_CGDIR) {
+    // select without indexing the parameter array (keeps it out of local memory)
+    p_old = (s_k & 1) ? a.pbuf[1] : a.pbuf[0];
+    p_new = (s_k & 1) ? a.pbuf[0] : a.pbuf[1];
+  }
+  const R cB = a.cB;
+
+  const size_t base = (size_t)tau * V;
+  const T* Ut = a.U + base * 2;
+  if (active) {
+    for (int s = threadIdx.x; s < V; s += blockDim.x) {
+      T v = load_input<R, MODE>(a, p_old, base + s, beta, first);
+      Z[s] = v;
+      Y[s] = v;
+      if (MODE == MODE_CGDIR) p_new[base + s] = v;
+    }
+    __syncthreads();
+    apply_P(a.g, Z, Ut);  // z_tau = P_tau x_tau
+  }
+  cluster_arrive();  // z_tau published
+
+  const T* Zprev = W;
+  if (rank == 0 && active) {
+    // halo: z_{tau-1} = P_{tau-1} x_{tau-1} for the first slice of the cluster
+    const int taum = (tau == 0) ? N - 1 : tau - 1;
+    const size_t bm = (size_t)taum * V;
+    for (int s = threadIdx.x; s < V; s += blockDim.x) W[s] = load_input<R, MODE>(a, p_old, bm + s, beta, first);
+    __syncthreads();
+    apply_P(a.g, W, a.U + bm * 2);
+  }
+  cluster_wait();
+  if (rank != 0) Zprev = cl.map_shared_rank(Z, rank - 1);
+
+  double acc0 = 0.0, acc1 = 0.0;
+  if (active) {
+    const R sig = (tau == 0) ? R(-1) : R(1);
+    const R sigp = (tau == N - 1) ? R(-1) : R(1);
+    for (int s = threadIdx.x; s < V; s += blockDim.x) Y[s] = caxpy(Y[s], -sig * cB, Zprev[s]);
+    __syncthreads();  // W (rank 0's halo) fully consumed before it is reused
+    const int taup = (tau == N - 1) ? 0 : tau + 1;
+    const size_t bp = (size_t)taup * V;
+    for (int s = threadIdx.x; s < V; s += blockDim.x) {
+      T xn = load_input<R, MODE>(a, p_old, bp + s, beta, first);
+      W[s] = caxpy(cscale(cB, Z[s]), -sigp, xn);
+    }
+  }
+  cluster_arrive();  // finished reading the neighbour's shared memory
+  if (active) {
+    __syncthreads();
+    apply_P(a.g, W, Ut);
+    for (int s = threadIdx.x; s < V; s += blockDim.x) {
+      T q = caxpy(Y[s], cB, W[s]);
+      if (MODE == MODE_APPLY) {
+        a.y[base + s] = q;
+      } else if (MODE == MODE_CGDIR) {
+        a.y[base + s] = q;
+        acc0 += cdot_re(p_new[base + s], q);
+      } else {  // MODE_RESID (R = double): r = b - O x
+        const double2 bv = a.b[base + s];
+        const double2 rv = make_double2(bv.x - (double)q.x, bv.y - (double)q.y);
+        if (a.r_out_fp32)
+          reinterpret_cast<float2*>(a.r_out)[base + s] = make_float2((float)rv.x, (float)rv.y);
+        else
+          reinterpret_cast<double2*>(a.r_out)[base + s] = rv;
+        acc0 += rv.x * rv.x + rv.y * rv.y;
+        acc1 += bv.x * bv.x + bv.y * bv.y;
+      }
+    }
+  }
+  if (MODE != MODE_APPLY) {
+    const double t0 = block_sum(acc0, red);
+    if (threadIdx.x == 0) a.part_out[blockIdx.x] = t0;
+    if (MODE == MODE_RESID) {
+      const double t1 = block_sum(acc1, red);
+      if (threadIdx.x == 0) a.part_out[gridDim.x + blockIdx.x] = t1;
+    }
+  }
+  cluster_wait();  // keep z_tau alive until the right neighbour has read it
+}
+
+template <class R, int MODE>
+static size_t mdagm_smem(const SliceLaunch& sl) {
+  return (size_t)3 * sl.g.V * sizeof(C2<R>);
+}
+
+template <class R, int MODE>
+cudaError_t prepare_mdagm(const SliceLaunch& sl) {
+  cudaError_t e = cudaFuncSetAttribute(mdagm_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)mdagm_smem<R, MODE>(sl));
+  if (e != cudaSuccess) return e;
+  if (sl.cluster > 8)
+    e = cudaFuncSetAttribute(mdagm_kernel<R, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+template <class R, int MODE>
+cudaError_t launch_mdagm(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sl.grid);
+  cfg.blockDim = dim3(sl.threads);
+  cfg.dynamicSmemBytes = mdagm_smem<R, MODE>(sl);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = sl.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mdagm_kernel<R, MODE>, a);
+}
+
+int mdagm_max_active_clusters(const SliceLaunch& sl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sl.grid);
+  cfg.blockDim = dim3(sl.threads);
+  cfg.dynamicSmemBytes = mdagm_smem<double, MODE_CGDIR>(sl);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = sl.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)mdagm_kernel<double, MODE_CGDIR>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return n;
+}
+
+template cudaError_t launch_mdagm<double, MODE_APPLY>(const SliceLaunch&, const MdagmArgs<double>&, cudaStream_t);
+template cudaError_t launch_mdagm<double, MODE_RESID>(const SliceLaunch&, const MdagmArgs<double>&, cudaStream_t);
+template cudaError_t launch_mdagm<double, MODE_CGDIR>(const SliceLaunch&, const MdagmArgs<double>&, cudaStream_t);
+template cudaError_t launch_mdagm<float, MODE_APPLY>(const SliceLaunch&, const MdagmArgs<float>&, cudaStream_t);
+template cudaError_t launch_mdagm<float, MODE_CGDIR>(const SliceLaunch&, const MdagmArgs<float>&, cudaStream_t);
+template cudaError_t prepare_mdagm<double, MODE_APPLY>(const SliceLaunch&);
+template cudaError_t prepare_mdagm<double, MODE_RESID>(const SliceLaunch&);
+template cudaError_t prepare_mdagm<double, MODE_CGDIR>(const SliceLaunch&);
+template cudaError_t prepare_mdagm<float, MODE_APPLY>(const SliceLaunch&);
+template cudaError_t prepare_mdagm<float, MODE_CGDIR>(const SliceLaunch&);
+
+// ---------------------------------------------------------------------------
+// y = M x:        y_tau = x_tau - s_tau  cB P_{tau-1} x_{tau-1}
+// y = M^dagger x: y_tau = x_tau - s'_tau cB P_tau x_{tau+1}   (B Hermitian)
+template <class R>
+__global__ void __launch_bounds__(1024, 1)
+apply_M_kernel(Geo g, R cB, const C2<R>* __restrict__ U, const C2<R>* __restrict__ x,
+               C2<R>* __restrict__ y, int dagger) {
+  using T = C2<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* W = reinterpret_cast<T*>(smem_raw);
+  const int V = g.V, N = g.Ntau;
+  const int tau = blockIdx.x;
+  int src, uslice;
+  R sign;
+  if (!dagger) {
+    src = (tau == 0) ? N - 1 : tau - 1;
+    uslice = src;
+    sign = (tau == 0) ? R(1) : R(-1);
+  } else {
+    src = (tau == N - 1) ? 0 : tau + 1;
+    uslice = tau;
+    sign = (tau == N - 1) ? R(1) : R(-1);
+  }
+  const size_t bs = (size_t)src * V, bt = (size_t)tau * V;
+  for (int s = threadIdx.x; s < V; s += blockDim.x) W[s] = x[bs + s];
+  __syncthreads();
+  apply_P(g, W, U + (size_t)uslice * V * 2);
+  for (int s = threadIdx.x; s < V; s += blockDim.x) y[bt + s] = caxpy(x[bt + s], sign * cB, W[s]);
+}
+
+template <class R>
+cudaError_t prepare_apply_M(const SliceLaunch& sl) {
+  return cudaFuncSetAttribute(apply_M_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sl.g.V * sizeof(C2<R>)));
+}
+
+template <class R>
+cudaError_t launch_apply_M(const SliceLaunch& sl, R cB, const C2<R>* U, const C2<R>* x, C2<R>* y,
+                           int dagger, cudaStream_t s) {
+  apply_M_kernel<R><<<sl.g.Ntau, sl.threads, sl.g.V * sizeof(C2<R>), s>>>(sl.g, cB, U, x, y, dagger);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_apply_M<double>(const SliceLaunch&, double, const double2*, const double2*, double2*, int, cudaStream_t);
+template cudaError_t launch_apply_M<float>(const SliceLaunch&, float, const float2*, const float2*, float2*, int, cudaStream_t);
+template cudaError_t prepare_apply_M<double>(const SliceLaunch&);
+template cudaError_t prepare_apply_M<float>(const SliceLaunch&);
+
+}  // namespace hqmc

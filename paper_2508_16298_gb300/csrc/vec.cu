@@ -1,0 +1,432 @@
+// Element-wise and reduction kernels of the HQMC path: link tables, the CG
+// vector update (Eq. (pCG)), residual bookkeeping, leapfrog kicks and drifts
+// (Eq. (leapfrog)), the Hamiltonian terms of Eq. (H_hmc) and the Gaussian
+// draws of HQMC step (i).
+#include "kernels.h"
+
+namespace hqmc {
+
+static inline int ew_blocks(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// Link tables: U[site][c] = t_f e^{i theta}, t1 = tanh(a) for x-bonds with even
+// tail x (family 1, the merged middle factor), t2 = tanh(a/2) for all others.
+__global__ void links_kernel(Geo g, const double* __restrict__ theta, double t1, double t2,
+                             double2* __restrict__ U64, float2* __restrict__ U32, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i % g.V);
+    const int x = s % g.L;
+    const double2 th = reinterpret_cast<const double2*>(theta)[i];
+    double sx, cx, sy, cy;
+    sincos(th.x, &sx, &cx);
+    sincos(th.y, &sy, &cy);
+    const double tx = (x & 1) ? t2 : t1;
+    const double2 ux = make_double2(tx * cx, tx * sx);
+    const double2 uy = make_double2(t2 * cy, t2 * sy);
+    if (U64) {
+      U64[2 * i] = ux;
+      U64[2 * i + 1] = uy;
+    }
+    if (U32) {
+      U32[2 * i] = make_float2((float)ux.x, (float)ux.y);
+      U32[2 * i + 1] = make_float2((float)uy.x, (float)uy.y);
+    }
+  }
+}
+
+cudaError_t launch_links(const Geo& g, const double* theta, double t1, double t2, double2* U64,
+                         float2* U32, cudaStream_t s) {
+  const long long n = (long long)g.V * g.Ntau;
+  links_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(g, theta, t1, t2, U64, U32, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CG update: alpha = <r,r>/<p,Op>; x += alpha p; r -= alpha Op; partial <r,r>.
+template <class R>
+__global__ void __launch_bounds__(256) cg_update_kernel(long long n, void* x, int x_is_double,
+                                                        C2<R>* __restrict__ r,
+                                                        C2<R>* p0, C2<R>* p1,
+                                                        const C2<R>* __restrict__ q,
+                                                        const double* __restrict__ part_pq, int n_pq,
+                                                        double* __restrict__ part_rr, CgState* st) {
+  __shared__ double red[32];
+  __shared__ int s_stop;
+  __shared__ double s_alpha;
+  __shared__ int s_k;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int done = *(volatile int*)&st->done;
+    int stop = 0;
+    double alpha = 0.0;
+    if (done != CG_RUNNING) {
+      stop = 1;
+    } else {
+      const int k = st->k2;
+      const double pq = warp_sum_partials(part_pq, n_pq);
+      const double rr = st->rr[k & 1];
+      if (!isfinite(pq) || !(pq > 0.0)) {
+        stop = 1;
+        if (blockIdx.x == 0 && lane == 0) st->done = isfinite(pq) ? CG_BREAKDOWN : CG_NONFINITE;
+      } else {
+        alpha = rr / pq;
+        if (blockIdx.x == 0 && lane == 0) {
+          st->pq_last = pq;
+          st->alpha_last = alpha;
+        }
+      }
+    }
+    if (lane == 0) {
+      s_stop = stop;
+      s_alpha = alpha;
+      s_k = st->k2;
+    }
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const R alpha = (R)s_alpha;
+  const C2<R>* __restrict__ p = ((s_k + 1) & 1) ? p1 : p0;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C2<R> pv = p[i];
+    C2<R> rv = caxpy(r[i], -alpha, q[i]);
+    r[i] = rv;
+    if (x_is_double) {
+      double2* xd = reinterpret_cast<double2*>(x);
+      xd[i] = caxpy(xd[i], (double)alpha, make_double2(pv.x, pv.y));
+    } else {
+      float2* xf = reinterpret_cast<float2*>(x);
+      xf[i] = caxpy(xf[i], (float)alpha, make_float2(pv.x, pv.y));
+    }
+    acc += cdot_re(rv, rv);
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    part_rr[blockIdx.x] = t;
+    if (blockIdx.x == 0) st->k = st->k2 + 1;
+  }
+}
+
+template <class R>
+cudaError_t launch_cg_update(long long n, int grid, void* x, int x_is_double, C2<R>* r,
+                             C2<R>* const pbuf[2], const C2<R>* q, const double* part_pq, int n_pq,
+                             double* part_rr, CgState* st, cudaStream_t s) {
+  cg_update_kernel<R><<<grid, 256, 0, s>>>(n, x, x_is_double, r, pbuf[0], pbuf[1], q, part_pq, n_pq,
+                                           part_rr, st);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_update<double>(long long, int, void*, int, double2*, double2* const[2],
+                                              const double2*, const double*, int, double*, CgState*,
+                                              cudaStream_t);
+template cudaError_t launch_cg_update<float>(long long, int, void*, int, float2*, float2* const[2],
+                                             const float2*, const double*, int, double*, CgState*,
+                                             cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Residual bookkeeping after r = b - O x (partials: <r,r> then <b,b>).
+//  START:    new solve; sets bb, tol2bb, k = seg_start = 0, rr[0].
+//  RESTART:  new recurrence segment from the true residual (FP64 solver).
+//  RELIABLE: keep the search direction; hand <r,r> to the next direction step
+//            through the update-kernel partial slots (mixed solver).
+//  REPORT:   only report ||r||/||b|| (final check after maxit).
+__global__ void resid_finalize_kernel(const double* __restrict__ part, int n, int mode, double tol,
+                                      int maxit, double* __restrict__ part_rr_out, int n_rr_out,
+                                      CgState* st, double* report) {
+  const double rr = warp_sum_partials(part, n);
+  const double bb = warp_sum_partials(part + n, n);
+  if (mode == FIN_RELIABLE)
+    for (int k = 1 + threadIdx.x; k < n_rr_out; k += blockDim.x) part_rr_out[k] = 0.0;
+  if (threadIdx.x != 0) return;
+  if (report) {
+    report[0] = rr;
+    report[1] = bb;
+  }
+  if (mode == FIN_START) {
+    st->bb = bb;
+    st->tol2bb = tol * tol * bb;
+    st->k = 0;
+    st->k2 = 0;
+    st->seg_start = 0;
+    st->maxit = maxit;
+    st->rr[0] = rr;
+    st->rr[1] = rr;
+    st->pq_last = 0.0;
+    st->alpha_last = 0.0;
+    if (!isfinite(rr) || !isfinite(bb)) st->done = CG_NONFINITE;
+    else if (bb == 0.0 || rr <= st->tol2bb) st->done = CG_CONVERGED;
+    else if (maxit <= 0) st->done = CG_MAXIT;
+    else st->done = CG_RUNNING;
+  } else if (mode == FIN_RESTART || mode == FIN_RELIABLE) {
+    const int k = st->k;
+    if (mode == FIN_RESTART) {
+      st->seg_start = k;
+      st->rr[k & 1] = rr;
+    } else {
+      part_rr_out[0] = rr;
+    }
+    if (!isfinite(rr)) st->done = CG_NONFINITE;
+    else if (rr <= st->tol2bb) st->done = CG_CONVERGED;
+    else if (k >= maxit) st->done = CG_MAXIT;
+    else st->done = CG_RUNNING;
+  }
+}
+
+cudaError_t launch_resid_finalize(const double* part, int n, int mode, double tol, int maxit,
+                                  double* part_rr_out, int n_rr_out, CgState* st, double* report,
+                                  cudaStream_t s) {
+  resid_finalize_kernel<<<1, 256, 0, s>>>(part, n, mode, tol, maxit, part_rr_out, n_rr_out, st, report);
+  return cudaGetLastError();
+}
+
+__global__ void accumulate_correction_kernel(long long n, double2* __restrict__ x, float2* __restrict__ xh) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 d = xh[i];
+    const double2 xv = x[i];
+    x[i] = make_double2(xv.x + (double)d.x, xv.y + (double)d.y);
+    xh[i] = make_float2(0.f, 0.f);
+  }
+}
+
+cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, cudaStream_t s) {
+  accumulate_correction_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, x, xh);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Bosonic force (Results, Eq. (eq3) and the compact action beside it, with
+// S = dtau sum_tau L_B):  dS_B/dtheta_{tau,b} = cK [f'(theta_tau - theta_{tau-1})
+// - f'(theta_{tau+1} - theta_tau)] with f' = sin (compact) or 2d (non-compact),
+// plus the plaquette term K dtau d/dtheta sum cos(curl theta).
+__device__ __forceinline__ double curl_at(const double* th, int L, int x, int y) {
+  const int xp = (x + 1 == L) ? 0 : x + 1, yp = (y + 1 == L) ? 0 : y + 1;
+  return th[2 * (x + L * y)] + th[2 * (xp + L * y) + 1] - th[2 * (x + L * yp)] - th[2 * (x + L * y) + 1];
+}
+
+__device__ __forceinline__ double fprime(double d, int noncompact) { return noncompact ? 2.0 * d : sin(d); }
+
+__global__ void force_finish_kernel(Geo g, BosonParams bp, const double* __restrict__ theta,
+                                    const double* __restrict__ dSf, double* __restrict__ F, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int tau = (int)(i / g.V);
+    const int s = (int)(i - (long long)tau * g.V);
+    const int x = s % g.L, y = s / g.L;
+    const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
+    const int tm = (tau == 0) ? g.Ntau - 1 : tau - 1;
+    const double* th = theta + (size_t)tau * g.V * 2;
+    const double* thp = theta + (size_t)tp * g.V * 2;
+    const double* thm = theta + (size_t)tm * g.V * 2;
+    double dB[2];
+    for (int c = 0; c < 2; ++c) {
+      const double t0 = th[2 * s + c];
+      dB[c] = bp.cK * (fprime(t0 - thm[2 * s + c], bp.noncompact) - fprime(thp[2 * s + c] - t0, bp.noncompact));
+    }
+    if (bp.Kdtau != 0.0) {
+      const int xm = (x == 0) ? g.L - 1 : x - 1, ym = (y == 0) ? g.L - 1 : y - 1;
+      const double s00 = sin(curl_at(th, g.L, x, y));
+      dB[0] += -bp.Kdtau * s00 + bp.Kdtau * sin(curl_at(th, g.L, x, ym));
+      dB[1] += bp.Kdtau * s00 - bp.Kdtau * sin(curl_at(th, g.L, xm, y));
+    }
+    const double2 f = reinterpret_cast<const double2*>(dSf)[i];
+    reinterpret_cast<double2*>(F)[i] = make_double2(-f.x - dB[0], -f.y - dB[1]);
+  }
+}
+
+cudaError_t launch_force_finish(const Geo& g, const BosonParams& bp, const double* theta,
+                                const double* dSf, double* F, cudaStream_t s) {
+  const long long n = (long long)g.V * g.Ntau;
+  force_finish_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(g, bp, theta, dSf, F, n);
+  return cudaGetLastError();
+}
+
+__global__ void kick_kernel(long long nb, double* __restrict__ p, const double* __restrict__ F, double h) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] += F[i] * h;
+}
+
+__global__ void kick_drift_kernel(long long nb, double* __restrict__ p, double* __restrict__ theta,
+                                  const double* __restrict__ F, double h, double dt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double pn = p[i] + F[i] * h;
+    p[i] = pn;
+    theta[i] += (2.0 * pn) * dt;
+  }
+}
+
+cudaError_t launch_kick(long long nb, double* p, const double* F, double h, cudaStream_t s) {
+  kick_kernel<<<ew_blocks(nb, 256, 4096), 256, 0, s>>>(nb, p, F, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(long long nb, double* p, double* theta, const double* F, double h,
+                              double dt, cudaStream_t s) {
+  kick_drift_kernel<<<ew_blocks(nb, 256, 4096), 256, 0, s>>>(nb, p, theta, F, h, dt);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Hamiltonian terms: S_B(theta), sum p^2, Re <a, b>.  Per-block partials, then
+// one block sums them in a fixed order.
+__global__ void action_partials_kernel(Geo g, BosonParams bp, const double* __restrict__ theta,
+                                       const double* __restrict__ p, const double2* __restrict__ a,
+                                       const double2* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[32];
+  const long long n = (long long)g.V * g.Ntau;
+  double kin = 0.0, pot = 0.0, pp = 0.0, ab = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int tau = (int)(i / g.V);
+    const int s = (int)(i - (long long)tau * g.V);
+    const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
+    const double* th = theta + (size_t)tau * g.V * 2;
+    const double* thp = theta + (size_t)tp * g.V * 2;
+    for (int c = 0; c < 2; ++c) {
+      const double d = thp[2 * s + c] - th[2 * s + c];
+      kin += bp.noncompact ? d * d : 1.0 - cos(d);
+    }
+    if (bp.Kdtau != 0.0) pot += cos(curl_at(th, g.L, s % g.L, s / g.L));
+    if (p) {
+      const double2 pv = reinterpret_cast<const double2*>(p)[i];
+      pp += pv.x * pv.x + pv.y * pv.y;
+    }
+    if (a && b) ab += cdot_re(a[i], b[i]);
+  }
+  double t;
+  t = block_sum(kin, red);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 0] = t;
+  t = block_sum(pot, red);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 1] = t;
+  t = block_sum(pp, red);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 2] = t;
+  t = block_sum(ab, red);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 3] = t;
+}
+
+__global__ void action_finalize_kernel(BosonParams bp, const double* __restrict__ part, int nblk,
+                                       double* __restrict__ terms) {
+  double s[4];
+  for (int c = 0; c < 4; ++c) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += 32) acc += part[4 * k + c];
+    acc = warp_sum(acc);
+    s[c] = __shfl_sync(0xffffffffu, acc, 0);
+  }
+  if (threadIdx.x == 0) {
+    terms[0] = bp.cK * s[0] + bp.Kdtau * s[1];
+    terms[1] = s[2];
+    terms[2] = s[3];
+  }
+}
+
+cudaError_t launch_action_terms(const Geo& g, const BosonParams& bp, const double* theta,
+                                const double* p, const double2* a, const double2* b, int grid,
+                                double* part, double* terms, cudaStream_t s) {
+  action_partials_kernel<<<grid, 256, 0, s>>>(g, bp, theta, p, a, b, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  action_finalize_kernel<<<1, 32, 0, s>>>(bp, part, grid, terms);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011): 10 rounds of two 32x32->64 products
+// with the round constants below and a Weyl key schedule.
+struct U4 {
+  uint32_t v[4];
+};
+
+__host__ __device__ inline U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.v[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.v[2];
+    U4 o;
+    o.v[0] = (uint32_t)(p1 >> 32) ^ c.v[1] ^ k0;
+    o.v[1] = (uint32_t)p1;
+    o.v[2] = (uint32_t)(p0 >> 32) ^ c.v[3] ^ k1;
+    o.v[3] = (uint32_t)p0;
+    c = o;
+  }
+  return c;
+}
+
+__host__ __device__ inline double u53(uint32_t hi, uint32_t lo) {
+  return ((double)(hi >> 5) * 67108864.0 + (double)(lo >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+__device__ inline void gauss_pair(uint64_t seed, uint32_t stream, uint64_t counter, uint32_t elem,
+                                  double* g0, double* g1) {
+  U4 c = {{elem, stream, (uint32_t)counter, (uint32_t)(counter >> 32)}};
+  const U4 w = philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double ua = u53(w.v[0], w.v[1]);
+  const double ub = u53(w.v[2], w.v[3]);
+  const double r = sqrt(-2.0 * log(1.0 - ua));
+  double sn, cs;
+  sincos(2.0 * 3.141592653589793 * ub, &sn, &cs);
+  *g0 = r * cs;
+  *g1 = r * sn;
+}
+
+__global__ void draw_kernel(long long n, uint64_t seed, uint64_t counter, double* __restrict__ p,
+                            double2* __restrict__ R) {
+  const double h = 0.70710678118654752440;  // sqrt(1/2)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double g0, g1;
+    if (p) {
+      gauss_pair(seed, 0u, counter, (uint32_t)i, &g0, &g1);
+      reinterpret_cast<double2*>(p)[i] = make_double2(g0 * h, g1 * h);
+    }
+    if (R) {
+      gauss_pair(seed, 1u, counter, (uint32_t)i, &g0, &g1);
+      R[i] = make_double2(g0 * h, g1 * h);
+    }
+  }
+}
+
+cudaError_t launch_draw(long long n_sites, uint64_t seed, uint64_t counter, double* p, double2* R,
+                        cudaStream_t s) {
+  draw_kernel<<<ew_blocks(n_sites, 256, 4096), 256, 0, s>>>(n_sites, seed, counter, p, R);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 throughput probe: every thread runs 8 independent FMA chains, so the
+// FP64 pipe, not latency, limits the rate.  Used only to measure the FP64
+// roofline denominator of this device.
+__global__ void fp64_probe_kernel(double* out, int iters, double a, double b) {
+  double v0 = threadIdx.x * 1e-3, v1 = v0 + 1, v2 = v0 + 2, v3 = v0 + 3, v4 = v0 + 4, v5 = v0 + 5,
+         v6 = v0 + 6, v7 = v0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    v0 = fma(v0, a, b); v1 = fma(v1, a, b); v2 = fma(v2, a, b); v3 = fma(v3, a, b);
+    v4 = fma(v4, a, b); v5 = fma(v5, a, b); v6 = fma(v6, a, b); v7 = fma(v7, a, b);
+  }
+  const double s = ((v0 + v1) + (v2 + v3)) + ((v4 + v5) + (v6 + v7));
+  if (s == 123.456) out[0] = s;  // keeps the chains live
+}
+
+cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s) {
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+  return cudaGetLastError();
+}
+
+void philox_uniform_host(uint64_t seed, uint64_t counter, double* u) {
+  U4 c = {{0u, 2u, (uint32_t)counter, (uint32_t)(counter >> 32)}};
+  const U4 w = philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  *u = u53(w.v[0], w.v[1]);
+}
+
+}  // namespace hqmc

@@ -1,0 +1,306 @@
+"""ctypes binding of libhqmc (include/hqmc.h) for torch CUDA tensors.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current stream.  Importing this module
+loads ``libhqmc.so`` and raises ImportError if it has not been built; there is
+no CPU fallback.
+
+Shapes and dtypes (all CUDA, contiguous):
+  theta, p, F : float64 (Ntau, L, L, 2)
+  vectors     : complex128 (Ntau, L, L); complex64 selects the FP32 operators.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhqmc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2508_16298_gb300.build.build() "
+                      "(needs the CUDA toolkit); there is no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
+FP64, FP32 = 0, 1
+ACTION_COMPACT, ACTION_NONCOMPACT = 0, 1
+SOLVER_CG64, SOLVER_MIXED = 0, 1
+TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE = 0, 1, 2
+
+# Every function declared in include/hqmc.h.
+EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_error", "hqmc_num_sites",
+           "hqmc_launch_count",
+           "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_cg_solve", "hqmc_force", "hqmc_action_terms",
+           "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
+           "hqmc_probe_fp64_rate")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("Ntau", ctypes.c_int), ("dtau", ctypes.c_double),
+                ("t", ctypes.c_double), ("J", ctypes.c_double), ("K", ctypes.c_double),
+                ("action", ctypes.c_int), ("reliable_interval", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("true_residual", ctypes.c_double),
+                ("recursive_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrajInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("accepted", ctypes.c_int), ("cg_solves", ctypes.c_int),
+                ("cg_iterations", ctypes.c_int), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("dH", ctypes.c_double), ("u", ctypes.c_double), ("max_true_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp, _i, _d, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+_sig = {
+    "hqmc_make_config": ([ctypes.POINTER(Params), ctypes.POINTER(_vp)], _i),
+    "hqmc_free_config": ([_vp], _i),
+    "hqmc_strerror": ([_i], ctypes.c_char_p),
+    "hqmc_last_error": ([_vp], ctypes.c_char_p),
+    "hqmc_num_sites": ([_vp], ctypes.c_longlong),
+    "hqmc_launch_count": ([_vp], ctypes.c_longlong),
+    "hqmc_apply_M": ([_vp, _vp, _vp, _vp, _i, _i, _vp], _i),
+    "hqmc_apply_MdagM": ([_vp, _vp, _vp, _vp, _i, _vp], _i),
+    "hqmc_cg_solve": ([_vp, _vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
+    "hqmc_force": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "hqmc_action_terms": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
+    "hqmc_draw": ([_vp, _u64, _u64, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
+    "hqmc_leapfrog": ([_vp, _vp, _vp, _vp, _vp, _i, _d, _d, _i, _i, ctypes.POINTER(TrajInfo), _vp], _i),
+    "hqmc_trajectory": ([_vp, _vp, _u64, _u64, _vp, _vp, ctypes.POINTER(ctypes.c_double), _i, _d, _d, _i, _i,
+                         ctypes.POINTER(TrajInfo), _vp], _i),
+    "hqmc_set_timing": ([_vp, _i], _i),
+    "hqmc_get_timing": ([_vp, _i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _i),
+    "hqmc_probe_fp64_rate": ([_vp, ctypes.POINTER(ctypes.c_double)], _i),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class HQMCError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        msg = _lib.hqmc_strerror(status).decode()
+        super().__init__(f"{msg} ({status})" + (f": {detail}" if detail else ""))
+
+
+def strerror(status: int) -> str:
+    return _lib.hqmc_strerror(status).decode()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Config:
+    """Owns an hqmc_config: lattice, model parameters, launch shapes and workspace."""
+
+    def __init__(self, L: int, Ntau: int, dtau: float = 0.1, t: float = 1.0, J: float = 1.0,
+                 K: float = 0.0, noncompact: bool = False, reliable_interval: int = 50):
+        self.params = Params(L, Ntau, dtau, t, J, K, ACTION_NONCOMPACT if noncompact else ACTION_COMPACT,
+                             reliable_interval)
+        h = _vp()
+        rc = _lib.hqmc_make_config(ctypes.byref(self.params), ctypes.byref(h))
+        if rc != OK:
+            raise HQMCError(rc, f"L={L} Ntau={Ntau}")
+        self._h = h
+        self.L, self.Ntau = L, Ntau
+        self.n_sites = int(_lib.hqmc_num_sites(h))
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("config already freed")
+        return self._h
+
+    def launch_count(self) -> int:
+        """Kernels this config has enqueued so far."""
+        return int(_lib.hqmc_launch_count(self.handle))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.hqmc_free_config(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def check(self, rc: int, allow=(OK,)):
+        if rc not in allow:
+            raise HQMCError(rc, (_lib.hqmc_last_error(self._h) or b"").decode())
+        return rc
+
+    # -- argument checks ---------------------------------------------------
+    def _bonds(self, a, name):
+        if a is None:
+            return None
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                and tuple(a.shape) == (self.Ntau, self.L, self.L, 2)):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape "
+                             f"({self.Ntau}, {self.L}, {self.L}, 2)")
+        return a
+
+    def _vec(self, a, name, dtypes=(torch.complex128,)):
+        if a is None:
+            return None
+        if not (a.is_cuda and a.dtype in dtypes and a.is_contiguous()
+                and tuple(a.shape) == (self.Ntau, self.L, self.L)):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {dtypes} and shape "
+                             f"({self.Ntau}, {self.L}, {self.L})")
+        return a
+
+    def empty_vec(self, dtype=torch.complex128):
+        return torch.empty((self.Ntau, self.L, self.L), dtype=dtype, device="cuda")
+
+    def empty_bonds(self):
+        return torch.empty((self.Ntau, self.L, self.L, 2), dtype=torch.float64, device="cuda")
+
+
+def make_config(L: int, Ntau: int, **kw) -> Config:
+    return Config(L, Ntau, **kw)
+
+
+def _prec(x) -> int:
+    return FP32 if x.dtype == torch.complex64 else FP64
+
+
+def apply_M(cfg: Config, theta, x, y=None, dagger: bool = False):
+    """y = M x (or M^dagger x); complex64 x selects the FP32 kernel."""
+    cfg._bonds(theta, "theta")
+    cfg._vec(x, "x", (torch.complex128, torch.complex64))
+    y = torch.empty_like(x) if y is None else cfg._vec(y, "y", (x.dtype,))
+    cfg.check(_lib.hqmc_apply_M(cfg.handle, _ptr(theta), _ptr(x), _ptr(y), int(dagger), _prec(x), _stream()))
+    return y
+
+
+def apply_MdagM(cfg: Config, theta, x, y=None):
+    """y = (M^dagger M) x with the fused kernel; complex64 x selects FP32."""
+    cfg._bonds(theta, "theta")
+    cfg._vec(x, "x", (torch.complex128, torch.complex64))
+    y = torch.empty_like(x) if y is None else cfg._vec(y, "y", (x.dtype,))
+    cfg.check(_lib.hqmc_apply_MdagM(cfg.handle, _ptr(theta), _ptr(x), _ptr(y), _prec(x), _stream()))
+    return y
+
+
+def _solver(s) -> int:
+    if isinstance(s, str):
+        return {"cg64": SOLVER_CG64, "mixed": SOLVER_MIXED}[s]
+    return int(s)
+
+
+def cg_solve(cfg: Config, theta, phi, x=None, tol: float = 1e-8, maxit: int = 100000, solver="cg64",
+             raise_on_fail: bool = True):
+    """Solve (M^dagger M) x = phi.  Returns (x, info dict).  x (if given) is the initial guess."""
+    cfg._bonds(theta, "theta")
+    cfg._vec(phi, "phi")
+    x = torch.zeros_like(phi) if x is None else cfg._vec(x, "x")
+    info = SolveInfo()
+    rc = _lib.hqmc_cg_solve(cfg.handle, _ptr(theta), _ptr(phi), _ptr(x), tol, maxit, _solver(solver),
+                            ctypes.byref(info), _stream())
+    if raise_on_fail:
+        cfg.check(rc)
+    return x, info.as_dict()
+
+
+def force(cfg: Config, theta, X, F=None, dSf=None):
+    """Total force F = -dS_B/dtheta - dS_f/dtheta given X = (M^dagger M)^{-1} phi."""
+    cfg._bonds(theta, "theta")
+    cfg._vec(X, "X")
+    F = cfg.empty_bonds() if F is None else cfg._bonds(F, "F")
+    cfg._bonds(dSf, "dSf")
+    cfg.check(_lib.hqmc_force(cfg.handle, _ptr(theta), _ptr(X), _ptr(F), _ptr(dSf), _stream()))
+    return F
+
+
+def action_terms(cfg: Config, theta, p=None, phi=None, X=None):
+    """(S_B, sum p^2, Re phi^dagger X) of Eq. (H_hmc)."""
+    cfg._bonds(theta, "theta")
+    cfg._bonds(p, "p")
+    cfg._vec(phi, "phi")
+    cfg._vec(X, "X")
+    out = (ctypes.c_double * 3)()
+    cfg.check(_lib.hqmc_action_terms(cfg.handle, _ptr(theta), _ptr(p), _ptr(phi), _ptr(X), out, _stream()))
+    return out[0], out[1], out[2]
+
+
+def draw(cfg: Config, seed: int, traj_counter: int, p=None, R=None, want_p: bool = True, want_R: bool = True):
+    """Philox draws of HQMC step (i): p ~ N(0, 1/2) per bond, R ~ CN(0, 1) per site, and u."""
+    if want_p and p is None:
+        p = cfg.empty_bonds()
+    if want_R and R is None:
+        R = cfg.empty_vec()
+    cfg._bonds(p, "p")
+    cfg._vec(R, "R")
+    u = ctypes.c_double()
+    cfg.check(_lib.hqmc_draw(cfg.handle, seed, traj_counter, _ptr(p), _ptr(R), ctypes.byref(u), _stream()))
+    return p, R, u.value
+
+
+def leapfrog(cfg: Config, theta, p, phi, X, nsteps: int, dt: float, tol: float = 1e-8, maxit: int = 100000,
+             solver="cg64"):
+    """nsteps leapfrog steps on (theta, p) in place; X is the CG guess in and the solution out."""
+    cfg._bonds(theta, "theta")
+    cfg._bonds(p, "p")
+    cfg._vec(phi, "phi")
+    cfg._vec(X, "X")
+    info = TrajInfo()
+    cfg.check(_lib.hqmc_leapfrog(cfg.handle, _ptr(theta), _ptr(p), _ptr(phi), _ptr(X), nsteps, dt, tol, maxit,
+                                 _solver(solver), ctypes.byref(info), _stream()), allow=(OK, ENOTCONV))
+    return info.as_dict()
+
+
+def trajectory(cfg: Config, theta, seed: int = 0, traj_counter: int = 0, p_in=None, R_in=None, u_in=None,
+               nsteps: int = 10, dt: float = 0.05, tol: float = 1e-8, maxit: int = 100000, solver="cg64"):
+    """One HQMC update of theta (in place).  Returns the trajectory info dict."""
+    cfg._bonds(theta, "theta")
+    cfg._bonds(p_in, "p_in")
+    cfg._vec(R_in, "R_in")
+    info = TrajInfo()
+    u = None if u_in is None else ctypes.byref(ctypes.c_double(u_in))
+    cfg.check(_lib.hqmc_trajectory(cfg.handle, _ptr(theta), seed, traj_counter, _ptr(p_in), _ptr(R_in), u,
+                                   nsteps, dt, tol, maxit, _solver(solver), ctypes.byref(info), _stream()),
+              allow=(OK, ENOTCONV))
+    return info.as_dict()
+
+
+def set_timing(cfg: Config, enable: bool):
+    cfg.check(_lib.hqmc_set_timing(cfg.handle, int(enable)))
+
+
+def get_timing(cfg: Config, timer: int):
+    """(launches, total milliseconds) of one kernel class since set_timing."""
+    n, ms = ctypes.c_longlong(), ctypes.c_double()
+    cfg.check(_lib.hqmc_get_timing(cfg.handle, timer, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def probe_fp64_rate(cfg: Config) -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s."""
+    out = ctypes.c_double()
+    cfg.check(_lib.hqmc_probe_fp64_rate(cfg.handle, ctypes.byref(out)))
+    return out.value
