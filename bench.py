@@ -5,8 +5,11 @@ N_lf + 1 CG solves of (M^dagger M) X = phi, forces, leapfrog, Metropolis) on a
 seeded synthetic gauge field; the chain continues from step to step.
 
 Default workload (plain FP64 GPU HMC): L = 24, Ntau = 240 (138,240 sites),
-dtau = 0.1, t = 1, J = 1, compact action, hot start theta ~ U[-pi, pi), CG to a
-true FP64 residual of 1e-8, 20 leapfrog steps of dt = 0.01.
+dtau = 0.1, t = 1, J = 1, compact action, CG to a true FP64 residual of 1e-8,
+20 leapfrog steps of dt = 0.01.  Start: every bond a uniform angle plus a
+periodic Gaussian walk in tau (inputs.theta_warm), i.e. smooth in imaginary time
+like an equilibrated field; a start i.i.d. in tau makes M^dagger M so singular
+that FP64 CG needs > 6e4 iterations per solve at this size.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
@@ -34,13 +37,13 @@ METRIC = "M†M apply GB/s vs HBM peak; HMC traj/s learned+FP32 vs plain FP64 at
 WORKLOADS = {
     # plain FP64 HMC at L = 24, Ntau = 240
     "hmc_fp64_L24_Nt240": dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.01, tol=1e-8,
-                               solver="cg64", seed=1),
+                               solver="cg64", seed=1, start="warm"),
     # plain FP64 HMC at L = 8, Ntau = 40 (oracle-sized)
     "hmc_fp64_L8_Nt40": dict(L=8, Ntau=40, dtau=0.1, t=1.0, J=1.0, nsteps=10, dt=0.02, tol=1e-10,
-                             solver="cg64", seed=1),
+                             solver="cg64", seed=1, start="hot"),
     # mixed precision at L = 48, Ntau = 480
     "hmc_mixed_L48_Nt480": dict(L=48, Ntau=480, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.01, tol=1e-8,
-                                solver="mixed", seed=1),
+                                solver="mixed", seed=1, start="warm"),
 }
 DEFAULT_WORKLOAD = "hmc_fp64_L24_Nt240"
 
@@ -150,7 +153,7 @@ def run_reference(args, wl_name, wl, rank, world):
     from paper_2508_16298_gb300 import inputs
 
     lat = oracle.Lattice(wl["L"], wl["Ntau"], dtau=wl["dtau"], t=wl["t"], J=wl["J"])
-    theta = inputs.theta_hot(wl["L"], wl["Ntau"], wl["seed"])
+    theta = start_theta(wl, wl["seed"])
     R = inputs.complex_gaussian(wl["L"], wl["Ntau"], wl["seed"] + 1)
     phi = oracle.apply_M(lat, theta, R, dagger=True)
     its = ITS_PER_TRAJ_HINT[wl_name]
@@ -169,9 +172,18 @@ def run_reference(args, wl_name, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def start_theta(wl, seed):
+    from paper_2508_16298_gb300 import inputs
+    if wl["start"] == "hot":
+        return inputs.theta_hot(wl["L"], wl["Ntau"], seed)
+    return inputs.theta_warm(wl["L"], wl["Ntau"], seed, J=wl["J"], dtau=wl["dtau"])
+
+
 def config_of(wl_name, wl):
     return {"workload": wl_name, "L": wl["L"], "Ntau": wl["Ntau"], "sites": wl["L"] * wl["L"] * wl["Ntau"],
-            "dtau": wl["dtau"], "t": wl["t"], "J": wl["J"], "action": "compact", "start": "hot (theta ~ U[-pi, pi))",
+            "dtau": wl["dtau"], "t": wl["t"], "J": wl["J"], "action": "compact",
+            "start": ("hot: theta i.i.d. U[-pi, pi)" if wl["start"] == "hot" else
+                      "warm: U[-pi, pi) per bond + periodic Gaussian walk in tau, step var J*dtau/2"),
             "n_leapfrog": wl["nsteps"], "dt": wl["dt"], "cg_tol": wl["tol"], "solver": wl["solver"],
             "l2": "flushed between timed steps (512 MiB write; step times exclude the flush)"}
 
@@ -189,7 +201,7 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     L, N = wl["L"], wl["Ntau"]
     cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"])
     seed = wl["seed"] + 1000 * rank
-    theta = torch.from_numpy(inputs.theta_hot(L, N, seed)).to(dev)
+    theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver=wl["solver"])
 
@@ -271,7 +283,7 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     # ---- oracle on the host cores: bounded sample --------------------------
     import oracle
     lat = oracle.Lattice(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"])
-    th_np = inputs.theta_hot(L, N, wl["seed"])
+    th_np = start_theta(wl, wl["seed"])
     phi_np = oracle.apply_M(lat, th_np, inputs.complex_gaussian(L, N, wl["seed"] + 1), dagger=True)
     cb = oracle_sample(wl, its_per_traj, th_np, phi_np)
 
@@ -296,6 +308,26 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(wl):
+    """A short, fixed sequence for ncu captures: three fused M^dagger M applies and
+    a 40-iteration CG solve at the workload's size (no JSON output)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_16298_gb300 import hqmc, inputs
+
+    L, N = wl["L"], wl["Ntau"]
+    with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"]) as cfg:
+        theta = torch.from_numpy(start_theta(wl, wl["seed"])).cuda()
+        x = torch.from_numpy(inputs.complex_gaussian(L, N, 2)).cuda()
+        for _ in range(3):
+            hqmc.apply_MdagM(cfg, theta, x)
+        hqmc.cg_solve(cfg, theta, x, tol=1e-30, maxit=40, solver=wl["solver"], raise_on_fail=False)
+        torch.cuda.synchronize()
+    print("profile case done", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,7 +335,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--profile", action="store_true", help="run the short ncu capture case and exit")
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(WORKLOADS[args.workload])
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

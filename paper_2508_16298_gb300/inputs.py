@@ -46,3 +46,19 @@ def momenta(L: int, Ntau: int, seed: int) -> np.ndarray:
 
 def uniform01(seed: int) -> float:
     return float(rng(seed).uniform(0.0, 1.0))
+
+
+def theta_warm(L: int, Ntau: int, seed: int, J: float = 1.0, dtau: float = 0.1) -> np.ndarray:
+    """Gauge field smooth in imaginary time, shaped like an equilibrated configuration.
+
+    Every bond gets a uniform angle u ~ U[-pi, pi) plus a periodic Gaussian walk
+    in tau: increments d_tau ~ N(0, J*dtau/2) with their mean removed (so the
+    walk closes on itself), which is the distribution of the temporal term
+    (1/(J dtau)) (theta_{tau+1} - theta_tau)^2 of the bosonic action on its own.
+    """
+    g = rng(seed)
+    u = g.uniform(-np.pi, np.pi, size=(1, L, L, 2))
+    d = g.standard_normal(size=(Ntau, L, L, 2)) * np.sqrt(0.5 * J * dtau)
+    d -= d.mean(axis=0, keepdims=True)
+    w = np.cumsum(d, axis=0) - d[0]
+    return u + w
