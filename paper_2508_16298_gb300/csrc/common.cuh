@@ -172,10 +172,24 @@ struct CgState {
   int k2;            // copy of k for the update kernel
   int seg_start;     // first iteration of the current recurrence segment
   int maxit;
-  int done;          // 0 running; 1 recursive residual below tol; 2 maxit; 3 breakdown; 4 non-finite
-  int pad[3];
+  int done;          // CG_* below
+  int loops;         // loop bodies executed in this solve
+  int loop_cap;      // hard bound on loop bodies (termination guard of the device-side loop)
+  int pad;
 };
 
-enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4 };
+// CG_REC_CONVERGED: the recursive residual met tol; the true residual still has
+// to be checked.  CG_CONVERGED: the true FP64 residual met tol.
+enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4, CG_REC_CONVERGED = 5 };
+
+// Gates of the kernels that close a loop body: run always, only after the
+// recursive residual converged, or whenever the solve is still active.
+enum { GATE_ALWAYS = 0, GATE_REC = 1, GATE_ACTIVE = 2 };
+
+__device__ __forceinline__ bool gate_open(int gate, int done) {
+  if (gate == GATE_ALWAYS) return true;
+  if (gate == GATE_REC) return done == CG_REC_CONVERGED;
+  return done == CG_RUNNING || done == CG_REC_CONVERGED;
+}
 
 }  // namespace hqmc

@@ -17,12 +17,23 @@ using namespace hqmc;
 namespace {
 
 constexpr int kMaxL = 68;             // 3 complex-double slices must fit in 227 KB of shared memory
-constexpr int kChunk = 32;            // CG iterations enqueued between host checks
-constexpr int kDefaultReliable = 50;  // mixed solver residual-update period
+constexpr int kBodyIters64 = 16;      // FP64 CG iterations per loop body
+constexpr int kDefaultReliable = 50;  // mixed solver residual-update period (iterations per body)
+constexpr int kMaxBreakdowns = 8;     // mixed solver: FP32 breakdown restarts before the FP64 fallback
+constexpr size_t kMaxGraphs = 8;      // cached solve graphs per config
 
 struct TimerClass {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
   size_t used = 0;
+};
+
+// An instantiated CG loop (WHILE node around one loop body) for fixed operands.
+struct SolveGraph {
+  const void* phi;
+  void* x;
+  int solver;
+  int body_kernels;  // kernels per body, including the loop-condition kernel
+  cudaGraphExec_t exec;
 };
 
 }  // namespace
@@ -57,6 +68,10 @@ struct hqmc_config {
 
   int timing = 0;
   long long launches = 0;  // kernels enqueued by this config
+  int capturing = 0;       // inside a stream capture: launches are counted when the graph runs
+  int graphs_ok = 1;       // cleared if this device cannot build the device-side CG loop
+  cudaStream_t cap = nullptr;
+  std::vector<SolveGraph> graphs;
   TimerClass timers[HQMC_TIMER_COUNT];
   std::vector<void*> allocs;
   char err[512] = {0};
@@ -90,10 +105,10 @@ int fail(hqmc_config* cfg, int code, const char* fmt, ...) {
 
 // Kernel launches are made through LK so that the config can report how many
 // of its kernels it enqueued (launch_action_terms enqueues two).
-#define LK(n, call)           \
-  do {                        \
-    cfg->launches += (n);     \
-    CK(call);                 \
+#define LK(n, call)                          \
+  do {                                       \
+    if (!cfg->capturing) cfg->launches += (n); \
+    CK(call);                                \
   } while (0)
 
 bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
@@ -129,12 +144,16 @@ void release(hqmc_config* cfg) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
     }
+  for (auto& g : cfg->graphs) cudaGraphExecDestroy(g.exec);
+  cfg->graphs.clear();
+  if (cfg->cap) cudaStreamDestroy(cfg->cap);
+  cfg->cap = nullptr;
 }
 
 // Event timing around launches of one kernel class.
 int timer_begin(hqmc_config* cfg, int cls, cudaStream_t s, int* slot) {
   *slot = -1;
-  if (!cfg->timing) return HQMC_OK;
+  if (!cfg->timing || cfg->capturing) return HQMC_OK;
   TimerClass& tc = cfg->timers[cls];
   if (tc.used == tc.pairs.size()) {
     cudaEvent_t a, b;
@@ -176,7 +195,7 @@ MdagmArgs<R> mdagm_args(hqmc_config* cfg) {
 
 // r_out = b - O x (FP64) with partials; then the state bookkeeping.
 int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, bool r_fp32, int fin_mode,
-             double tol, int maxit, cudaStream_t s) {
+             double tol, int maxit, int gate, cudaStream_t s) {
   MdagmArgs<double> a = mdagm_args<double, MODE_RESID>(cfg);
   a.U = cfg->U64;
   a.x = x;
@@ -184,12 +203,14 @@ int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, 
   a.r_out = r_out;
   a.r_out_fp32 = r_fp32 ? 1 : 0;
   a.part_out = cfg->part_resid;
+  a.st = cfg->st;
+  a.gate = gate;
   int slot;
   RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
   LK(1, (launch_mdagm<double, MODE_RESID>(cfg->sl, a, s)));
   RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
   LK(1, launch_resid_finalize(cfg->part_resid, cfg->sl.grid, fin_mode, tol, maxit, cfg->part_ew, cfg->ew_grid,
-                           cfg->st, cfg->report, s));
+                           cfg->st, cfg->report, gate, s));
   return HQMC_OK;
 }
 
@@ -224,56 +245,153 @@ int read_state(hqmc_config* cfg, cudaStream_t s) {
   return HQMC_OK;
 }
 
+// One body of the CG loop: a block of iterations followed by the residual
+// check that closes it.  FP64: kBodyIters64 iterations, then (only if the
+// recursive residual converged) the true residual and a restart if needed.
+// Mixed: reliable_interval FP32 iterations, then the FP64 reliable update
+// x += xh, r = phi - O x (whenever the solve is still active).
+int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, cudaStream_t s, int* nkernels) {
+  const bool mixed = solver == HQMC_SOLVER_MIXED;
+  const int iters = mixed ? cfg->reliable : kBodyIters64;
+  for (int c = 0; c < iters; ++c) {
+    if (mixed)
+      RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, s));
+    else
+      RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, s));
+  }
+  if (mixed) {
+    LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, cfg->st, GATE_ACTIVE, s));
+    RET(residual(cfg, phi, x, cfg->r32, true, FIN_RELIABLE, 0.0, 0, GATE_ACTIVE, s));
+  } else {
+    RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, 0.0, 0, GATE_REC, s));
+  }
+  *nkernels = 2 * iters + (mixed ? 3 : 2);
+  return HQMC_OK;
+}
+
+// Builds (or finds) the graph that runs loop bodies under a WHILE node until
+// the CG state leaves RUNNING: the loop condition is decided on the device.
+int get_graph(hqmc_config* cfg, int solver, const double2* phi, double2* x, SolveGraph** out) {
+  for (auto& g : cfg->graphs)
+    if (g.phi == phi && g.x == x && g.solver == solver) {
+      *out = &g;
+      return HQMC_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(cfg, HQMC_ECUDA, "conditional graph node: %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(cfg->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cfg->capturing = 1;
+  int nk = 0;
+  int rc = enqueue_body(cfg, solver, phi, x, cfg->cap, &nk);
+  if (rc == HQMC_OK) {
+    cudaError_t le = launch_loop_condition(cfg->st, handle, cfg->cap);
+    if (le != cudaSuccess) rc = fail(cfg, HQMC_ECUDA, "loop condition launch: %s", cudaGetErrorString(le));
+  }
+  cfg->capturing = 0;
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cfg->cap, &captured);
+  if (rc == HQMC_OK && e != cudaSuccess) rc = fail(cfg, HQMC_ECUDA, "end capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  if (rc == HQMC_OK) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) rc = fail(cfg, HQMC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(graph);
+  if (rc != HQMC_OK) {
+    cudaGetLastError();
+    return rc;
+  }
+  if (cfg->graphs.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(cfg->graphs.front().exec);
+    cfg->graphs.erase(cfg->graphs.begin());
+  }
+  cfg->graphs.push_back(SolveGraph{phi, x, solver, nk + 1, exec});
+  *out = &cfg->graphs.back();
+  return HQMC_OK;
+}
+
+// Runs loop bodies until the state leaves RUNNING / REC_CONVERGED; the state
+// is in cfg->st_h on return.  Uses the device-side loop unless event timing is
+// on (per-launch events cannot sit inside a conditional body).
+int run_loop(hqmc_config* cfg, int solver, const double2* phi, double2* x, int* loops_seen, cudaStream_t s) {
+  if (!cfg->timing && cfg->graphs_ok) {
+    SolveGraph* gr = nullptr;
+    if (get_graph(cfg, solver, phi, x, &gr) == HQMC_OK) {
+      CK(cudaGraphLaunch(gr->exec, s));
+      RET(read_state(cfg, s));
+      const int loops = cfg->st_h->loops;
+      cfg->launches += (long long)(loops - *loops_seen) * gr->body_kernels;
+      *loops_seen = loops;
+      return HQMC_OK;
+    }
+    cfg->graphs_ok = 0;  // fall back to host-driven bodies from now on
+  }
+  for (;;) {
+    RET(read_state(cfg, s));
+    const int d = cfg->st_h->done;
+    if (d != CG_RUNNING && d != CG_REC_CONVERGED) return HQMC_OK;
+    int nk = 0;
+    RET(enqueue_body(cfg, solver, phi, x, s, &nk));
+  }
+}
+
 // CG on (M^dagger M) x = phi with the link tables already built for theta.
 int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
           hqmc_solve_info* info, cudaStream_t s) {
   const bool mixed = solver == HQMC_SOLVER_MIXED;
   hqmc_solve_info inf{};
-  RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, s));
+  RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, GATE_ALWAYS, s));
   if (mixed) CK(cudaMemsetAsync(cfg->xh32, 0, sizeof(float2) * cfg->n, s));
-  bool after_resid = true;
-  int status = HQMC_OK;
+  int cur = solver, loops_seen = 0, status = HQMC_OK;
   for (;;) {
-    RET(read_state(cfg, s));
+    RET(run_loop(cfg, cur, phi, x, &loops_seen, s));
     const CgState& st = *cfg->st_h;
     if (st.bb == 0.0) {  // phi = 0: the solution is zero whatever the guess
       CK(cudaMemsetAsync(x, 0, sizeof(double2) * cfg->n, s));
       cfg->report_h[0] = 0.0;
       break;
     }
-    if (st.done == CG_RUNNING && !(mixed && !after_resid)) {
-      const int chunk = mixed ? cfg->reliable : kChunk;
-      for (int c = 0; c < chunk; ++c) {
-        if (mixed)
-          RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, s));
-        else
-          RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, s));
-      }
-      after_resid = false;
-      continue;
-    }
-    if ((st.done == CG_CONVERGED || st.done == CG_RUNNING) && after_resid) break;  // true residual below tol
-    if (st.done == CG_CONVERGED || st.done == CG_RUNNING) {
-      if (mixed) {
-        LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, s));
-        RET(residual(cfg, phi, x, cfg->r32, true, FIN_RELIABLE, tol, maxit, s));
-        inf.reliable_updates++;
+    if (st.done == CG_CONVERGED) break;
+    if (st.done == CG_BREAKDOWN && cur == HQMC_SOLVER_MIXED) {
+      // <p, O32 p> <= 0: the FP32 operator cannot resolve the lowest modes of
+      // this field.  Fold in the correction, restart from the FP64 residual,
+      // and after repeated breakdowns finish the solve in FP64.
+      inf.restarts++;
+      LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
+      if (inf.restarts > kMaxBreakdowns) {
+        cur = HQMC_SOLVER_CG64;
+        inf.fp64_fallback = 1;
+        RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, tol, maxit, GATE_ALWAYS, s));
       } else {
-        RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, tol, maxit, s));
-        inf.restarts++;
+        RET(residual(cfg, phi, x, cfg->r32, true, FIN_RESTART, tol, maxit, GATE_ALWAYS, s));
       }
-      after_resid = true;
       continue;
     }
-    // MAXIT, BREAKDOWN or NONFINITE: report the true residual of the last iterate
+    // MAXIT, NONFINITE, or a breakdown of the FP64 recurrence: report the true residual of x
     status = st.done == CG_MAXIT ? HQMC_ENOTCONV : st.done == CG_BREAKDOWN ? HQMC_EBREAKDOWN : HQMC_ENONFINITE;
-    if (mixed) LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, s));
-    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, s));
+    if (cur == HQMC_SOLVER_MIXED) LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
+    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
     RET(read_state(cfg, s));
     break;
   }
   const CgState& st = *cfg->st_h;
-  if (!mixed && inf.restarts > 0 && status == HQMC_OK) inf.restarts--;  // the final check is not a restart
+  inf.reliable_updates = mixed ? st.loops : 0;
   inf.status = status;
   inf.iterations = st.k;
   inf.true_residual = st.bb > 0 ? std::sqrt(cfg->report_h[0] / st.bb) : 0.0;
@@ -464,6 +582,10 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
         cudaMallocHost(&cfg->terms_h, 8 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&cfg->report_h, 2 * sizeof(double)) != cudaSuccess) {
       rc = fail(cfg, HQMC_ENOMEM, "pinned host allocation failed");
+      break;
+    }
+    if (cudaStreamCreateWithFlags(&cfg->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(cfg, HQMC_ECUDA, "stream creation failed");
       break;
     }
     cudaMemset(cfg->st, 0, sizeof(CgState));

@@ -35,6 +35,7 @@ struct MdagmArgs {
   int n_part_in;
   double* part_out;        // per-CTA partials: CGDIR <p, Op>; RESID <r,r> then <b,b>
   CgState* st;
+  int gate;                // RESID: GATE_* condition on st->done (GATE_ALWAYS needs no st)
 };
 
 // Fused M^dagger M (three modes).
@@ -68,10 +69,15 @@ enum { FIN_START = 0, FIN_RESTART = 1, FIN_RELIABLE = 2, FIN_REPORT = 3 };
 // Sums the RESID partials into the CG state.
 cudaError_t launch_resid_finalize(const double* part, int n, int mode, double tol, int maxit,
                                   double* part_rr_out, int n_rr_out, CgState* st, double* report,
-                                  cudaStream_t s);
+                                  int gate, cudaStream_t s);
 
-// x64 += xh32; xh32 = 0.
-cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, cudaStream_t s);
+// x64 += xh32; xh32 = 0 (gated on st->done unless st is NULL).
+cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, const CgState* st, int gate,
+                                         cudaStream_t s);
+
+// Ends a device-side CG loop body: counts it and sets the WHILE condition to
+// "still running", forcing CG_MAXIT once loop_cap bodies have run.
+cudaError_t launch_loop_condition(CgState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 
 // Fermion force dS_f/dtheta given X (FP64).
 cudaError_t launch_force(const SliceLaunch& sl, double cB, const double2* U, const double2* X,

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(1024, 1) mdagm_kernel(const MdagmArgs<R> a) {
           new_done = CG_NONFINITE;
         } else if (rr <= st->tol2bb) {
           flags = 1;
-          new_done = CG_CONVERGED;
+          new_done = CG_REC_CONVERGED;
         } else {
           beta = rr / st->rr[(k - 1) & 1];
         }
@@ -103,6 +103,12 @@ __global__ void __launch_bounds__(1024, 1) mdagm_kernel(const MdagmArgs<R> a) {
     }
     __syncthreads();
     if (s_flags & 1) return;  // uniform over the whole grid: no cluster barrier is pending
+  }
+  if (MODE == MODE_RESID && a.gate != GATE_ALWAYS) {
+    // this launch writes no CG state, so every CTA reads the same st->done
+    if (threadIdx.x == 0) s_flags = gate_open(a.gate, *(volatile int*)&a.st->done) ? 0 : 1;
+    __syncthreads();
+    if (s_flags & 1) return;
   }
   const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);
   const R beta = (MODE == MODE_CGDIR) ? s_beta : R(0);

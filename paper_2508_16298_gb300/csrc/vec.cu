@@ -138,7 +138,11 @@ template cudaError_t launch_cg_update<float>(long long, int, void*, int, float2*
 //  REPORT:   only report ||r||/||b|| (final check after maxit).
 __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, int mode, double tol,
                                       int maxit, double* __restrict__ part_rr_out, int n_rr_out,
-                                      CgState* st, double* report) {
+                                      CgState* st, double* report, int gate) {
+  __shared__ int s_open;
+  if (threadIdx.x == 0) s_open = gate_open(gate, *(volatile int*)&st->done);
+  __syncthreads();
+  if (!s_open) return;
   const double rr = warp_sum_partials(part, n);
   const double bb = warp_sum_partials(part + n, n);
   if (mode == FIN_RELIABLE)
@@ -159,6 +163,8 @@ __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, in
     st->rr[1] = rr;
     st->pq_last = 0.0;
     st->alpha_last = 0.0;
+    st->loops = 0;
+    st->loop_cap = (maxit > (1 << 29) ? (1 << 30) : 2 * maxit) + 64;
     if (!isfinite(rr) || !isfinite(bb)) st->done = CG_NONFINITE;
     else if (bb == 0.0 || rr <= st->tol2bb) st->done = CG_CONVERGED;
     else if (maxit <= 0) st->done = CG_MAXIT;
@@ -180,12 +186,31 @@ __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, in
 
 cudaError_t launch_resid_finalize(const double* part, int n, int mode, double tol, int maxit,
                                   double* part_rr_out, int n_rr_out, CgState* st, double* report,
-                                  cudaStream_t s) {
-  resid_finalize_kernel<<<1, 256, 0, s>>>(part, n, mode, tol, maxit, part_rr_out, n_rr_out, st, report);
+                                  int gate, cudaStream_t s) {
+  resid_finalize_kernel<<<1, 256, 0, s>>>(part, n, mode, tol, maxit, part_rr_out, n_rr_out, st, report, gate);
   return cudaGetLastError();
 }
 
-__global__ void accumulate_correction_kernel(long long n, double2* __restrict__ x, float2* __restrict__ xh) {
+__global__ void loop_condition_kernel(CgState* st, cudaGraphConditionalHandle h) {
+  int d = st->done;
+  const int loops = st->loops + 1;
+  st->loops = loops;
+  bool cont = d == CG_RUNNING || d == CG_REC_CONVERGED;
+  if (cont && loops >= st->loop_cap) {
+    st->done = CG_MAXIT;
+    cont = false;
+  }
+  cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+cudaError_t launch_loop_condition(CgState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  loop_condition_kernel<<<1, 1, 0, s>>>(st, h);
+  return cudaGetLastError();
+}
+
+__global__ void accumulate_correction_kernel(long long n, double2* __restrict__ x, float2* __restrict__ xh,
+                                             const CgState* st, int gate) {
+  if (st && !gate_open(gate, *(volatile const int*)&st->done)) return;  // st is not written here
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const float2 d = xh[i];
@@ -195,8 +220,9 @@ __global__ void accumulate_correction_kernel(long long n, double2* __restrict__ 
   }
 }
 
-cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, cudaStream_t s) {
-  accumulate_correction_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, x, xh);
+cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, const CgState* st, int gate,
+                                         cudaStream_t s) {
+  accumulate_correction_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, x, xh, st, gate);
   return cudaGetLastError();
 }
 

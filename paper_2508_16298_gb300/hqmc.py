@@ -47,7 +47,8 @@ class Params(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("true_residual", ctypes.c_double),
-                ("recursive_residual", ctypes.c_double)]
+                ("recursive_residual", ctypes.c_double), ("fp64_fallback", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

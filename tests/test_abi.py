@@ -51,5 +51,5 @@ def test_params_struct_layout_matches_header(lib_path):
     from paper_2508_16298_gb300 import hqmc
     # int L, int Ntau, 4 doubles, int action, int reliable_interval
     assert ctypes.sizeof(hqmc.Params) == 4 + 4 + 4 * 8 + 4 + 4
-    assert ctypes.sizeof(hqmc.SolveInfo) == 4 * 4 + 2 * 8
+    assert ctypes.sizeof(hqmc.SolveInfo) == 4 * 4 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(hqmc.TrajInfo) == 4 * 4 + 5 * 8
