@@ -123,6 +123,68 @@ __device__ __forceinline__ void apply_P(const Geo& g, T* v, const T* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident sweep.  A thread owns bonds b = threadIdx.x + m*blockDim.x
+// (m < MB) of every family; their endpoint pairs (packed i | j << 16, valid
+// for V < 32768) are slice-independent and their link factors are loaded once
+// per slice, so the seven passes of a sweep touch only shared memory.
+// Largest block that leaves enough registers for MB bonds per family (MB = 0:
+// links are re-read from global memory in every pass instead).
+template <class R, int MB> struct SweepThreads {
+  static constexpr int max = MB == 0 ? 1024
+                             : sizeof(R) == 8 ? (MB == 1 ? 1024 : 512)
+                                              : (MB <= 2 ? 1024 : (MB == 3 ? 768 : 512));
+};
+__host__ __device__ constexpr int sweep_thread_cap(int bytes_per_real, int mb) {
+  return mb == 0 ? 1024 : bytes_per_real == 8 ? (mb == 1 ? 1024 : 512) : (mb <= 2 ? 1024 : (mb == 3 ? 768 : 512));
+}
+
+template <int MB>
+__device__ __forceinline__ void make_bonds(const Geo& g, int (&ij)[4][MB]) {
+  const int nb = g.V >> 1;
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+      const int b = threadIdx.x + m * blockDim.x;
+      int i = 0, j = 0, c = 0;
+      if (b < nb) bond_of(g, f + 1, b, i, j, c);
+      ij[f][m] = (b < nb) ? (i | (j << 16)) : -1;
+    }
+}
+
+template <class T, int MB>
+__device__ __forceinline__ void load_links(const int (&ij)[4][MB], const T* __restrict__ U, T (&u)[4][MB]) {
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+      T z = {};
+      if (ij[f][m] >= 0) z = __ldg(U + 2 * (ij[f][m] & 0xffff) + (f >= 2 ? 1 : 0));
+      u[f][m] = z;
+    }
+}
+
+// v <- P v (factors applied rightmost first: families 4 3 2 1 2 3 4).
+template <class T, int MB>
+__device__ __forceinline__ void sweep(T* v, const int (&ij)[4][MB], const T (&u)[4][MB]) {
+  constexpr int fam[7] = {3, 2, 1, 0, 1, 2, 3};
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+      const int p = ij[fam[k]][m];
+      if (p >= 0) {
+        const int i = p & 0xffff, j = p >> 16;
+        const T vi = v[i], vj = v[j];
+        v[i] = cfma(vi, u[fam[k]][m], vj);
+        v[j] = cfmac(vj, u[fam[k]][m], vi);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic reductions: a fixed tree per block and a fixed order over the
 // per-block partials, so that every block of a consumer kernel that sums the
 // same partials gets bit-identical totals.

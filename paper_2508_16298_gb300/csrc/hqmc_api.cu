@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <utility>
 #include <vector>
@@ -45,8 +46,9 @@ struct hqmc_config {
   long long n = 0;  // sites
   double a = 0, t1 = 0, t2 = 0, cB = 0;
   BosonParams bp{};
-  SliceLaunch sl{};   // fused M^dagger M
-  SliceLaunch sl1{};  // apply_M and force (one CTA per slice, no cluster)
+  SliceLaunch sl{};    // fused M^dagger M in FP64
+  SliceLaunch sl32{};  // fused M^dagger M in FP32 (same grid and clusters, own block shape)
+  SliceLaunch sl1{};   // apply_M and force (one CTA per slice, no cluster)
   int ew_grid = 0;    // CG update grid (= number of <r,r> partials)
   int act_grid = 0;
   int reliable = kDefaultReliable;
@@ -228,8 +230,9 @@ int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, con
   a.part_out = cfg->part_mdagm;
   a.st = cfg->st;
   int slot;
+  const SliceLaunch& sl = sizeof(R) == 8 ? cfg->sl : cfg->sl32;
   RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
-  LK(1, (launch_mdagm<R, MODE_CGDIR>(cfg->sl, a, s)));
+  LK(1, (launch_mdagm<R, MODE_CGDIR>(sl, a, s)));
   RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
   RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
   LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, cfg->sl.grid,
@@ -513,18 +516,37 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     cfg->bp.noncompact = p->action == HQMC_ACTION_NONCOMPACT;
     cfg->reliable = p->reliable_interval > 0 ? p->reliable_interval : kDefaultReliable;
 
-    // slice kernels: enough threads for one pass over a family's V/2 bonds
+    // slice kernels: enough threads for one pass over a family's V/2 bonds; the
+    // fused kernel holds mb bonds of every family per thread in registers when
+    // a block shape with enough registers exists (mb = 0 otherwise)
     const int bonds = V / 2;
-    const int rounds = (bonds + 1023) / 1024;
-    int threads = (bonds + rounds - 1) / rounds;
-    threads = ((threads + 31) / 32) * 32;
-    if (threads < 64) threads = 64;
+    auto shape = [&](int real_bytes, int* mb_out) {
+      for (int mb = 1; mb <= 3; ++mb) {  // mb = 4 would spill registers
+        const int th = ((bonds + mb - 1) / mb + 31) / 32 * 32;
+        if (th <= sweep_thread_cap(real_bytes, mb)) {
+          *mb_out = mb;
+          return th < 64 ? 64 : th;
+        }
+      }
+      *mb_out = 0;
+      const int rounds = (bonds + 1023) / 1024;
+      return ((bonds + rounds - 1) / rounds + 31) / 32 * 32;
+    };
+    int mb64 = 0, mb32 = 0;
+    const int th64 = shape(8, &mb64), th32 = shape(4, &mb32);
+    int threads = th64;
+    cfg->sl.mb = mb64;
     cfg->sl.g = cfg->g;
     cfg->sl.threads = threads;
     cfg->sl.cluster = p->Ntau < 8 ? p->Ntau : 8;
     cfg->sl1 = cfg->sl;
     cfg->sl1.cluster = 1;
     cfg->sl1.grid = p->Ntau;
+    cfg->sl1.mb = 0;
+    {
+      const int rounds = (bonds + 1023) / 1024;
+      cfg->sl1.threads = std::max(64, ((bonds + rounds - 1) / rounds + 31) / 32 * 32);
+    }
     // shrink the cluster until the device can co-schedule it
     for (;;) {
       cfg->sl.grid = ((p->Ntau + cfg->sl.cluster - 1) / cfg->sl.cluster) * cfg->sl.cluster;
@@ -536,11 +558,14 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
       if (cfg->sl.cluster == 1 || mdagm_max_active_clusters(cfg->sl) > 0) break;
       cfg->sl.cluster--;
     }
+    cfg->sl32 = cfg->sl;
+    cfg->sl32.mb = mb32;
+    cfg->sl32.threads = th32;
     if (rc != HQMC_OK) break;
     if (prepare_mdagm<double, MODE_APPLY>(cfg->sl) != cudaSuccess ||
         prepare_mdagm<double, MODE_RESID>(cfg->sl) != cudaSuccess ||
-        prepare_mdagm<float, MODE_APPLY>(cfg->sl) != cudaSuccess ||
-        prepare_mdagm<float, MODE_CGDIR>(cfg->sl) != cudaSuccess || prepare_apply_M<double>(cfg->sl1) != cudaSuccess ||
+        prepare_mdagm<float, MODE_APPLY>(cfg->sl32) != cudaSuccess ||
+        prepare_mdagm<float, MODE_CGDIR>(cfg->sl32) != cudaSuccess || prepare_apply_M<double>(cfg->sl1) != cudaSuccess ||
         prepare_apply_M<float>(cfg->sl1) != cudaSuccess || prepare_force(cfg->sl1) != cudaSuccess) {
       cudaGetLastError();
       rc = fail(cfg, HQMC_EUNSUPPORTED, "cannot configure slice kernels for L=%d", L);
@@ -657,7 +682,7 @@ int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void*
     a.x = (const float2*)x;
     a.y = (float2*)y;
     RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
-    LK(1, (launch_mdagm<float, MODE_APPLY>(cfg->sl, a, s)));
+    LK(1, (launch_mdagm<float, MODE_APPLY>(cfg->sl32, a, s)));
     RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
   }
   return HQMC_OK;

@@ -15,6 +15,7 @@ struct SliceLaunch {
   int threads;   // threads per CTA
   int cluster;   // CTAs per cluster (consecutive slices)
   int grid;      // CTAs, a multiple of cluster, >= Ntau
+  int mb;        // bonds of each family per thread held in registers (1..4; 0: links from global)
 };
 
 enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_CGDIR = 2 };

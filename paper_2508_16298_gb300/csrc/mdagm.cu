@@ -41,8 +41,8 @@ __device__ __forceinline__ C2<R> load_input(const MdagmArgs<R>& a, const C2<R>* 
   return a.x[g];
 }
 
-template <class R, int MODE>
-__global__ void __launch_bounds__(1024, 1) mdagm_kernel(const MdagmArgs<R> a) {
+template <class R, int MODE, int MB>
+__global__ void __launch_bounds__((SweepThreads<R, MB>::max), 1) mdagm_kernel(const MdagmArgs<R> a) {
   using T = C2<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int V = a.g.V, N = a.g.Ntau;
@@ -120,29 +120,42 @@ __global__ void __launch_bounds__(1024, 1) mdagm_kernel(const MdagmArgs<R> a) {
     p_new = (s_k & 1) ? a.pbuf[0] : a.pbuf[1];
   }
   const R cB = a.cB;
-
+  const int taum = (tau == 0) ? N - 1 : tau - 1;
+  const int taup = (tau == N - 1) ? 0 : tau + 1;
   const size_t base = (size_t)tau * V;
+
+  constexpr int MBA = MB > 0 ? MB : 1;
+  int ij[4][MBA];
+  T uu[4][MBA];
   const T* Ut = a.U + base * 2;
+  if constexpr (MB > 0) make_bonds(a.g, ij);
   if (active) {
+    if constexpr (MB > 0) load_links(ij, Ut, uu);
+    // rank 0 prefetches its halo input x_{tau-1}, the others x_{tau+1}
+    const size_t bpre = (size_t)(rank == 0 ? taum : taup) * V;
     for (int s = threadIdx.x; s < V; s += blockDim.x) {
-      T v = load_input<R, MODE>(a, p_old, base + s, beta, first);
+      const T v = load_input<R, MODE>(a, p_old, base + s, beta, first);
       Z[s] = v;
       Y[s] = v;
       if (MODE == MODE_CGDIR) p_new[base + s] = v;
+      W[s] = load_input<R, MODE>(a, p_old, bpre + s, beta, first);
     }
     __syncthreads();
-    apply_P(a.g, Z, Ut);  // z_tau = P_tau x_tau
+    if constexpr (MB > 0) sweep(Z, ij, uu);  // z_tau = P_tau x_tau
+    else apply_P(a.g, Z, Ut);
   }
   cluster_arrive();  // z_tau published
 
   const T* Zprev = W;
   if (rank == 0 && active) {
     // halo: z_{tau-1} = P_{tau-1} x_{tau-1} for the first slice of the cluster
-    const int taum = (tau == 0) ? N - 1 : tau - 1;
-    const size_t bm = (size_t)taum * V;
-    for (int s = threadIdx.x; s < V; s += blockDim.x) W[s] = load_input<R, MODE>(a, p_old, bm + s, beta, first);
-    __syncthreads();
-    apply_P(a.g, W, a.U + bm * 2);
+    if constexpr (MB > 0) {
+      load_links(ij, a.U + (size_t)taum * V * 2, uu);
+      sweep(W, ij, uu);
+      load_links(ij, Ut, uu);
+    } else {
+      apply_P(a.g, W, a.U + (size_t)taum * V * 2);
+    }
   }
   cluster_wait();
   if (rank != 0) Zprev = cl.map_shared_rank(Z, rank - 1);
@@ -151,19 +164,24 @@ __global__ void __launch_bounds__(1024, 1) mdagm_kernel(const MdagmArgs<R> a) {
   if (active) {
     const R sig = (tau == 0) ? R(-1) : R(1);
     const R sigp = (tau == N - 1) ? R(-1) : R(1);
-    for (int s = threadIdx.x; s < V; s += blockDim.x) Y[s] = caxpy(Y[s], -sig * cB, Zprev[s]);
-    __syncthreads();  // W (rank 0's halo) fully consumed before it is reused
-    const int taup = (tau == N - 1) ? 0 : tau + 1;
-    const size_t bp = (size_t)taup * V;
-    for (int s = threadIdx.x; s < V; s += blockDim.x) {
-      T xn = load_input<R, MODE>(a, p_old, bp + s, beta, first);
-      W[s] = caxpy(cscale(cB, Z[s]), -sigp, xn);
+    if (rank == 0) {
+      const size_t bp = (size_t)taup * V;
+      for (int s = threadIdx.x; s < V; s += blockDim.x) {
+        Y[s] = caxpy(Y[s], -sig * cB, W[s]);
+        W[s] = caxpy(cscale(cB, Z[s]), -sigp, load_input<R, MODE>(a, p_old, bp + s, beta, first));
+      }
+    } else {
+      for (int s = threadIdx.x; s < V; s += blockDim.x) {
+        Y[s] = caxpy(Y[s], -sig * cB, Zprev[s]);
+        W[s] = caxpy(cscale(cB, Z[s]), -sigp, W[s]);
+      }
     }
   }
   cluster_arrive();  // finished reading the neighbour's shared memory
   if (active) {
     __syncthreads();
-    apply_P(a.g, W, Ut);
+    if constexpr (MB > 0) sweep(W, ij, uu);
+    else apply_P(a.g, W, Ut);
     for (int s = threadIdx.x; s < V; s += blockDim.x) {
       T q = caxpy(Y[s], cB, W[s]);
       if (MODE == MODE_APPLY) {
@@ -199,18 +217,30 @@ static size_t mdagm_smem(const SliceLaunch& sl) {
   return (size_t)3 * sl.g.V * sizeof(C2<R>);
 }
 
-template <class R, int MODE>
-cudaError_t prepare_mdagm(const SliceLaunch& sl) {
-  cudaError_t e = cudaFuncSetAttribute(mdagm_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <class R, int MODE, int MB>
+static cudaError_t prepare_mb(const SliceLaunch& sl) {
+  cudaError_t e = cudaFuncSetAttribute(mdagm_kernel<R, MODE, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)mdagm_smem<R, MODE>(sl));
   if (e != cudaSuccess) return e;
   if (sl.cluster > 8)
-    e = cudaFuncSetAttribute(mdagm_kernel<R, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(mdagm_kernel<R, MODE, MB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
 template <class R, int MODE>
-cudaError_t launch_mdagm(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStream_t s) {
+cudaError_t prepare_mdagm(const SliceLaunch& sl) {
+  switch (sl.mb) {
+    case 0: return prepare_mb<R, MODE, 0>(sl);
+    case 1: return prepare_mb<R, MODE, 1>(sl);
+    case 2: return prepare_mb<R, MODE, 2>(sl);
+    case 3: return prepare_mb<R, MODE, 3>(sl);
+    case 4: return prepare_mb<R, MODE, 4>(sl);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class R, int MODE, int MB>
+static cudaError_t launch_mb(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sl.grid);
   cfg.blockDim = dim3(sl.threads);
@@ -223,10 +253,23 @@ cudaError_t launch_mdagm(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStrea
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, mdagm_kernel<R, MODE>, a);
+  return cudaLaunchKernelEx(&cfg, mdagm_kernel<R, MODE, MB>, a);
 }
 
-int mdagm_max_active_clusters(const SliceLaunch& sl) {
+template <class R, int MODE>
+cudaError_t launch_mdagm(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStream_t s) {
+  switch (sl.mb) {
+    case 0: return launch_mb<R, MODE, 0>(sl, a, s);
+    case 1: return launch_mb<R, MODE, 1>(sl, a, s);
+    case 2: return launch_mb<R, MODE, 2>(sl, a, s);
+    case 3: return launch_mb<R, MODE, 3>(sl, a, s);
+    case 4: return launch_mb<R, MODE, 4>(sl, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MB>
+static int max_active_clusters_mb(const SliceLaunch& sl) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sl.grid);
   cfg.blockDim = dim3(sl.threads);
@@ -239,11 +282,22 @@ int mdagm_max_active_clusters(const SliceLaunch& sl) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (const void*)mdagm_kernel<double, MODE_CGDIR>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)mdagm_kernel<double, MODE_CGDIR, MB>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
   return n;
+}
+
+int mdagm_max_active_clusters(const SliceLaunch& sl) {
+  switch (sl.mb) {
+    case 0: return max_active_clusters_mb<0>(sl);
+    case 1: return max_active_clusters_mb<1>(sl);
+    case 2: return max_active_clusters_mb<2>(sl);
+    case 3: return max_active_clusters_mb<3>(sl);
+    case 4: return max_active_clusters_mb<4>(sl);
+    default: return -1;
+  }
 }
 
 template cudaError_t launch_mdagm<double, MODE_APPLY>(const SliceLaunch&, const MdagmArgs<double>&, cudaStream_t);

@@ -177,9 +177,10 @@ __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, in
     } else {
       part_rr_out[0] = rr;
     }
+    // the iteration budget is the one set at the start of the solve
     if (!isfinite(rr)) st->done = CG_NONFINITE;
     else if (rr <= st->tol2bb) st->done = CG_CONVERGED;
-    else if (k >= maxit) st->done = CG_MAXIT;
+    else if (k >= st->maxit) st->done = CG_MAXIT;
     else st->done = CG_RUNNING;
   }
 }
