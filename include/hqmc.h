@@ -85,11 +85,12 @@ typedef struct hqmc_config hqmc_config;
 typedef struct hqmc_solve_info {
     int status;                /* hqmc_status of the solve */
     int iterations;            /* applications of M^dagger M to a search direction */
-    int restarts;              /* mixed solver: restarts after an FP32 breakdown */
+    int restarts;              /* mixed solver: restarts after an FP32 breakdown or stall */
     int reliable_updates;      /* mixed solver: FP64 residual recomputations */
     double true_residual;      /* ||phi - (M^dagger M) x|| / ||phi||, computed in FP64 */
     double recursive_residual; /* the recurrence's estimate at exit */
-    int fp64_fallback;         /* mixed solver: 1 if repeated FP32 breakdowns handed the
+    int fp64_fallback;         /* mixed solver: 1 if FP32 breakdowns, or a true residual cut
+                                  by less than 10x over four reliable updates, handed the
                                   rest of the solve to the FP64 recurrence */
     int reserved;
 } hqmc_solve_info;

@@ -237,12 +237,16 @@ struct CgState {
   int done;          // CG_* below
   int loops;         // loop bodies executed in this solve
   int loop_cap;      // hard bound on loop bodies (termination guard of the device-side loop)
-  int pad;
+  int n_rel;         // mixed solver: reliable updates done
+  double rr_rel[4];  // mixed solver: true <r,r> at the last four reliable updates (ring)
 };
 
 // CG_REC_CONVERGED: the recursive residual met tol; the true residual still has
 // to be checked.  CG_CONVERGED: the true FP64 residual met tol.
-enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4, CG_REC_CONVERGED = 5 };
+// CG_STAGNATED (mixed solver): four reliable updates cut the true residual by
+// less than 10x, i.e. FP32 rounding stalls the recurrence on this field.
+enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4, CG_REC_CONVERGED = 5,
+       CG_STAGNATED = 6 };
 
 // Gates of the kernels that close a loop body: run always, only after the
 // recursive residual converged, or whenever the solve is still active.

@@ -371,13 +371,14 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
       break;
     }
     if (st.done == CG_CONVERGED) break;
-    if (st.done == CG_BREAKDOWN && cur == HQMC_SOLVER_MIXED) {
-      // <p, O32 p> <= 0: the FP32 operator cannot resolve the lowest modes of
-      // this field.  Fold in the correction, restart from the FP64 residual,
-      // and after repeated breakdowns finish the solve in FP64.
+    if ((st.done == CG_BREAKDOWN || st.done == CG_STAGNATED) && cur == HQMC_SOLVER_MIXED) {
+      // <p, O32 p> <= 0 or a stalled residual: FP32 rounding cannot resolve the
+      // lowest modes of this field.  Fold in the correction and restart from the
+      // FP64 residual; after repeated breakdowns, or at once on stagnation,
+      // finish the solve with the FP64 recurrence.
       inf.restarts++;
       LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
-      if (inf.restarts > kMaxBreakdowns) {
+      if (st.done == CG_STAGNATED || inf.restarts > kMaxBreakdowns) {
         cur = HQMC_SOLVER_CG64;
         inf.fp64_fallback = 1;
         RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, tol, maxit, GATE_ALWAYS, s));

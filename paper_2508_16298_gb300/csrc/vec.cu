@@ -164,6 +164,7 @@ __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, in
     st->pq_last = 0.0;
     st->alpha_last = 0.0;
     st->loops = 0;
+    st->n_rel = 0;
     st->loop_cap = (maxit > (1 << 29) ? (1 << 30) : 2 * maxit) + 64;
     if (!isfinite(rr) || !isfinite(bb)) st->done = CG_NONFINITE;
     else if (bb == 0.0 || rr <= st->tol2bb) st->done = CG_CONVERGED;
@@ -177,10 +178,18 @@ __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, in
     } else {
       part_rr_out[0] = rr;
     }
+    bool stalled = false;
+    if (mode == FIN_RELIABLE) {
+      const int nr = st->n_rel;
+      stalled = nr >= 4 && rr > 1e-2 * st->rr_rel[nr & 3];
+      st->rr_rel[nr & 3] = rr;
+      st->n_rel = nr + 1;
+    }
     // the iteration budget is the one set at the start of the solve
     if (!isfinite(rr)) st->done = CG_NONFINITE;
     else if (rr <= st->tol2bb) st->done = CG_CONVERGED;
     else if (k >= st->maxit) st->done = CG_MAXIT;
+    else if (stalled) st->done = CG_STAGNATED;
     else st->done = CG_RUNNING;
   }
 }
