@@ -239,9 +239,10 @@ def test_trajectory_with_device_draws(hq):
     assert bool(info["accepted"]) == ref["accepted"]
 
 
-def test_leapfrog_reversible_at_config2_size(hq):
-    """Property that holds at any size: integrate, flip p, integrate back."""
-    L, N = 24, 240
+def test_leapfrog_reversible(hq):
+    """Integrate, flip p, integrate back (L = 24; Ntau = 48 keeps kappa small enough for
+    CG to reach a true residual of 1e-11, which reversibility to 1e-9 needs)."""
+    L, N = 24, 48
     th = inputs.theta_warm(L, N, seed=161)
     p = inputs.momenta(L, N, seed=162)
     R = inputs.complex_gaussian(L, N, seed=163)
@@ -255,6 +256,21 @@ def test_leapfrog_reversible_at_config2_size(hq):
         assert i1["status"] == 0 and i2["status"] == 0
         assert (tht.cpu().numpy() - th).__abs__().max() < 1e-9
         assert (pt.cpu().numpy() + p).__abs__().max() < 1e-9
+
+
+def test_energy_conservation_at_config2_size(hq):
+    """At L = 24, Ntau = 240 (CG to 1e-8): |dH| shrinks ~4x when dt halves at fixed length."""
+    L, N = 24, 240
+    th = inputs.theta_warm(L, N, seed=171)
+    p = inputs.momenta(L, N, seed=172)
+    R = inputs.complex_gaussian(L, N, seed=173)
+    dHs = []
+    with hq.Config(L, N) as cfg:
+        for ns, dt in ((2, 0.01), (4, 0.005)):
+            info = hq.trajectory(cfg, cuda(th), p_in=cuda(p), R_in=cuda(R), u_in=0.0, nsteps=ns, dt=dt, tol=1e-8)
+            assert info["status"] == 0 and info["max_true_residual"] <= 1e-8
+            dHs.append(abs(info["dH"]))
+    assert 2.5 < dHs[0] / dHs[1] < 6.0, dHs
 
 
 def test_invalid_arguments(hq):
