@@ -62,3 +62,26 @@ def theta_warm(L: int, Ntau: int, seed: int, J: float = 1.0, dtau: float = 0.1) 
     d -= d.mean(axis=0, keepdims=True)
     w = np.cumsum(d, axis=0) - d[0]
     return u + w
+
+
+def theta_ordered(L: int, Ntau: int, seed: int, J: float = 1.0, dtau: float = 0.1,
+                  sigma_space: float = 0.3) -> np.ndarray:
+    """Gauge field near the pi-flux background that half-filled fermions favour.
+
+    theta = pi-flux + fluctuation + random gauge transformation:
+      * fluctuation: every bond gets N(0, sigma_space^2) plus a periodic Gaussian
+        walk in tau with step variance J*dtau/2 (as in theta_warm);
+      * gauge transformation: theta_ij += l_i - l_j with l ~ U[-pi, pi) per
+        spatial site (the same at every tau), which changes no gauge-invariant
+        quantity, so the field looks random bond by bond.
+    """
+    g = rng(seed)
+    th = theta_pi_flux(L, Ntau)
+    th += g.standard_normal(size=(1, L, L, 2)) * sigma_space
+    d = g.standard_normal(size=(Ntau, L, L, 2)) * np.sqrt(0.5 * J * dtau)
+    d -= d.mean(axis=0, keepdims=True)
+    th += np.cumsum(d, axis=0) - d[0]
+    lam = g.uniform(-np.pi, np.pi, size=(L, L))  # [y, x]
+    th[..., 0] += lam[None, :, :] - np.roll(lam, -1, axis=1)[None, :, :]
+    th[..., 1] += lam[None, :, :] - np.roll(lam, -1, axis=0)[None, :, :]
+    return th
