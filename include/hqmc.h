@@ -75,6 +75,10 @@ typedef struct hqmc_params {
     double K;              /* plaquette coupling (0 in the compact runs here) */
     int action;            /* HQMC_ACTION_COMPACT or HQMC_ACTION_NONCOMPACT */
     int reliable_interval; /* mixed solver: FP64 residual update period; <= 0 means 50 */
+    int autotune;          /* 1: time every admissible launch shape of the fused M^dagger M in
+                              hqmc_make_config and keep the fastest; 0: built-in choice */
+    int variant;           /* fused M^dagger M kernel: 0 any, 1 generic only, 2 register-blocked
+                              only (HQMC_EUNSUPPORTED if no strip shape fits L) */
 } hqmc_params;
 
 /* Opaque configuration: geometry, launch shapes and the device workspace
@@ -129,6 +133,15 @@ HQMC_API long long hqmc_num_sites(const hqmc_config* cfg);
 /* Number of CUDA kernels this config has enqueued since it was made (host
  * counter; no device work).  Differences around a region count its launches. */
 HQMC_API long long hqmc_launch_count(const hqmc_config* cfg);
+
+/* Launch shape of the fused M^dagger M for one precision (host query):
+ * *variant > 0: register-blocked kernel with strips of *variant 2x2 blocks;
+ * *variant <= 0: generic kernel holding -*variant bonds per family in registers
+ * (0: links re-read from memory).  *cluster: CTAs (slices) per cluster;
+ * *threads: block size; *tuned_us: autotuner's time of one apply (0 if not
+ * tuned).  Any output may be NULL. */
+HQMC_API int hqmc_get_launch_shape(const hqmc_config* cfg, int precision, int* variant, int* cluster,
+                                   int* threads, float* tuned_us);
 
 /* ---- operators (Methods, Eq. (M_alpha) and the checkerboard Eq. (eq24)) -- */
 

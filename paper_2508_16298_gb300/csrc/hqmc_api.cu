@@ -48,6 +48,10 @@ struct hqmc_config {
   BosonParams bp{};
   SliceLaunch sl{};    // fused M^dagger M in FP64
   SliceLaunch sl32{};  // fused M^dagger M in FP32 (same grid and clusters, own block shape)
+  SliceLaunch slb64{}; // register-blocked fused M^dagger M, FP64 (nby = 0: not available)
+  SliceLaunch slb32{}; // register-blocked fused M^dagger M, FP32 (nby = 0: not available)
+  SliceLaunch fused64{}, fused32{};  // shapes used for APPLY / CG direction (nby > 0: register-blocked)
+  float tuned_us64 = 0.f, tuned_us32 = 0.f;  // autotuner: time of one FP64 / FP32 apply (0: not tuned)
   SliceLaunch sl1{};   // apply_M and force (one CTA per slice, no cluster)
   int ew_grid = 0;    // CG update grid (= number of <r,r> partials)
   int act_grid = 0;
@@ -56,6 +60,7 @@ struct hqmc_config {
   // device workspace
   double2* U64 = nullptr;
   float2* U32 = nullptr;
+  float2* th32 = nullptr;
   double2 *r64 = nullptr, *p64[2] = {nullptr, nullptr}, *q64 = nullptr;
   float2 *r32 = nullptr, *p32[2] = {nullptr, nullptr}, *q32 = nullptr, *xh32 = nullptr;
   double2 *eta = nullptr, *Xw = nullptr, *Rw = nullptr, *vscratch = nullptr;
@@ -182,9 +187,26 @@ int check_device(hqmc_config* cfg) {
   return HQMC_OK;
 }
 
+// Per-gauge-field tables: the FP64 link table, and for FP32 either the float
+// link table (generic kernel) or theta as float (register-blocked kernel).
 int links(hqmc_config* cfg, const double* theta, bool need64, bool need32, cudaStream_t s) {
-  LK(1, launch_links(cfg->g, theta, cfg->t1, cfg->t2, need64 ? cfg->U64 : nullptr, need32 ? cfg->U32 : nullptr, s));
+  const bool blk32 = need32 && cfg->fused32.nby > 0;
+  LK(1, launch_links(cfg->g, theta, cfg->t1, cfg->t2, need64 ? cfg->U64 : nullptr,
+                     (need32 && !blk32) ? cfg->U32 : nullptr, blk32 ? cfg->th32 : nullptr, s));
   return HQMC_OK;
+}
+
+// Fused M^dagger M launch in the kernel variant chosen for this precision.
+template <class R>
+const SliceLaunch& fused_shape(const hqmc_config* cfg) {
+  return sizeof(R) == 8 ? cfg->fused64 : cfg->fused32;
+}
+
+template <class R, int MODE>
+cudaError_t launch_fused(hqmc_config* cfg, const MdagmArgs<R>& a, cudaStream_t s) {
+  const SliceLaunch& sh = fused_shape<R>(cfg);
+  if (sh.nby > 0) return launch_mdagm_block<R, MODE>(sh, a, s);
+  return launch_mdagm<R, MODE>(sh, a, s);
 }
 
 template <class R, int MODE>
@@ -192,6 +214,9 @@ MdagmArgs<R> mdagm_args(hqmc_config* cfg) {
   MdagmArgs<R> a{};
   a.g = cfg->g;
   a.cB = (R)cfg->cB;
+  a.th32 = cfg->th32;
+  a.t1 = cfg->t1;
+  a.t2 = cfg->t2;
   return a;
 }
 
@@ -230,12 +255,11 @@ int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, con
   a.part_out = cfg->part_mdagm;
   a.st = cfg->st;
   int slot;
-  const SliceLaunch& sl = sizeof(R) == 8 ? cfg->sl : cfg->sl32;
   RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
-  LK(1, (launch_mdagm<R, MODE_CGDIR>(sl, a, s)));
+  LK(1, (launch_fused<R, MODE_CGDIR>(cfg, a, s)));
   RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
   RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
-  LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, cfg->sl.grid,
+  LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, fused_shape<R>(cfg).grid,
                          cfg->part_ew, cfg->st, s));
   RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
   return HQMC_OK;
@@ -452,6 +476,99 @@ int check_solver(hqmc_config* cfg, int solver) {
   return HQMC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: times every admissible launch shape of the fused M^dagger M for
+// this lattice (generic or register-blocked kernel, strip height nby, cluster
+// size along tau) and keeps the fastest per precision.  Runs once per config
+// on zero-valued operands (the kernels' cost does not depend on the values).
+
+template <class R>
+int time_shape(hqmc_config* cfg, const SliceLaunch& sh, float* us) {
+  MdagmArgs<R> a = mdagm_args<R, MODE_APPLY>(cfg);
+  if (sizeof(R) == 8) {
+    a.U = (const C2<R>*)cfg->U64;
+    a.x = (const C2<R>*)cfg->p64[0];
+    a.y = (C2<R>*)cfg->q64;
+  } else {
+    a.U = (const C2<R>*)cfg->U32;
+    a.x = (const C2<R>*)cfg->p32[0];
+    a.y = (C2<R>*)cfg->q32;
+  }
+  auto go = [&]() { return sh.nby > 0 ? launch_mdagm_block<R, MODE_APPLY>(sh, a, 0) : launch_mdagm<R, MODE_APPLY>(sh, a, 0); };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t err = go();
+  const int reps = 5;
+  if (err == cudaSuccess) err = cudaEventRecord(e0, 0);
+  for (int k = 0; k < reps && err == cudaSuccess; ++k) err = go();
+  if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    *us = -1.f;
+    return HQMC_OK;
+  }
+  cfg->launches += reps + 1;
+  *us = 1e3f * ms / reps;
+  return HQMC_OK;
+}
+
+int autotune(hqmc_config* cfg) {
+  const int N = cfg->p.Ntau;
+  CK(cudaMemset(cfg->th0, 0, 2 * cfg->n * sizeof(double)));
+  CK(cudaMemset(cfg->p64[0], 0, cfg->n * sizeof(double2)));
+  CK(cudaMemset(cfg->p32[0], 0, cfg->n * sizeof(float2)));
+  LK(1, launch_links(cfg->g, cfg->th0, cfg->t1, cfg->t2, cfg->U64, cfg->U32, cfg->th32, 0));
+  const int clusters[4] = {1, 2, 4, 8};
+  for (int prec = 0; prec < 2; ++prec) {
+    const bool dbl = prec == 0;
+    std::vector<SliceLaunch> cand;
+    const SliceLaunch gen = dbl ? cfg->sl : cfg->sl32;
+    const SliceLaunch blk = dbl ? cfg->slb64 : cfg->slb32;
+    for (int c : clusters) {
+      if (c > N) continue;
+      SliceLaunch g = gen;
+      g.nby = 0;
+      g.cluster = c;
+      g.grid = (N + c - 1) / c * c;
+      if (cfg->p.variant != 2) cand.push_back(g);
+      if (blk.nby > 0) {
+        SliceLaunch b = blk;
+        b.cluster = c;
+        b.grid = g.grid;
+        cand.push_back(b);
+      }
+    }
+    float best = 1e30f;
+    SliceLaunch chosen = dbl ? cfg->fused64 : cfg->fused32;
+    for (const SliceLaunch& c : cand) {
+      const int rb = dbl ? 8 : 4;
+      const int nclus = c.nby > 0 ? mdagm_block_max_active_clusters(c, rb) : (dbl ? mdagm_max_active_clusters(c) : 1);
+      if (c.cluster > 1 && nclus <= 0) continue;
+      float us = -1.f;
+      RET(dbl ? time_shape<double>(cfg, c, &us) : time_shape<float>(cfg, c, &us));
+      if (us > 0.f && us < best) {
+        best = us;
+        chosen = c;
+      }
+    }
+    if (dbl) {
+      cfg->fused64 = chosen;
+      cfg->tuned_us64 = best;
+    } else {
+      cfg->fused32 = chosen;
+      cfg->tuned_us32 = best;
+    }
+  }
+  CK(cudaDeviceSynchronize());
+  return HQMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -477,6 +594,17 @@ long long hqmc_num_sites(const hqmc_config* cfg) { return cfg ? cfg->n : 0; }
 
 long long hqmc_launch_count(const hqmc_config* cfg) { return cfg ? cfg->launches : 0; }
 
+int hqmc_get_launch_shape(const hqmc_config* cfg, int precision, int* variant, int* cluster, int* threads,
+                          float* tuned_us) {
+  if (!cfg || (precision != HQMC_FP64 && precision != HQMC_FP32)) return HQMC_EINVAL;
+  const SliceLaunch& sh = precision == HQMC_FP64 ? cfg->fused64 : cfg->fused32;
+  if (variant) *variant = sh.nby > 0 ? sh.nby : -sh.mb;
+  if (cluster) *cluster = sh.cluster;
+  if (threads) *threads = sh.threads;
+  if (tuned_us) *tuned_us = precision == HQMC_FP64 ? cfg->tuned_us64 : cfg->tuned_us32;
+  return HQMC_OK;
+}
+
 int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
   if (!p || !out) return HQMC_EINVAL;
   *out = nullptr;
@@ -486,6 +614,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
       !std::isfinite(p->J) || !std::isfinite(p->K))
     return HQMC_EINVAL;
   if (p->action != HQMC_ACTION_COMPACT && p->action != HQMC_ACTION_NONCOMPACT) return HQMC_EINVAL;
+  if (p->variant < 0 || p->variant > 2) return HQMC_EINVAL;
   const long long n = (long long)p->L * p->L * p->Ntau;
   if (n > (1LL << 31) - 1) return HQMC_EINVAL;
 
@@ -562,6 +691,43 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     cfg->sl32 = cfg->sl;
     cfg->sl32.mb = mb32;
     cfg->sl32.threads = th32;
+    // register-blocked variant: strips of nby 2x2 blocks, (L/2)^2/nby threads
+    auto pick_block = [&](int real_bytes, SliceLaunch* out) {
+      *out = cfg->sl;
+      out->nby = 0;
+      const int Lh = L / 2;
+      for (int nby = 1; nby <= 3; ++nby) {
+        if (Lh % nby) continue;
+        const int th = Lh * Lh / nby;
+        const int cap = block_thread_cap(real_bytes, nby);
+        if (cap <= 0 || th > cap) continue;
+        SliceLaunch c = cfg->sl;
+        c.nby = nby;
+        c.threads = th;
+        cudaError_t pe = real_bytes == 8 ? prepare_mdagm_block<double, MODE_CGDIR>(c) : prepare_mdagm_block<float, MODE_CGDIR>(c);
+        if (pe == cudaSuccess)
+          pe = real_bytes == 8 ? prepare_mdagm_block<double, MODE_APPLY>(c) : prepare_mdagm_block<float, MODE_APPLY>(c);
+        if (pe != cudaSuccess || mdagm_block_max_active_clusters(c, real_bytes) <= 0) {
+          cudaGetLastError();
+          continue;
+        }
+        *out = c;
+        return;
+      }
+    };
+    pick_block(8, &cfg->slb64);
+    pick_block(4, &cfg->slb32);
+    // variant 1 keeps the generic kernel, 2 demands the register-blocked one
+    if (p->variant == 1) {
+      cfg->slb64.nby = 0;
+      cfg->slb32.nby = 0;
+    } else if (p->variant == 2 && (cfg->slb64.nby == 0 || cfg->slb32.nby == 0)) {
+      rc = fail(cfg, HQMC_EUNSUPPORTED, "no register-blocked shape fits L=%d", L);
+      break;
+    }
+    // default shapes: the register-blocked kernel where it fits (the autotuner may override)
+    cfg->fused64 = cfg->slb64.nby > 0 ? cfg->slb64 : cfg->sl;
+    cfg->fused32 = cfg->slb32.nby > 0 ? cfg->slb32 : cfg->sl32;
     if (rc != HQMC_OK) break;
     if (prepare_mdagm<double, MODE_APPLY>(cfg->sl) != cudaSuccess ||
         prepare_mdagm<double, MODE_RESID>(cfg->sl) != cudaSuccess ||
@@ -580,6 +746,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     // workspace
     if ((rc = dalloc(cfg, &cfg->U64, 2 * n))) break;
     if ((rc = dalloc(cfg, &cfg->U32, 2 * n))) break;
+    if ((rc = dalloc(cfg, &cfg->th32, n))) break;
     if ((rc = dalloc(cfg, &cfg->r64, n))) break;
     if ((rc = dalloc(cfg, &cfg->p64[0], n))) break;
     if ((rc = dalloc(cfg, &cfg->p64[1], n))) break;
@@ -597,8 +764,9 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     if ((rc = dalloc(cfg, &cfg->F, 2 * n))) break;
     if ((rc = dalloc(cfg, &cfg->th0, 2 * n))) break;
     if ((rc = dalloc(cfg, &cfg->pm, 2 * n))) break;
-    if ((rc = dalloc(cfg, &cfg->part_mdagm, 2 * (size_t)cfg->sl.grid))) break;
-    if ((rc = dalloc(cfg, &cfg->part_resid, 2 * (size_t)cfg->sl.grid))) break;
+    // partials of the fused kernel: room for any cluster size (grid <= Ntau + 7)
+    if ((rc = dalloc(cfg, &cfg->part_mdagm, 2 * ((size_t)p->Ntau + 8)))) break;
+    if ((rc = dalloc(cfg, &cfg->part_resid, 2 * ((size_t)p->Ntau + 8)))) break;
     if ((rc = dalloc(cfg, &cfg->part_ew, (size_t)cfg->ew_grid))) break;
     if ((rc = dalloc(cfg, &cfg->part_act, 4 * (size_t)cfg->act_grid))) break;
     if ((rc = dalloc(cfg, &cfg->terms, 8))) break;
@@ -621,6 +789,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
       rc = fail(cfg, HQMC_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
       break;
     }
+    if (p->autotune && (rc = autotune(cfg)) != HQMC_OK) break;
   } while (0);
   if (rc != HQMC_OK) {
     release(cfg);
@@ -674,7 +843,7 @@ int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void*
     a.x = (const double2*)x;
     a.y = (double2*)y;
     RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
-    LK(1, (launch_mdagm<double, MODE_APPLY>(cfg->sl, a, s)));
+    LK(1, (launch_fused<double, MODE_APPLY>(cfg, a, s)));
     RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
   } else {
     RET(links(cfg, theta, false, true, s));
@@ -683,7 +852,7 @@ int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void*
     a.x = (const float2*)x;
     a.y = (float2*)y;
     RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
-    LK(1, (launch_mdagm<float, MODE_APPLY>(cfg->sl32, a, s)));
+    LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
     RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
   }
   return HQMC_OK;

@@ -16,6 +16,7 @@ struct SliceLaunch {
   int cluster;   // CTAs per cluster (consecutive slices)
   int grid;      // CTAs, a multiple of cluster, >= Ntau
   int mb;        // bonds of each family per thread held in registers (1..4; 0: links from global)
+  int nby;       // register-blocked kernel: 2x2 blocks stacked per thread strip (0: not used)
 };
 
 enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_CGDIR = 2 };
@@ -37,6 +38,8 @@ struct MdagmArgs {
   double* part_out;        // per-CTA partials: CGDIR <p, Op>; RESID <r,r> then <b,b>
   CgState* st;
   int gate;                // RESID: GATE_* condition on st->done (GATE_ALWAYS needs no st)
+  const float2* th32;      // register-blocked FP32 kernel: (theta_x, theta_y) per site, wrapped to [-pi, pi)
+  double t1, t2;           // tanh(a), tanh(a/2)
 };
 
 // Fused M^dagger M (three modes).
@@ -47,6 +50,15 @@ cudaError_t prepare_mdagm(const SliceLaunch& sl);
 // Clusters of sl.cluster CTAs the device can keep resident (<= 0: none / error).
 int mdagm_max_active_clusters(const SliceLaunch& sl);
 
+// Register-blocked fused M^dagger M (APPLY and CGDIR modes; sl.nby in 1..3).
+template <class R, int MODE>
+cudaError_t launch_mdagm_block(const SliceLaunch& sl, const MdagmArgs<R>& a, cudaStream_t s);
+template <class R, int MODE>
+cudaError_t prepare_mdagm_block(const SliceLaunch& sl);
+// Largest block for a strip of nby 2x2 blocks in this precision (0: not available).
+int block_thread_cap(int real_bytes, int nby);
+int mdagm_block_max_active_clusters(const SliceLaunch& sl, int real_bytes);
+
 // y = M x or M^dagger x.
 template <class R>
 cudaError_t launch_apply_M(const SliceLaunch& sl, R cB, const C2<R>* U, const C2<R>* x, C2<R>* y,
@@ -55,8 +67,9 @@ template <class R>
 cudaError_t prepare_apply_M(const SliceLaunch& sl);
 
 // Link tables U = t_f e^{i theta} (double and/or float), theta -> links.
+// th32 (optional): theta as float, wrapped to [-pi, pi), for the FP32 register-blocked kernel.
 cudaError_t launch_links(const Geo& g, const double* theta, double t1, double t2, double2* U64,
-                         float2* U32, cudaStream_t s);
+                         float2* U32, float2* th32, cudaStream_t s);
 
 // CG update x += alpha p, r -= alpha q, partial <r,r>; MIXED: x is the float
 // correction.  Reads alpha from the partials of <p, Op>.

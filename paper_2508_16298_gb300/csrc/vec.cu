@@ -17,7 +17,8 @@ static inline int ew_blocks(long long n, int threads, int cap) {
 // Link tables: U[site][c] = t_f e^{i theta}, t1 = tanh(a) for x-bonds with even
 // tail x (family 1, the merged middle factor), t2 = tanh(a/2) for all others.
 __global__ void links_kernel(Geo g, const double* __restrict__ theta, double t1, double t2,
-                             double2* __restrict__ U64, float2* __restrict__ U32, long long n) {
+                             double2* __restrict__ U64, float2* __restrict__ U32, float2* __restrict__ th32,
+                             long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(i % g.V);
@@ -37,13 +38,18 @@ __global__ void links_kernel(Geo g, const double* __restrict__ theta, double t1,
       U32[2 * i] = make_float2((float)ux.x, (float)ux.y);
       U32[2 * i + 1] = make_float2((float)uy.x, (float)uy.y);
     }
+    if (th32) {
+      // 2 pi periodicity of the links: wrap before rounding to float
+      const double w = 6.283185307179586;
+      th32[i] = make_float2((float)(th.x - w * rint(th.x / w)), (float)(th.y - w * rint(th.y / w)));
+    }
   }
 }
 
 cudaError_t launch_links(const Geo& g, const double* theta, double t1, double t2, double2* U64,
-                         float2* U32, cudaStream_t s) {
+                         float2* U32, float2* th32, cudaStream_t s) {
   const long long n = (long long)g.V * g.Ntau;
-  links_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(g, theta, t1, t2, U64, U32, n);
+  links_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(g, theta, t1, t2, U64, U32, th32, n);
   return cudaGetLastError();
 }
 

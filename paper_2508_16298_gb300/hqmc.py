@@ -32,7 +32,7 @@ TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE = 0, 1, 2
 
 # Every function declared in include/hqmc.h.
 EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_error", "hqmc_num_sites",
-           "hqmc_launch_count",
+           "hqmc_launch_count", "hqmc_get_launch_shape",
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_cg_solve", "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate")
@@ -41,7 +41,8 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("Ntau", ctypes.c_int), ("dtau", ctypes.c_double),
                 ("t", ctypes.c_double), ("J", ctypes.c_double), ("K", ctypes.c_double),
-                ("action", ctypes.c_int), ("reliable_interval", ctypes.c_int)]
+                ("action", ctypes.c_int), ("reliable_interval", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("variant", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -71,6 +72,8 @@ _sig = {
     "hqmc_last_error": ([_vp], ctypes.c_char_p),
     "hqmc_num_sites": ([_vp], ctypes.c_longlong),
     "hqmc_launch_count": ([_vp], ctypes.c_longlong),
+    "hqmc_get_launch_shape": ([_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                               ctypes.POINTER(ctypes.c_float)], _i),
     "hqmc_apply_M": ([_vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "hqmc_apply_MdagM": ([_vp, _vp, _vp, _vp, _i, _vp], _i),
     "hqmc_cg_solve": ([_vp, _vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
@@ -113,9 +116,10 @@ class Config:
     """Owns an hqmc_config: lattice, model parameters, launch shapes and workspace."""
 
     def __init__(self, L: int, Ntau: int, dtau: float = 0.1, t: float = 1.0, J: float = 1.0,
-                 K: float = 0.0, noncompact: bool = False, reliable_interval: int = 50):
+                 K: float = 0.0, noncompact: bool = False, reliable_interval: int = 50, autotune: bool = False,
+                 variant: int = 0):
         self.params = Params(L, Ntau, dtau, t, J, K, ACTION_NONCOMPACT if noncompact else ACTION_COMPACT,
-                             reliable_interval)
+                             reliable_interval, int(autotune), variant)
         h = _vp()
         rc = _lib.hqmc_make_config(ctypes.byref(self.params), ctypes.byref(h))
         if rc != OK:
@@ -129,6 +133,13 @@ class Config:
         if self._h is None:
             raise ValueError("config already freed")
         return self._h
+
+    def launch_shape(self, precision: int = FP64) -> dict:
+        """Fused M^dagger M launch shape chosen for a precision (see hqmc_get_launch_shape)."""
+        v, c, t, us = _i(), _i(), _i(), ctypes.c_float()
+        self.check(_lib.hqmc_get_launch_shape(self.handle, precision, ctypes.byref(v), ctypes.byref(c),
+                                              ctypes.byref(t), ctypes.byref(us)))
+        return {"variant": v.value, "cluster": c.value, "threads": t.value, "tuned_us": us.value}
 
     def launch_count(self) -> int:
         """Kernels this config has enqueued so far."""

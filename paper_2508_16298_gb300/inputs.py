@@ -65,12 +65,13 @@ def theta_warm(L: int, Ntau: int, seed: int, J: float = 1.0, dtau: float = 0.1) 
 
 
 def theta_ordered(L: int, Ntau: int, seed: int, J: float = 1.0, dtau: float = 0.1,
-                  sigma_space: float = 0.3) -> np.ndarray:
+                  sigma_space: float = 0.3, tau_walk: float = 1.0) -> np.ndarray:
     """Gauge field near the pi-flux background that half-filled fermions favour.
 
     theta = pi-flux + fluctuation + random gauge transformation:
       * fluctuation: every bond gets N(0, sigma_space^2) plus a periodic Gaussian
-        walk in tau with step variance J*dtau/2 (as in theta_warm);
+        walk in tau with step variance tau_walk * J*dtau/2 (tau_walk = 0: the
+        field does not depend on tau, a "cold" start);
       * gauge transformation: theta_ij += l_i - l_j with l ~ U[-pi, pi) per
         spatial site (the same at every tau), which changes no gauge-invariant
         quantity, so the field looks random bond by bond.
@@ -78,7 +79,7 @@ def theta_ordered(L: int, Ntau: int, seed: int, J: float = 1.0, dtau: float = 0.
     g = rng(seed)
     th = theta_pi_flux(L, Ntau)
     th += g.standard_normal(size=(1, L, L, 2)) * sigma_space
-    d = g.standard_normal(size=(Ntau, L, L, 2)) * np.sqrt(0.5 * J * dtau)
+    d = g.standard_normal(size=(Ntau, L, L, 2)) * np.sqrt(0.5 * J * dtau * tau_walk)
     d -= d.mean(axis=0, keepdims=True)
     th += np.cumsum(d, axis=0) - d[0]
     lam = g.uniform(-np.pi, np.pi, size=(L, L))  # [y, x]

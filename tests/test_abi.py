@@ -49,7 +49,7 @@ def test_strerror_is_host_only(lib_path):
 
 def test_params_struct_layout_matches_header(lib_path):
     from paper_2508_16298_gb300 import hqmc
-    # int L, int Ntau, 4 doubles, int action, int reliable_interval
-    assert ctypes.sizeof(hqmc.Params) == 4 + 4 + 4 * 8 + 4 + 4
+    # int L, int Ntau, 4 doubles, int action, int reliable_interval, int autotune, int variant
+    assert ctypes.sizeof(hqmc.Params) == 4 + 4 + 4 * 8 + 4 * 4
     assert ctypes.sizeof(hqmc.SolveInfo) == 4 * 4 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(hqmc.TrajInfo) == 4 * 4 + 5 * 8

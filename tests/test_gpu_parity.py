@@ -43,11 +43,13 @@ APPLY_CASES = [(4, 2), (4, 5), (6, 7), (8, 13), (8, 40), (12, 17), (16, 160), (2
 
 
 @pytest.mark.parametrize("L,N", APPLY_CASES)
-def test_apply_MdagM_fp64(hq, L, N):
+@pytest.mark.parametrize("variant", [1, 0])
+def test_apply_MdagM_fp64(hq, L, N, variant):
+    """variant 1: generic kernel; 0: the register-blocked one where a strip shape fits."""
     lat = oracle.Lattice(L, N)
     th = inputs.theta_hot(L, N, seed=1000 + 7 * L + N)
     x = inputs.complex_gaussian(L, N, seed=2000 + 7 * L + N)
-    with hq.Config(L, N) as cfg:
+    with hq.Config(L, N, variant=variant) as cfg:
         y = hq.apply_MdagM(cfg, cuda(th), cuda(x)).cpu().numpy()
     assert rel(y, oracle.apply_MdagM(lat, th, x)) < 1e-12
 
@@ -63,13 +65,14 @@ def test_apply_M_fp64(hq, L, N, dagger):
     assert rel(y, oracle.apply_M(lat, th, x, dagger=dagger)) < 1e-12
 
 
-@pytest.mark.parametrize("L,N", [(4, 5), (8, 40), (24, 240), (48, 480), (66, 660)])
-def test_apply_fp32(hq, L, N):
+@pytest.mark.parametrize("L,N", [(4, 5), (8, 40), (12, 7), (24, 240), (48, 480), (66, 660)])
+@pytest.mark.parametrize("variant", [1, 0])
+def test_apply_fp32(hq, L, N, variant):
     lat = oracle.Lattice(L, N)
     th = inputs.theta_hot(L, N, seed=5000 + L)
     x = inputs.complex_gaussian(L, N, seed=6000 + L).astype(np.complex64)
     xo = x.astype(np.complex128)
-    with hq.Config(L, N) as cfg:
+    with hq.Config(L, N, variant=variant) as cfg:
         y = hq.apply_MdagM(cfg, cuda(th), cuda(x)).cpu().numpy()
         ym = hq.apply_M(cfg, cuda(th), cuda(x), dagger=True).cpu().numpy()
     assert y.dtype == np.complex64
@@ -118,6 +121,22 @@ def test_cg_solve_fp64(hq, L, N):
     assert rel(X, Xo) < 1e-7
     # phi^dagger X = R^dagger R (Eq. (H_hmc) at the draw point)
     assert abs(np.vdot(phi, X).real - np.vdot(R, R).real) < 1e-9 * np.vdot(R, R).real
+
+
+def test_cg_iterations_match_oracle_on_a_tau_smooth_field(hq):
+    """L = 12, Ntau = 120 (several thousand iterations): the GPU recurrence follows the
+    oracle's, so both stop at the same iteration up to rounding."""
+    L, N = 12, 120
+    lat = oracle.Lattice(L, N)
+    th = inputs.theta_warm(L, N, seed=201)
+    phi = oracle.apply_M(lat, th, inputs.complex_gaussian(L, N, seed=202), dagger=True)
+    Xo, it_o, res_o, st_o = oracle.cg(lat, th, phi, tol=1e-8, maxit=50000)
+    with hq.Config(L, N) as cfg:
+        X, info = hq.cg_solve(cfg, cuda(th), cuda(phi), tol=1e-8, maxit=50000)
+    assert st_o == 0 and info["status"] == 0
+    assert abs(info["iterations"] - it_o) <= 0.01 * it_o + 2, (info["iterations"], it_o)
+    r = phi - oracle.apply_MdagM(lat, th, X.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(phi)
 
 
 def test_cg_warm_start_and_edge_cases(hq):
@@ -286,6 +305,38 @@ def test_invalid_arguments(hq):
         assert e.value.status == hq.EINVAL
         with pytest.raises(ValueError):
             hq.apply_MdagM(cfg, th, torch.zeros((4, 4, 5), dtype=torch.complex128, device="cuda"))
+
+
+@pytest.mark.parametrize("L,N", [(8, 13), (24, 240), (66, 660)])
+def test_autotuned_shapes_keep_parity(hq, L, N):
+    """The autotuner picks kernel variant and cluster size; results must not change."""
+    lat = oracle.Lattice(L, N)
+    th = inputs.theta_hot(L, N, seed=181)
+    x = inputs.complex_gaussian(L, N, seed=182)
+    with hq.Config(L, N, autotune=True) as cfg:
+        for prec in (hq.FP64, hq.FP32):
+            sh = cfg.launch_shape(prec)
+            assert sh["tuned_us"] > 0 and 1 <= sh["cluster"] <= 8
+        y = hq.apply_MdagM(cfg, cuda(th), cuda(x)).cpu().numpy()
+        y32 = hq.apply_MdagM(cfg, cuda(th), cuda(x.astype(np.complex64))).cpu().numpy()
+    yo = oracle.apply_MdagM(lat, th, x)
+    assert rel(y, yo) < 1e-12
+    assert rel(y32, oracle.apply_MdagM(lat, th, x.astype(np.complex64).astype(np.complex128))) < 1e-5
+
+
+def test_cg_with_each_kernel_variant(hq):
+    L, N = 8, 40
+    lat = oracle.Lattice(L, N)
+    th = inputs.theta_hot(L, N, seed=191)
+    phi = inputs.complex_gaussian(L, N, seed=192)
+    Xo, it_o, _, _ = oracle.cg(lat, th, phi, tol=1e-12)
+    for variant in (1, 2):
+        with hq.Config(L, N, variant=variant) as cfg:
+            X, info = hq.cg_solve(cfg, cuda(th), cuda(phi), tol=1e-12)
+            Xm, infom = hq.cg_solve(cfg, cuda(th), cuda(phi), tol=1e-9, solver="mixed")
+        assert info["status"] == 0 and abs(info["iterations"] - it_o) <= 2
+        assert rel(X.cpu().numpy(), Xo) < 1e-7
+        assert infom["status"] == 0 and infom["true_residual"] <= 1e-9
 
 
 def test_timing_counters(hq):
