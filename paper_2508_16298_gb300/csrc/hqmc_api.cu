@@ -189,10 +189,12 @@ int check_device(hqmc_config* cfg) {
 
 // Per-gauge-field tables: the FP64 link table, and for FP32 either the float
 // link table (generic kernel) or theta as float (register-blocked kernel).
-int links(hqmc_config* cfg, const double* theta, bool need64, bool need32, cudaStream_t s) {
+// need32: tables for the FP32 fused kernel; table32: the float link table itself
+// (the FP32 apply of M reads it whatever the fused kernel uses).
+int links(hqmc_config* cfg, const double* theta, bool need64, bool need32, cudaStream_t s, bool table32 = false) {
   const bool blk32 = need32 && cfg->fused32.nby > 0;
   LK(1, launch_links(cfg->g, theta, cfg->t1, cfg->t2, need64 ? cfg->U64 : nullptr,
-                     (need32 && !blk32) ? cfg->U32 : nullptr, blk32 ? cfg->th32 : nullptr, s));
+                     ((need32 && !blk32) || table32) ? cfg->U32 : nullptr, blk32 ? cfg->th32 : nullptr, s));
   return HQMC_OK;
 }
 
@@ -821,7 +823,7 @@ int hqmc_apply_M(hqmc_config* cfg, const double* theta, const void* x, void* y, 
     RET(links(cfg, theta, true, false, s));
     LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, (const double2*)x, (double2*)y, dagger ? 1 : 0, s));
   } else {
-    RET(links(cfg, theta, false, true, s));
+    RET(links(cfg, theta, false, false, s, true));
     LK(1, launch_apply_M<float>(cfg->sl1, (float)cfg->cB, cfg->U32, (const float2*)x, (float2*)y, dagger ? 1 : 0, s));
   }
   return HQMC_OK;
