@@ -6,12 +6,14 @@ seeded synthetic gauge field; the chain continues from step to step.
 
 Default workload (plain FP64 GPU HMC): L = 24, Ntau = 240 (138,240 sites),
 dtau = 0.1, t = 1, J = 1, compact action, CG to a true FP64 residual of 1e-8,
-20 leapfrog steps of dt = 0.01.  Start (inputs.theta_ordered): the pi-flux
-background favoured by half-filled fermions plus Gaussian fluctuations smooth in
-imaginary time, under a random gauge transformation.  A start i.i.d. on every
-bond and slice makes M^dagger M so singular at this size that FP64 CG needs more
-than 6e4 iterations per solve and the pseudofermion force drives the leapfrog
-unstable at dt = 0.01.
+20 leapfrog steps of dt = 0.0005.  Start (inputs.theta_ordered with tau_walk=0):
+the pi-flux background favoured by half-filled fermions plus N(0, 0.3^2) on every
+bond, the same at every tau, under a random gauge transformation.  A start
+i.i.d. on every bond and slice makes M^dagger M so singular at this size that
+FP64 CG needs more than 6e4 iterations per solve, and fields that wander in tau
+let the pseudofermion force drive the leapfrog into singular configurations.
+The step keeps |dH| below 1 at this volume (|dH| grows like volume * dt^2 from
+a cold start: 125 at dt = 0.01, 31 at dt = 0.005, measured).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
@@ -38,14 +40,14 @@ METRIC = "M†M apply GB/s vs HBM peak; HMC traj/s learned+FP32 vs plain FP64 at
 
 WORKLOADS = {
     # plain FP64 HMC at L = 24, Ntau = 240
-    "hmc_fp64_L24_Nt240": dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.01, tol=1e-8,
-                               solver="cg64", seed=1, start="ordered"),
+    "hmc_fp64_L24_Nt240": dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.0005, tol=1e-8,
+                               solver="cg64", seed=1, start="cold"),
     # plain FP64 HMC at L = 8, Ntau = 40 (oracle-sized)
     "hmc_fp64_L8_Nt40": dict(L=8, Ntau=40, dtau=0.1, t=1.0, J=1.0, nsteps=10, dt=0.02, tol=1e-10,
                              solver="cg64", seed=1, start="hot"),
     # mixed precision at L = 48, Ntau = 480
-    "hmc_mixed_L48_Nt480": dict(L=48, Ntau=480, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.01, tol=1e-8,
-                                solver="mixed", seed=1, start="ordered"),
+    "hmc_mixed_L48_Nt480": dict(L=48, Ntau=480, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.00018, tol=1e-8,
+                                solver="mixed", seed=1, start="cold"),
 }
 DEFAULT_WORKLOAD = "hmc_fp64_L24_Nt240"
 
@@ -144,7 +146,7 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
 
 # CG iterations per trajectory used to scale oracle samples when no GPU run is
 # available (the reference arm); measured on the GPU with the same algorithm.
-ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 40000.0, "hmc_fp64_L8_Nt40": 11000.0, "hmc_mixed_L48_Nt480": 80000.0}
+ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 16500.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 40000.0}
 
 
 def run_reference(args, wl_name, wl, rank, world):
@@ -180,6 +182,8 @@ def start_theta(wl, seed):
         return inputs.theta_hot(wl["L"], wl["Ntau"], seed)
     if wl["start"] == "ordered":
         return inputs.theta_ordered(wl["L"], wl["Ntau"], seed, J=wl["J"], dtau=wl["dtau"])
+    if wl["start"] == "cold":
+        return inputs.theta_ordered(wl["L"], wl["Ntau"], seed, J=wl["J"], dtau=wl["dtau"], tau_walk=0.0)
     return inputs.theta_warm(wl["L"], wl["Ntau"], seed, J=wl["J"], dtau=wl["dtau"])
 
 
@@ -189,7 +193,9 @@ def config_of(wl_name, wl):
             "start": {"hot": "hot: theta i.i.d. U[-pi, pi)",
                       "warm": "warm: U[-pi, pi) per bond + periodic Gaussian walk in tau, step var J*dtau/2",
                       "ordered": "pi-flux + N(0, 0.3^2) per bond + periodic Gaussian walk in tau (step var "
-                                 "J*dtau/2) + random gauge transformation"}[wl["start"]],
+                                 "J*dtau/2) + random gauge transformation",
+                      "cold": "pi-flux + N(0, 0.3^2) per bond, tau-independent, + random gauge transformation"}
+                     [wl["start"]],
             "n_leapfrog": wl["nsteps"], "dt": wl["dt"], "cg_tol": wl["tol"], "solver": wl["solver"],
             "l2": "flushed between timed steps (512 MiB write; step times exclude the flush)"}
 
@@ -205,7 +211,7 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     L, N = wl["L"], wl["Ntau"]
-    cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"])
+    cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True)
     seed = wl["seed"] + 1000 * rank
     theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -286,7 +292,11 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     achieved_gbs = MDAGM_BYTES_PER_SITE[wl["solver"]] * sites / (md_avg_ms * 1e-3) / 1e9
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"kernel": "mdagm_kernel<double, CG direction>", "bound": "alu", "achieved": achieved_tflops,
+    shape = cfg.launch_shape(hqmc.FP64 if wl["solver"] == "cg64" else hqmc.FP32)
+    kname = (f"mdagm_block_kernel<{'double' if wl['solver'] == 'cg64' else 'float'}, CG direction, nby={shape['variant']}>"
+             if shape["variant"] > 0 else
+             f"mdagm_kernel<{'double' if wl['solver'] == 'cg64' else 'float'}, CG direction, mb={-shape['variant']}>")
+    roofline = {"kernel": kname, "cluster": shape["cluster"], "bound": "alu", "achieved": achieved_tflops,
                 "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_tflops,
                 "traffic": None,
                 "peak_note": "FP64 FMA rate measured on this GPU by hqmc_probe_fp64_rate",
@@ -331,7 +341,7 @@ def run_profile_case(wl):
     from paper_2508_16298_gb300 import hqmc, inputs
 
     L, N = wl["L"], wl["Ntau"]
-    with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"]) as cfg:
+    with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True) as cfg:
         # event timing makes the CG loop host-driven, so a profiler sees each kernel
         # (kernels inside a graph with conditional nodes cannot be profiled one by one)
         hqmc.set_timing(cfg, True)
