@@ -75,8 +75,7 @@ force_kernel(Geo g, double cB, const double2* __restrict__ U, const double2* __r
 }
 
 cudaError_t prepare_force(const SliceLaunch& sl) {
-  return cudaFuncSetAttribute(force_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(2 * sl.g.V * sizeof(double2)));
+  return raise_smem_limit(force_kernel, 2 * sl.g.V * sizeof(double2));
 }
 
 cudaError_t launch_force(const SliceLaunch& sl, double cB, const double2* U, const double2* X,

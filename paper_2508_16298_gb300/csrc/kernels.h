@@ -8,6 +8,17 @@
 
 namespace hqmc {
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never
+// lowers it: several configs of different sizes share the kernel in a process).
+template <class F>
+inline cudaError_t raise_smem_limit(F* kernel, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Launch shape of the slice kernels: one CTA per imaginary-time slice, grouped
 // into thread-block clusters of `cluster` consecutive slices.
 struct SliceLaunch {

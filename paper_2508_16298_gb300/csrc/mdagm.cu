@@ -219,8 +219,7 @@ static size_t mdagm_smem(const SliceLaunch& sl) {
 
 template <class R, int MODE, int MB>
 static cudaError_t prepare_mb(const SliceLaunch& sl) {
-  cudaError_t e = cudaFuncSetAttribute(mdagm_kernel<R, MODE, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)mdagm_smem<R, MODE>(sl));
+  cudaError_t e = raise_smem_limit(mdagm_kernel<R, MODE, MB>, mdagm_smem<R, MODE>(sl));
   if (e != cudaSuccess) return e;
   if (sl.cluster > 8)
     e = cudaFuncSetAttribute(mdagm_kernel<R, MODE, MB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -343,8 +342,7 @@ apply_M_kernel(Geo g, R cB, const C2<R>* __restrict__ U, const C2<R>* __restrict
 
 template <class R>
 cudaError_t prepare_apply_M(const SliceLaunch& sl) {
-  return cudaFuncSetAttribute(apply_M_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sl.g.V * sizeof(C2<R>)));
+  return raise_smem_limit(apply_M_kernel<R>, sl.g.V * sizeof(C2<R>));
 }
 
 template <class R>

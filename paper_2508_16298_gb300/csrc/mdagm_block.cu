@@ -400,8 +400,7 @@ __global__ void __launch_bounds__((BlockThreads<R, NBY>::max), 1) mdagm_block_ke
 
 template <class R, int MODE, int NBY>
 static cudaError_t block_prepare(const SliceLaunch& sl) {
-  return cudaFuncSetAttribute(mdagm_block_kernel<R, MODE, NBY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(4 * sl.g.V * sizeof(C2<R>)));
+  return raise_smem_limit(mdagm_block_kernel<R, MODE, NBY>, 4 * sl.g.V * sizeof(C2<R>));
 }
 
 template <class R, int MODE, int NBY>

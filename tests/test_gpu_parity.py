@@ -340,6 +340,21 @@ def test_cg_with_each_kernel_variant(hq):
         assert infom["status"] == 0 and infom["true_residual"] <= 1e-9
 
 
+def test_configs_of_different_sizes_coexist(hq):
+    """A small config made after a large one must not shrink kernel limits the large one needs."""
+    big, small = hq.Config(48, 16), hq.Config(8, 8)
+    try:
+        for cfg, (L, N) in ((big, (48, 16)), (small, (8, 8)), (big, (48, 16))):
+            lat = oracle.Lattice(L, N)
+            th = inputs.theta_hot(L, N, seed=211)
+            x = inputs.complex_gaussian(L, N, seed=212)
+            y = hq.apply_MdagM(cfg, cuda(th), cuda(x)).cpu().numpy()
+            assert rel(y, oracle.apply_MdagM(lat, th, x)) < 1e-12
+    finally:
+        big.close()
+        small.close()
+
+
 def test_timing_counters(hq):
     L, N = 8, 16
     with hq.Config(L, N) as cfg:
