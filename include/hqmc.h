@@ -162,6 +162,29 @@ HQMC_API int hqmc_apply_M(hqmc_config* cfg, const double* theta, const void* x, 
 HQMC_API int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void* y,
                      int precision, void* stream);
 
+/* y = (M^dagger M) x in FP64 without a config and without allocating device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate, such as code running while another component owns the
+ * device allocator (a memory pool that must not be bypassed, or a budget that is
+ * already handed out), plug-ins that are only given device pointers, or code
+ * that must not let cudaMalloc/cudaFree synchronise the device.  The fused
+ * apply's only scratch, the gauge field's FP64 link table, lives in a
+ * fixed-size device array that every device loading the library holds until
+ * the process exits.
+ *   p: model and lattice (autotune, variant and reliable_interval are ignored);
+ *   theta (double), x, y (complex double): caller device memory as for
+ *   hqmc_apply_MdagM; x and y must not overlap.
+ * Limit: Ntau * L * L <= 262144 sites (8 MiB of scratch); larger lattices
+ * return HQMC_EUNSUPPORTED without touching the device.  Every call fully
+ * rewrites the scratch before reading it, but all calls on a device share it:
+ * calls whose executions overlap on the GPU (different streams with no
+ * ordering) race and give wrong results, so order them on one stream.  The
+ * first call on each device looks up the scratch address (cudaGetSymbolAddress,
+ * once per device); make that first call before any stream capture.  The call
+ * only enqueues work on `stream`. */
+HQMC_API int hqmc_apply_MdagM_static(const hqmc_params* p, const double* theta, const void* x, void* y,
+                                     void* stream);
+
 /* ---- solver (Methods, "CG method and preconditioner", Eq. (pCG)) ------- */
 
 /* Solves (M^dagger M) x = phi.  phi and x are complex double.  x holds the

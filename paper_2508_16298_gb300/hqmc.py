@@ -35,7 +35,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_launch_count", "hqmc_get_launch_shape",
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_cg_solve", "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
-           "hqmc_probe_fp64_rate")
+           "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static")
 
 
 class Params(ctypes.Structure):
@@ -86,6 +86,7 @@ _sig = {
     "hqmc_set_timing": ([_vp, _i], _i),
     "hqmc_get_timing": ([_vp, _i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _i),
     "hqmc_probe_fp64_rate": ([_vp, ctypes.POINTER(ctypes.c_double)], _i),
+    "hqmc_apply_MdagM_static": ([ctypes.POINTER(Params), _vp, _vp, _vp, _vp], _i),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -316,3 +317,25 @@ def probe_fp64_rate(cfg: Config) -> float:
     out = ctypes.c_double()
     cfg.check(_lib.hqmc_probe_fp64_rate(cfg.handle, ctypes.byref(out)))
     return out.value
+
+
+STATIC_MAX_SITES = 262144
+
+
+def apply_MdagM_static(L: int, Ntau: int, theta, x, y=None, dtau: float = 0.1, t: float = 1.0):
+    """y = (M^dagger M) x in FP64 through hqmc_apply_MdagM_static: no config and no
+    device allocation inside the library, for callers that cannot allocate
+    (scratch is a fixed device array of STATIC_MAX_SITES sites; calls on one
+    device must not overlap on the GPU).  Returns y; raises HQMCError on failure."""
+    shape = (Ntau, L, L)
+    if not (theta.is_cuda and theta.dtype == torch.float64 and theta.is_contiguous()
+            and tuple(theta.shape) == shape + (2,)):
+        raise ValueError("theta must be a contiguous CUDA float64 tensor of shape (Ntau, L, L, 2)")
+    if not (x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous() and tuple(x.shape) == shape):
+        raise ValueError("x must be a contiguous CUDA complex128 tensor of shape (Ntau, L, L)")
+    y = torch.empty_like(x) if y is None else y
+    p = Params(L, Ntau, dtau, t, 1.0, 0.0, ACTION_COMPACT, 0, 0, 0)
+    rc = _lib.hqmc_apply_MdagM_static(ctypes.byref(p), _ptr(theta), _ptr(x), _ptr(y), _stream())
+    if rc != OK:
+        raise HQMCError(rc, f"static apply at L={L} Ntau={Ntau}")
+    return y
