@@ -243,6 +243,38 @@ HQMC_API int hqmc_trajectory(hqmc_config* cfg, double* theta, uint64_t seed, uin
                     double dt, double tol, int maxit, int solver, hqmc_traj_info* info,
                     void* stream);
 
+/* ---- batches of independent chains (many lattices, one launch per CG step) */
+
+/* A batch of nchains independent chains, chain c described by params[c] (L and
+ * Ntau may differ; the batched kernels are the generic fused ones and every
+ * chain gets the same cluster size, the smallest the chains admit).  Each
+ * chain owns a config's workspace.  Inside a CG solve every iteration is ONE
+ * launch of the fused M^dagger M over a tile table covering every chain's
+ * slices plus ONE launch of the vector update over every chain's blocks, under
+ * a device-side WHILE loop that runs while any chain is unconverged.  Every
+ * chain's arithmetic and reduction order equal those of its own single-chain
+ * config, so a batch reproduces independent runs bit for bit. */
+typedef struct hqmc_batch hqmc_batch;
+
+HQMC_API int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out);
+HQMC_API int hqmc_free_batch(hqmc_batch* b);
+HQMC_API const char* hqmc_batch_last_error(const hqmc_batch* b);
+/* Kernels the batch has enqueued (including its chains' configs). */
+HQMC_API long long hqmc_batch_launch_count(const hqmc_batch* b);
+
+/* CG on every chain: theta[c], phi[c], x[c] are HOST arrays of device
+ * pointers with chain c's layouts (as in hqmc_cg_solve); infos (host, nchains
+ * entries, nullable).  Returns the worst chain status.  Synchronises. */
+HQMC_API int hqmc_batch_cg_solve(hqmc_batch* b, const double* const* theta, const void* const* phi, void* const* x,
+                                 double tol, int maxit, hqmc_solve_info* infos, void* stream);
+
+/* One HQMC update of every chain (as hqmc_trajectory with device draws:
+ * seeds[c], the shared traj_counter, nsteps steps of dt[c]); theta[c] in/out;
+ * infos (host, nchains entries, nullable).  Synchronises. */
+HQMC_API int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* seeds, uint64_t traj_counter,
+                                   int nsteps, const double* dt, double tol, int maxit, hqmc_traj_info* infos,
+                                   void* stream);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 enum { HQMC_TIMER_MDAGM = 0, HQMC_TIMER_CG_UPDATE = 1, HQMC_TIMER_FORCE = 2, HQMC_TIMER_COUNT = 3 };

@@ -1041,3 +1041,437 @@ int hqmc_get_timing(hqmc_config* cfg, int timer, long long* launches, double* to
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Batches of independent chains (lattices of different L in one launch per CG
+// iteration).  Each chain keeps its own config (workspace, link tables, CG
+// state); the CG loop runs the generic fused kernel over a tile table that
+// covers every chain's slices, and a batched update over every chain's vector
+// blocks, under one WHILE node that continues while any chain is running.
+
+struct hqmc_batch {
+  std::vector<hqmc_config*> cfgs;
+  int C = 1;           // cluster size (slices per tile), shared by all chains
+  int threads = 64;    // block size of the batched fused kernel
+  size_t smem = 0;     // its dynamic shared memory (largest chain)
+  int ntiles = 0;
+  int total_ublocks = 0;
+  MdagmArgs<double>* d_cgdir = nullptr;
+  MdagmArgs<double>* d_resid_start = nullptr;
+  MdagmArgs<double>* d_resid_loop = nullptr;
+  UpdArgs<double>* d_upd = nullptr;
+  FinArgs* d_fin = nullptr;
+  int2* d_tiles = nullptr;
+  int2* d_ublocks = nullptr;
+  int* d_unblocks = nullptr;
+  CgState** d_states = nullptr;
+  void* h_stage = nullptr;  // pinned staging of the descriptor arrays
+  size_t stage_bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int body_kernels = 0;
+  long long launches = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+int bfail(hqmc_batch* b, int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b->err, sizeof(b->err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define BCK(call)                                                                                       \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess)                                                                              \
+      return bfail(b, HQMC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define BRET(call, c)                                          \
+  do {                                                         \
+    int rc_ = (call);                                          \
+    if (rc_ != HQMC_OK) {                                      \
+      snprintf(b->err, sizeof(b->err), "%s", (c)->err);        \
+      return rc_;                                              \
+    }                                                          \
+  } while (0)
+
+void batch_release(hqmc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_cgdir);
+  cudaFree(b->d_resid_start);
+  cudaFree(b->d_resid_loop);
+  cudaFree(b->d_upd);
+  cudaFree(b->d_fin);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_ublocks);
+  cudaFree(b->d_unblocks);
+  cudaFree(b->d_states);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  for (hqmc_config* c : b->cfgs) hqmc_free_config(c);
+  b->cfgs.clear();
+}
+
+// Per-chain descriptors of the batched CG kernels for operands (phi, x).
+int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* x, cudaStream_t s) {
+  const int nc = (int)b->cfgs.size();
+  char* st = (char*)b->h_stage;
+  auto* cgdir = (MdagmArgs<double>*)st;
+  auto* rs = cgdir + nc;
+  auto* rl = rs + nc;
+  auto* up = (UpdArgs<double>*)(rl + nc);
+  auto* fin = (FinArgs*)(up + nc);
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    const int nslots = (cfg->p.Ntau + b->C - 1) / b->C * b->C;
+    MdagmArgs<double> a = mdagm_args<double, MODE_CGDIR>(cfg);
+    a.U = cfg->U64;
+    a.y = cfg->q64;
+    a.r = cfg->r64;
+    a.pbuf[0] = cfg->p64[0];
+    a.pbuf[1] = cfg->p64[1];
+    a.part_in = cfg->part_ew;
+    a.n_part_in = cfg->ew_grid;
+    a.part_out = cfg->part_mdagm;
+    a.st = cfg->st;
+    cgdir[c] = a;
+    MdagmArgs<double> r = mdagm_args<double, MODE_RESID>(cfg);
+    r.U = cfg->U64;
+    r.x = x[c];
+    r.b = phi[c];
+    r.r_out = cfg->r64;
+    r.r_out_fp32 = 0;
+    r.part_out = cfg->part_resid;
+    r.st = cfg->st;
+    r.gate = GATE_ALWAYS;
+    rs[c] = r;
+    r.gate = GATE_REC;
+    rl[c] = r;
+    up[c] = UpdArgs<double>{cfg->n, x[c], 1, cfg->r64, cfg->p64[0], cfg->p64[1], cfg->q64, cfg->part_mdagm,
+                            nslots, cfg->part_ew, cfg->st};
+    fin[c] = FinArgs{cfg->part_resid, nslots, cfg->part_ew, cfg->ew_grid, cfg->st, cfg->report};
+  }
+  BCK(cudaMemcpyAsync(b->d_cgdir, cgdir, nc * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_resid_start, rs, nc * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_resid_loop, rl, nc * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_upd, up, nc * sizeof(UpdArgs<double>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_fin, fin, nc * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
+  return HQMC_OK;
+}
+
+int batch_body(hqmc_batch* b, cudaStream_t s) {
+  const int nc = (int)b->cfgs.size();
+  for (int it = 0; it < kBodyIters64; ++it) {
+    BCK((launch_mdagm_batch<double, MODE_CGDIR>(b->d_cgdir, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
+    BCK(launch_cg_update_batch(b->d_upd, b->d_ublocks, b->d_unblocks, b->total_ublocks, s));
+  }
+  BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_loop, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
+  BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_RESTART, 0.0, 0, GATE_REC, s));
+  return HQMC_OK;
+}
+
+int batch_graph(hqmc_batch* b) {
+  if (b->exec) return HQMC_OK;
+  cudaGraph_t graph = nullptr;
+  BCK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return bfail(b, HQMC_ECUDA, "conditional graph node: %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  BCK(cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = batch_body(b, b->cap);
+  if (rc == HQMC_OK) {
+    cudaError_t le = launch_loop_condition_batch(b->d_states, (int)b->cfgs.size(), handle, b->cap);
+    if (le != cudaSuccess) rc = bfail(b, HQMC_ECUDA, "loop condition: %s", cudaGetErrorString(le));
+  }
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(b->cap, &captured);
+  if (rc == HQMC_OK && e != cudaSuccess) rc = bfail(b, HQMC_ECUDA, "end capture: %s", cudaGetErrorString(e));
+  if (rc == HQMC_OK) {
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (e != cudaSuccess) rc = bfail(b, HQMC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(graph);
+  if (rc != HQMC_OK) cudaGetLastError();
+  b->body_kernels = 2 * kBodyIters64 + 3;
+  return rc;
+}
+
+// CG on every chain (links already built); infos[c] filled; returns the worst status.
+int batch_solve(hqmc_batch* b, const double2* const* phi, double2* const* x, double tol, int maxit,
+                hqmc_solve_info* infos, cudaStream_t s) {
+  const int nc = (int)b->cfgs.size();
+  int rc = batch_descriptors(b, phi, x, s);
+  if (rc != HQMC_OK) return rc;
+  BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_start, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
+  BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_START, tol, maxit, GATE_ALWAYS, s));
+  b->launches += 2;
+  if ((rc = batch_graph(b)) != HQMC_OK) return rc;
+  BCK(cudaGraphLaunch(b->exec, s));
+  int worst = HQMC_OK;
+  int max_loops = 0;
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    BRET(read_state(cfg, s), cfg);
+    max_loops = std::max(max_loops, cfg->st_h->loops);
+  }
+  b->launches += (long long)max_loops * (b->body_kernels + 1);
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    const CgState st = *cfg->st_h;
+    int status = HQMC_OK;
+    if (st.bb == 0.0) {
+      BCK(cudaMemsetAsync(x[c], 0, sizeof(double2) * cfg->n, s));
+      cfg->report_h[0] = 0.0;
+    } else if (st.done != CG_CONVERGED) {
+      status = st.done == CG_MAXIT ? HQMC_ENOTCONV : st.done == CG_BREAKDOWN ? HQMC_EBREAKDOWN : HQMC_ENONFINITE;
+      BRET(residual(cfg, phi[c], x[c], cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s), cfg);
+      BRET(read_state(cfg, s), cfg);
+    }
+    hqmc_solve_info inf{};
+    inf.status = status;
+    inf.iterations = st.k;
+    inf.true_residual = st.bb > 0 ? std::sqrt(cfg->report_h[0] / st.bb) : 0.0;
+    inf.recursive_residual = st.bb > 0 ? std::sqrt(st.rr[st.k & 1] / st.bb) : 0.0;
+    if (status == HQMC_OK && !(inf.true_residual <= tol)) status = inf.status = HQMC_ENOTCONV;
+    if (infos) infos[c] = inf;
+    worst = merge_status(worst, status);
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
+  if (!params || !out || nchains < 1) return HQMC_EINVAL;
+  *out = nullptr;
+  hqmc_batch* b = new (std::nothrow) hqmc_batch();
+  if (!b) return HQMC_ENOMEM;
+  int rc = HQMC_OK;
+  do {
+    int maxV = 0, minC = 8, maxThreads = 64;
+    for (int c = 0; c < nchains; ++c) {
+      hqmc_params p = params[c];
+      p.variant = 1;  // the batched kernel is the generic one; chains stay bit-identical to it
+      p.autotune = 0;
+      hqmc_config* cfg = nullptr;
+      if ((rc = hqmc_make_config(&p, &cfg)) != HQMC_OK) {
+        bfail(b, rc, "chain %d: %s", c, hqmc_strerror(rc));
+        break;
+      }
+      b->cfgs.push_back(cfg);
+      maxV = std::max(maxV, cfg->g.V);
+      minC = std::min(minC, cfg->sl.cluster);
+      maxThreads = std::max(maxThreads, cfg->sl1.threads);
+    }
+    if (rc != HQMC_OK) break;
+    b->C = minC;
+    b->threads = maxThreads;
+    b->smem = (size_t)3 * maxV * sizeof(double2);
+    std::vector<int2> tiles, ublocks;
+    std::vector<int> unblocks;
+    for (int c = 0; c < nchains; ++c) {
+      hqmc_config* cfg = b->cfgs[c];
+      // each chain keeps its own cluster size C (equal to the batch's) and update grid
+      cfg->sl.cluster = b->C;
+      cfg->sl.grid = (cfg->p.Ntau + b->C - 1) / b->C * b->C;
+      cfg->fused64.cluster = b->C;
+      cfg->fused64.grid = cfg->sl.grid;
+      for (int t0 = 0; t0 < cfg->p.Ntau; t0 += b->C) tiles.push_back(make_int2(c, t0));
+      for (int j = 0; j < cfg->ew_grid; ++j) ublocks.push_back(make_int2(c, j));
+      unblocks.push_back(cfg->ew_grid);
+    }
+    b->ntiles = (int)tiles.size();
+    b->total_ublocks = (int)ublocks.size();
+    std::vector<CgState*> states;
+    for (hqmc_config* cfg : b->cfgs) states.push_back(cfg->st);
+    auto dal = [&](void** p, size_t bytes) {
+      if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      return true;
+    };
+    if (!dal((void**)&b->d_cgdir, nchains * sizeof(MdagmArgs<double>)) ||
+        !dal((void**)&b->d_resid_start, nchains * sizeof(MdagmArgs<double>)) ||
+        !dal((void**)&b->d_resid_loop, nchains * sizeof(MdagmArgs<double>)) ||
+        !dal((void**)&b->d_upd, nchains * sizeof(UpdArgs<double>)) ||
+        !dal((void**)&b->d_fin, nchains * sizeof(FinArgs)) || !dal((void**)&b->d_tiles, tiles.size() * sizeof(int2)) ||
+        !dal((void**)&b->d_ublocks, ublocks.size() * sizeof(int2)) ||
+        !dal((void**)&b->d_unblocks, unblocks.size() * sizeof(int)) ||
+        !dal((void**)&b->d_states, states.size() * sizeof(CgState*))) {
+      rc = bfail(b, HQMC_ENOMEM, "batch tables");
+      break;
+    }
+    b->stage_bytes = nchains * (3 * sizeof(MdagmArgs<double>) + sizeof(UpdArgs<double>) + sizeof(FinArgs));
+    if (cudaMallocHost(&b->h_stage, b->stage_bytes) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      rc = bfail(b, HQMC_ENOMEM, "batch staging");
+      break;
+    }
+    if (cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_ublocks, ublocks.data(), ublocks.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_unblocks, unblocks.data(), unblocks.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_states, states.data(), states.size() * sizeof(CgState*), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = bfail(b, HQMC_ECUDA, "batch table upload");
+      break;
+    }
+  } while (0);
+  if (rc != HQMC_OK) {
+    const int keep = rc;
+    batch_release(b);
+    delete b;
+    return keep;
+  }
+  *out = b;
+  return HQMC_OK;
+}
+
+int hqmc_free_batch(hqmc_batch* b) {
+  if (!b) return HQMC_OK;
+  cudaDeviceSynchronize();
+  batch_release(b);
+  delete b;
+  return HQMC_OK;
+}
+
+const char* hqmc_batch_last_error(const hqmc_batch* b) { return b ? b->err : "no batch"; }
+
+long long hqmc_batch_launch_count(const hqmc_batch* b) {
+  if (!b) return 0;
+  long long n = b->launches;
+  for (const hqmc_config* c : b->cfgs) n += c->launches;
+  return n;
+}
+
+int hqmc_batch_cg_solve(hqmc_batch* b, const double* const* theta, const void* const* phi, void* const* x, double tol,
+                        int maxit, hqmc_solve_info* infos, void* stream) {
+  if (!b || !theta || !phi || !x) return HQMC_EINVAL;
+  if (!(tol > 0) || maxit < 0) return bfail(b, HQMC_EINVAL, "tol must be > 0 and maxit >= 0");
+  const int nc = (int)b->cfgs.size();
+  for (int c = 0; c < nc; ++c)
+    if (!aligned16(theta[c]) || !aligned16(phi[c]) || !aligned16(x[c]))
+      return bfail(b, HQMC_EINVAL, "chain %d: NULL or misaligned pointer", c);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int c = 0; c < nc; ++c) BRET(links(b->cfgs[c], theta[c], true, false, s), b->cfgs[c]);
+  return batch_solve(b, (const double2* const*)phi, (double2* const*)x, tol, maxit, infos, s);
+}
+
+int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* seeds, uint64_t traj_counter,
+                          int nsteps, const double* dt, double tol, int maxit, hqmc_traj_info* infos, void* stream) {
+  if (!b || !theta || !seeds || !dt) return HQMC_EINVAL;
+  if (nsteps < 0 || !(tol > 0) || maxit < 0) return bfail(b, HQMC_EINVAL, "bad step parameters");
+  const int nc = (int)b->cfgs.size();
+  for (int c = 0; c < nc; ++c)
+    if (!aligned16(theta[c]) || !std::isfinite(dt[c])) return bfail(b, HQMC_EINVAL, "chain %d: bad theta or dt", c);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<hqmc_traj_info> ti(nc);
+  std::vector<hqmc_solve_info> si(nc);
+  std::vector<const double2*> eta(nc);
+  std::vector<double2*> X(nc);
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    const long long n = cfg->n;
+    BRET([&]() -> int {
+      LK(1, launch_draw(n, seeds[c], traj_counter, cfg->pm, cfg->Rw, s));
+      philox_uniform_host(seeds[c], traj_counter, &ti[c].u);
+      RET(links(cfg, theta[c], true, false, s));
+      LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, cfg->Rw, cfg->eta, 1, s));
+      LK(2, launch_action_terms(cfg->g, cfg->bp, theta[c], cfg->pm, cfg->Rw, cfg->Rw, cfg->act_grid, cfg->part_act,
+                                cfg->terms, s));
+      CK(cudaMemcpyAsync(cfg->th0, theta[c], 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemsetAsync(cfg->Xw, 0, n * sizeof(double2), s));
+      return HQMC_OK;
+    }(), cfg);
+    eta[c] = cfg->eta;
+    X[c] = cfg->Xw;
+  }
+  int worst = HQMC_OK;
+  auto solve_all = [&]() -> int {
+    const int rc = batch_solve(b, eta.data(), X.data(), tol, maxit, si.data(), s);
+    if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
+    worst = merge_status(worst, rc);
+    for (int c = 0; c < nc; ++c) {
+      ti[c].cg_solves++;
+      ti[c].cg_iterations += si[c].iterations;
+      ti[c].max_true_residual = std::fmax(ti[c].max_true_residual, si[c].true_residual);
+      ti[c].status = merge_status(ti[c].status, si[c].status);
+    }
+    return HQMC_OK;
+  };
+  int rc = solve_all();
+  for (int c = 0; c < nc && rc == HQMC_OK; ++c) BRET(force(b->cfgs[c], theta[c], X[c], b->cfgs[c]->F, b->cfgs[c]->dSf, s), b->cfgs[c]);
+  for (int step = 0; step < nsteps && rc == HQMC_OK; ++step) {
+    for (int c = 0; c < nc; ++c) {
+      hqmc_config* cfg = b->cfgs[c];
+      BRET([&]() -> int {
+        LK(1, launch_kick_drift(2 * cfg->n, cfg->pm, theta[c], cfg->F, dt[c] / 2, dt[c], s));
+        RET(links(cfg, theta[c], true, false, s));
+        return HQMC_OK;
+      }(), cfg);
+    }
+    rc = solve_all();
+    if (rc != HQMC_OK) break;
+    for (int c = 0; c < nc; ++c) {
+      hqmc_config* cfg = b->cfgs[c];
+      BRET(force(cfg, theta[c], X[c], cfg->F, cfg->dSf, s), cfg);
+      BRET([&]() -> int {
+        LK(1, launch_kick(2 * cfg->n, cfg->pm, cfg->F, dt[c] / 2, s));
+        return HQMC_OK;
+      }(), cfg);
+    }
+  }
+  if (rc != HQMC_OK) {
+    for (int c = 0; c < nc; ++c)
+      BCK(cudaMemcpyAsync(theta[c], b->cfgs[c]->th0, 2 * b->cfgs[c]->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BCK(cudaStreamSynchronize(s));
+    return rc;
+  }
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    BRET([&]() -> int {
+      LK(2, launch_action_terms(cfg->g, cfg->bp, theta[c], cfg->pm, cfg->eta, cfg->Xw, cfg->act_grid, cfg->part_act,
+                                cfg->terms + 3, s));
+      CK(cudaMemcpyAsync(cfg->terms_h, cfg->terms, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      return HQMC_OK;
+    }(), cfg);
+  }
+  BCK(cudaStreamSynchronize(s));
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    const double* t = cfg->terms_h;
+    ti[c].H0 = t[0] + t[1] + t[2];
+    ti[c].H1 = t[3] + t[4] + t[5];
+    ti[c].dH = ti[c].H1 - ti[c].H0;
+    ti[c].accepted = std::isfinite(ti[c].dH) && ti[c].u < std::exp(-ti[c].dH);
+    if (!std::isfinite(ti[c].dH)) ti[c].status = merge_status(ti[c].status, HQMC_ENONFINITE);
+    if (!ti[c].accepted)
+      BCK(cudaMemcpyAsync(theta[c], cfg->th0, 2 * cfg->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (infos) infos[c] = ti[c];
+    worst = merge_status(worst, ti[c].status);
+  }
+  BCK(cudaStreamSynchronize(s));
+  return worst;
+}
+
+}  // extern "C"

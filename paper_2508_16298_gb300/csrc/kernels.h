@@ -70,6 +70,12 @@ cudaError_t prepare_mdagm_block(const SliceLaunch& sl);
 int block_thread_cap(int real_bytes, int nby);
 int mdagm_block_max_active_clusters(const SliceLaunch& sl, int real_bytes);
 
+// Fused M^dagger M over many chains in one launch (generic kernel, links from
+// memory): CTA b runs cluster tile b / C = (chain, first slice) of `tiles`.
+template <class R, int MODE>
+cudaError_t launch_mdagm_batch(const MdagmArgs<R>* descs, const int2* tiles, int ntiles, int C, int threads,
+                               size_t smem, cudaStream_t s);
+
 // y = M x or M^dagger x.
 template <class R>
 cudaError_t launch_apply_M(const SliceLaunch& sl, R cB, const C2<R>* U, const C2<R>* x, C2<R>* y,
@@ -90,7 +96,43 @@ cudaError_t launch_cg_update(long long n, int grid, void* x, int x_is_double, C2
                              C2<R>* const pbuf[2], const C2<R>* q, const double* part_pq, int n_pq,
                              double* part_rr, CgState* st, cudaStream_t s);
 
+// Arguments of the CG update for one chain.
+template <class R>
+struct UpdArgs {
+  long long n;
+  void* x;
+  int x_is_double;
+  C2<R>* r;
+  C2<R>* p0;
+  C2<R>* p1;
+  const C2<R>* q;
+  const double* part_pq;
+  int n_pq;
+  double* part_rr;
+  CgState* st;
+};
+
+// Arguments of the residual bookkeeping for one chain.
+struct FinArgs {
+  const double* part;
+  int n;
+  double* part_rr_out;
+  int n_rr_out;
+  CgState* st;
+  double* report;
+};
+
+// Batched CG update: descs is a device array of per-chain UpdArgs<double>;
+// blocks[b] = (chain, local block), nblocks[chain].
+cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
+                                   cudaStream_t s);
+
 enum { FIN_START = 0, FIN_RESTART = 1, FIN_RELIABLE = 2, FIN_REPORT = 3 };
+// Batched finalize (START or RESTART), one block per chain; descs: device array of FinArgs.
+cudaError_t launch_resid_finalize_batch(const void* descs, int nchains, int mode, double tol, int maxit, int gate,
+                                        cudaStream_t s);
+cudaError_t launch_loop_condition_batch(CgState* const* states, int nchains, cudaGraphConditionalHandle h,
+                                        cudaStream_t s);
 // Sums the RESID partials into the CG state.
 cudaError_t launch_resid_finalize(const double* part, int n, int mode, double tol, int maxit,
                                   double* part_rr_out, int n_rr_out, CgState* st, double* report,

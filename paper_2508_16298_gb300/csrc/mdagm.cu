@@ -41,8 +41,10 @@ __device__ __forceinline__ C2<R> load_input(const MdagmArgs<R>& a, const C2<R>* 
   return a.x[g];
 }
 
+// Body of the fused kernel for the CTA that owns slice `tau` of the chain
+// described by `a`; `slot` / `nslots` index its reduction partial (slot < nslots).
 template <class R, int MODE, int MB>
-__global__ void __launch_bounds__((SweepThreads<R, MB>::max), 1) mdagm_kernel(const MdagmArgs<R> a) {
+__device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau, const int slot, const int nslots) {
   using T = C2<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int V = a.g.V, N = a.g.Ntau;
@@ -56,7 +58,6 @@ __global__ void __launch_bounds__((SweepThreads<R, MB>::max), 1) mdagm_kernel(co
 
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
-  const int tau = blockIdx.x;
   const bool active = tau < N;
 
   if (MODE == MODE_CGDIR) {
@@ -89,9 +90,9 @@ __global__ void __launch_bounds__((SweepThreads<R, MB>::max), 1) mdagm_kernel(co
         } else {
           beta = rr / st->rr[(k - 1) & 1];
         }
-        if (blockIdx.x == 0 && lane == 0) st->rr[k & 1] = rr;
+        if (slot == 0 && lane == 0) st->rr[k & 1] = rr;
       }
-      if (blockIdx.x == 0 && lane == 0) {
+      if (slot == 0 && lane == 0) {
         if (new_done != CG_RUNNING) st->done = new_done;
         if (!(flags & 1)) st->k2 = k;
       }
@@ -203,13 +204,34 @@ __global__ void __launch_bounds__((SweepThreads<R, MB>::max), 1) mdagm_kernel(co
   }
   if (MODE != MODE_APPLY) {
     const double t0 = block_sum(acc0, red);
-    if (threadIdx.x == 0) a.part_out[blockIdx.x] = t0;
+    if (threadIdx.x == 0) a.part_out[slot] = t0;
     if (MODE == MODE_RESID) {
       const double t1 = block_sum(acc1, red);
-      if (threadIdx.x == 0) a.part_out[gridDim.x + blockIdx.x] = t1;
+      if (threadIdx.x == 0) a.part_out[nslots + slot] = t1;
     }
   }
   cluster_wait();  // keep z_tau alive until the right neighbour has read it
+}
+
+template <class R, int MODE, int MB>
+__global__ void __launch_bounds__((SweepThreads<R, MB>::max), 1) mdagm_kernel(const MdagmArgs<R> a) {
+  mdagm_body<R, MODE, MB>(a, blockIdx.x, blockIdx.x, gridDim.x);
+}
+
+// Many chains in one launch: CTA b serves cluster tile b / C of the tile table,
+// i.e. slice tau0 + (b mod C) of chain `chain`.  Clusters never straddle two
+// chains, so every chain sees exactly the decisions and partial sums of its own
+// single-chain launch with the same cluster size.
+template <class R, int MODE>
+__global__ void __launch_bounds__(1024, 1) mdagm_batch_kernel(const MdagmArgs<R>* __restrict__ descs,
+                                                              const int2* __restrict__ tiles, int C) {
+  __shared__ MdagmArgs<R> a;
+  const int2 tile = tiles[blockIdx.x / C];
+  if (threadIdx.x == 0) a = descs[tile.x];
+  __syncthreads();
+  const int tau = tile.y + (int)(blockIdx.x % C);
+  const int nslots = (a.g.Ntau + C - 1) / C * C;
+  mdagm_body<R, MODE, 0>(a, tau, tau, nslots);
 }
 
 template <class R, int MODE>
@@ -298,6 +320,30 @@ int mdagm_max_active_clusters(const SliceLaunch& sl) {
     default: return -1;
   }
 }
+
+template <class R, int MODE>
+cudaError_t launch_mdagm_batch(const MdagmArgs<R>* descs, const int2* tiles, int ntiles, int C, int threads,
+                               size_t smem, cudaStream_t s) {
+  cudaError_t e = raise_smem_limit(mdagm_batch_kernel<R, MODE>, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntiles * C);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mdagm_batch_kernel<R, MODE>, descs, tiles, C);
+}
+template cudaError_t launch_mdagm_batch<double, MODE_CGDIR>(const MdagmArgs<double>*, const int2*, int, int, int,
+                                                            size_t, cudaStream_t);
+template cudaError_t launch_mdagm_batch<double, MODE_RESID>(const MdagmArgs<double>*, const int2*, int, int, int,
+                                                            size_t, cudaStream_t);
 
 template cudaError_t launch_mdagm<double, MODE_APPLY>(const SliceLaunch&, const MdagmArgs<double>&, cudaStream_t);
 template cudaError_t launch_mdagm<double, MODE_RESID>(const SliceLaunch&, const MdagmArgs<double>&, cudaStream_t);

@@ -55,17 +55,14 @@ cudaError_t launch_links(const Geo& g, const double* theta, double t1, double t2
 
 // ---------------------------------------------------------------------------
 // CG update: alpha = <r,r>/<p,Op>; x += alpha p; r -= alpha Op; partial <r,r>.
+// Body of the CG update for block j of nblocks serving one chain.
 template <class R>
-__global__ void __launch_bounds__(256) cg_update_kernel(long long n, void* x, int x_is_double,
-                                                        C2<R>* __restrict__ r,
-                                                        C2<R>* p0, C2<R>* p1,
-                                                        const C2<R>* __restrict__ q,
-                                                        const double* __restrict__ part_pq, int n_pq,
-                                                        double* __restrict__ part_rr, CgState* st) {
+__device__ __forceinline__ void cg_update_body(const UpdArgs<R>& u, const int j, const int nblocks) {
   __shared__ double red[32];
   __shared__ int s_stop;
   __shared__ double s_alpha;
   __shared__ int s_k;
+  CgState* st = u.st;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     const int done = *(volatile int*)&st->done;
@@ -75,14 +72,14 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, void* x, in
       stop = 1;
     } else {
       const int k = st->k2;
-      const double pq = warp_sum_partials(part_pq, n_pq);
+      const double pq = warp_sum_partials(u.part_pq, u.n_pq);
       const double rr = st->rr[k & 1];
       if (!isfinite(pq) || !(pq > 0.0)) {
         stop = 1;
-        if (blockIdx.x == 0 && lane == 0) st->done = isfinite(pq) ? CG_BREAKDOWN : CG_NONFINITE;
+        if (j == 0 && lane == 0) st->done = isfinite(pq) ? CG_BREAKDOWN : CG_NONFINITE;
       } else {
         alpha = rr / pq;
-        if (blockIdx.x == 0 && lane == 0) {
+        if (j == 0 && lane == 0) {
           st->pq_last = pq;
           st->alpha_last = alpha;
         }
@@ -97,35 +94,55 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, void* x, in
   __syncthreads();
   if (s_stop) return;
   const R alpha = (R)s_alpha;
-  const C2<R>* __restrict__ p = ((s_k + 1) & 1) ? p1 : p0;
+  const C2<R>* __restrict__ p = ((s_k + 1) & 1) ? u.p1 : u.p0;
   double acc = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = j * (long long)blockDim.x + threadIdx.x; i < u.n; i += (long long)nblocks * blockDim.x) {
     const C2<R> pv = p[i];
-    C2<R> rv = caxpy(r[i], -alpha, q[i]);
-    r[i] = rv;
-    if (x_is_double) {
-      double2* xd = reinterpret_cast<double2*>(x);
+    C2<R> rv = caxpy(u.r[i], -alpha, u.q[i]);
+    u.r[i] = rv;
+    if (u.x_is_double) {
+      double2* xd = reinterpret_cast<double2*>(u.x);
       xd[i] = caxpy(xd[i], (double)alpha, make_double2(pv.x, pv.y));
     } else {
-      float2* xf = reinterpret_cast<float2*>(x);
+      float2* xf = reinterpret_cast<float2*>(u.x);
       xf[i] = caxpy(xf[i], (float)alpha, make_float2(pv.x, pv.y));
     }
     acc += cdot_re(rv, rv);
   }
   const double t = block_sum(acc, red);
   if (threadIdx.x == 0) {
-    part_rr[blockIdx.x] = t;
-    if (blockIdx.x == 0) st->k = st->k2 + 1;
+    u.part_rr[j] = t;
+    if (j == 0) st->k = st->k2 + 1;
   }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) cg_update_kernel(const UpdArgs<R> u) {
+  cg_update_body<R>(u, blockIdx.x, gridDim.x);
+}
+
+// Many chains in one launch: block b serves (chain, local block) = blocks[b];
+// each chain keeps the block count and element mapping of its own launch.
+template <class R>
+__global__ void __launch_bounds__(256) cg_update_batch_kernel(const UpdArgs<R>* __restrict__ descs,
+                                                             const int2* __restrict__ blocks,
+                                                             const int* __restrict__ nblocks) {
+  const int2 b = blocks[blockIdx.x];
+  cg_update_body<R>(descs[b.x], b.y, nblocks[b.x]);
 }
 
 template <class R>
 cudaError_t launch_cg_update(long long n, int grid, void* x, int x_is_double, C2<R>* r,
                              C2<R>* const pbuf[2], const C2<R>* q, const double* part_pq, int n_pq,
                              double* part_rr, CgState* st, cudaStream_t s) {
-  cg_update_kernel<R><<<grid, 256, 0, s>>>(n, x, x_is_double, r, pbuf[0], pbuf[1], q, part_pq, n_pq,
-                                           part_rr, st);
+  UpdArgs<R> u{n, x, x_is_double, r, pbuf[0], pbuf[1], q, part_pq, n_pq, part_rr, st};
+  cg_update_kernel<R><<<grid, 256, 0, s>>>(u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
+                                   cudaStream_t s) {
+  cg_update_batch_kernel<double><<<total_blocks, 256, 0, s>>>((const UpdArgs<double>*)descs, blocks, nblocks);
   return cudaGetLastError();
 }
 template cudaError_t launch_cg_update<double>(long long, int, void*, int, double2*, double2* const[2],
@@ -204,6 +221,81 @@ cudaError_t launch_resid_finalize(const double* part, int n, int mode, double to
                                   double* part_rr_out, int n_rr_out, CgState* st, double* report,
                                   int gate, cudaStream_t s) {
   resid_finalize_kernel<<<1, 256, 0, s>>>(part, n, mode, tol, maxit, part_rr_out, n_rr_out, st, report, gate);
+  return cudaGetLastError();
+}
+
+// One block per chain; the same bookkeeping as resid_finalize_kernel.
+__global__ void resid_finalize_batch_kernel(const FinArgs* __restrict__ descs, int mode, double tol, int maxit,
+                                            int gate) {
+  const FinArgs f = descs[blockIdx.x];
+  __shared__ int s_open;
+  if (threadIdx.x == 0) s_open = gate_open(gate, *(volatile int*)&f.st->done);
+  __syncthreads();
+  if (!s_open) return;
+  const double rr = warp_sum_partials(f.part, f.n);
+  const double bb = warp_sum_partials(f.part + f.n, f.n);
+  if (threadIdx.x != 0) return;
+  CgState* st = f.st;
+  if (f.report) {
+    f.report[0] = rr;
+    f.report[1] = bb;
+  }
+  if (mode == FIN_START) {
+    st->bb = bb;
+    st->tol2bb = tol * tol * bb;
+    st->k = 0;
+    st->k2 = 0;
+    st->seg_start = 0;
+    st->maxit = maxit;
+    st->rr[0] = rr;
+    st->rr[1] = rr;
+    st->pq_last = 0.0;
+    st->alpha_last = 0.0;
+    st->loops = 0;
+    st->n_rel = 0;
+    st->loop_cap = (maxit > (1 << 29) ? (1 << 30) : 2 * maxit) + 64;
+    if (!isfinite(rr) || !isfinite(bb)) st->done = CG_NONFINITE;
+    else if (bb == 0.0 || rr <= st->tol2bb) st->done = CG_CONVERGED;
+    else if (maxit <= 0) st->done = CG_MAXIT;
+    else st->done = CG_RUNNING;
+  } else if (mode == FIN_RESTART) {
+    const int k = st->k;
+    st->seg_start = k;
+    st->rr[k & 1] = rr;
+    if (!isfinite(rr)) st->done = CG_NONFINITE;
+    else if (rr <= st->tol2bb) st->done = CG_CONVERGED;
+    else if (k >= st->maxit) st->done = CG_MAXIT;
+    else st->done = CG_RUNNING;
+  }
+}
+
+cudaError_t launch_resid_finalize_batch(const void* descs, int nchains, int mode, double tol, int maxit, int gate,
+                                        cudaStream_t s) {
+  resid_finalize_batch_kernel<<<nchains, 32, 0, s>>>((const FinArgs*)descs, mode, tol, maxit, gate);
+  return cudaGetLastError();
+}
+
+// WHILE condition over many chains: continue while any chain is still active.
+__global__ void loop_condition_batch_kernel(CgState* const* states, int nchains, cudaGraphConditionalHandle h) {
+  bool cont = false;
+  for (int c = 0; c < nchains; ++c) {
+    CgState* st = states[c];
+    const int d = st->done;
+    const int loops = st->loops + 1;
+    st->loops = loops;
+    bool run = d == CG_RUNNING || d == CG_REC_CONVERGED;
+    if (run && loops >= st->loop_cap) {
+      st->done = CG_MAXIT;
+      run = false;
+    }
+    cont = cont || run;
+  }
+  cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+cudaError_t launch_loop_condition_batch(CgState* const* states, int nchains, cudaGraphConditionalHandle h,
+                                        cudaStream_t s) {
+  loop_condition_batch_kernel<<<1, 1, 0, s>>>(states, nchains, h);
   return cudaGetLastError();
 }
 

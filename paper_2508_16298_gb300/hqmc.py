@@ -35,7 +35,8 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_launch_count", "hqmc_get_launch_shape",
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_cg_solve", "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
-           "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static")
+           "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
+           "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory")
 
 
 class Params(ctypes.Structure):
@@ -87,6 +88,14 @@ _sig = {
     "hqmc_get_timing": ([_vp, _i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _i),
     "hqmc_probe_fp64_rate": ([_vp, ctypes.POINTER(ctypes.c_double)], _i),
     "hqmc_apply_MdagM_static": ([ctypes.POINTER(Params), _vp, _vp, _vp, _vp], _i),
+    "hqmc_make_batch": ([ctypes.POINTER(Params), _i, ctypes.POINTER(_vp)], _i),
+    "hqmc_free_batch": ([_vp], _i),
+    "hqmc_batch_last_error": ([_vp], ctypes.c_char_p),
+    "hqmc_batch_launch_count": ([_vp], ctypes.c_longlong),
+    "hqmc_batch_cg_solve": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
+                             ctypes.POINTER(SolveInfo), _vp], _i),
+    "hqmc_batch_trajectory": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), _u64, _i,
+                               ctypes.POINTER(ctypes.c_double), _d, _i, ctypes.POINTER(TrajInfo), _vp], _i),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -339,3 +348,65 @@ def apply_MdagM_static(L: int, Ntau: int, theta, x, y=None, dtau: float = 0.1, t
     if rc != OK:
         raise HQMCError(rc, f"static apply at L={L} Ntau={Ntau}")
     return y
+
+
+class Batch:
+    """Independent chains of possibly different lattices driven together (hqmc_make_batch)."""
+
+    def __init__(self, lattices, dtau: float = 0.1, t: float = 1.0, J: float = 1.0, K: float = 0.0,
+                 noncompact: bool = False):
+        self.lattices = [(int(L), int(N)) for L, N in lattices]
+        n = len(self.lattices)
+        arr = (Params * n)(*[Params(L, N, dtau, t, J, K, ACTION_NONCOMPACT if noncompact else ACTION_COMPACT,
+                                    0, 0, 1) for L, N in self.lattices])
+        h = _vp()
+        rc = _lib.hqmc_make_batch(arr, n, ctypes.byref(h))
+        if rc != OK:
+            raise HQMCError(rc, "batch creation")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.hqmc_free_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def launch_count(self) -> int:
+        return int(_lib.hqmc_batch_launch_count(self._h))
+
+    def _check(self, rc, allow=(OK,)):
+        if rc not in allow:
+            raise HQMCError(rc, (_lib.hqmc_batch_last_error(self._h) or b"").decode())
+
+    def _ptrs(self, tensors):
+        return (_vp * len(tensors))(*[t.data_ptr() for t in tensors])
+
+    def cg_solve(self, thetas, phis, xs=None, tol: float = 1e-8, maxit: int = 100000, raise_on_fail: bool = True):
+        n = len(self.lattices)
+        xs = [torch.zeros_like(p) for p in phis] if xs is None else xs
+        infos = (SolveInfo * n)()
+        rc = _lib.hqmc_batch_cg_solve(self._h, self._ptrs(thetas), self._ptrs(phis), self._ptrs(xs), tol, maxit,
+                                      infos, _stream())
+        if raise_on_fail:
+            self._check(rc)
+        return xs, [i.as_dict() for i in infos]
+
+    def trajectory(self, thetas, seeds, traj_counter: int, nsteps: int, dts, tol: float = 1e-8,
+                   maxit: int = 100000):
+        n = len(self.lattices)
+        infos = (TrajInfo * n)()
+        rc = _lib.hqmc_batch_trajectory(self._h, self._ptrs(thetas), (ctypes.c_uint64 * n)(*seeds), traj_counter,
+                                        nsteps, (ctypes.c_double * n)(*dts), tol, maxit, infos, _stream())
+        self._check(rc, allow=(OK, ENOTCONV))
+        return [i.as_dict() for i in infos]
