@@ -1139,6 +1139,7 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
     a.n_part_in = cfg->ew_grid;
     a.part_out = cfg->part_mdagm;
     a.st = cfg->st;
+    a.teff = cfg->fused64.threads;  // this chain's own block size: identical reduction order
     cgdir[c] = a;
     MdagmArgs<double> r = mdagm_args<double, MODE_RESID>(cfg);
     r.U = cfg->U64;
@@ -1148,6 +1149,7 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
     r.r_out_fp32 = 0;
     r.part_out = cfg->part_resid;
     r.st = cfg->st;
+    r.teff = cfg->sl.threads;
     r.gate = GATE_ALWAYS;
     rs[c] = r;
     r.gate = GATE_REC;
@@ -1281,7 +1283,7 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
       b->cfgs.push_back(cfg);
       maxV = std::max(maxV, cfg->g.V);
       minC = std::min(minC, cfg->sl.cluster);
-      maxThreads = std::max(maxThreads, cfg->sl1.threads);
+      maxThreads = std::max(maxThreads, std::max(cfg->sl.threads, cfg->fused64.threads));
     }
     if (rc != HQMC_OK) break;
     b->C = minC;

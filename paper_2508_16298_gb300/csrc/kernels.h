@@ -51,6 +51,8 @@ struct MdagmArgs {
   int gate;                // RESID: GATE_* condition on st->done (GATE_ALWAYS needs no st)
   const float2* th32;      // register-blocked FP32 kernel: (theta_x, theta_y) per site, wrapped to [-pi, pi)
   double t1, t2;           // tanh(a), tanh(a/2)
+  int teff;                // generic kernel: threads that take part in the site loops (0: the whole block);
+                           // a batch sets each chain's own block size so sums group sites as in its own launch
 };
 
 // Fused M^dagger M (three modes).

@@ -121,6 +121,8 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
     p_new = (s_k & 1) ? a.pbuf[0] : a.pbuf[1];
   }
   const R cB = a.cB;
+  const int NT = a.teff > 0 ? a.teff : (int)blockDim.x;  // stride of the site loops
+  const int t0 = (int)threadIdx.x < NT ? (int)threadIdx.x : V;  // threads beyond NT take no sites
   const int taum = (tau == 0) ? N - 1 : tau - 1;
   const int taup = (tau == N - 1) ? 0 : tau + 1;
   const size_t base = (size_t)tau * V;
@@ -134,7 +136,7 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
     if constexpr (MB > 0) load_links(ij, Ut, uu);
     // rank 0 prefetches its halo input x_{tau-1}, the others x_{tau+1}
     const size_t bpre = (size_t)(rank == 0 ? taum : taup) * V;
-    for (int s = threadIdx.x; s < V; s += blockDim.x) {
+    for (int s = t0; s < V; s += NT) {
       const T v = load_input<R, MODE>(a, p_old, base + s, beta, first);
       Z[s] = v;
       Y[s] = v;
@@ -167,12 +169,12 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
     const R sigp = (tau == N - 1) ? R(-1) : R(1);
     if (rank == 0) {
       const size_t bp = (size_t)taup * V;
-      for (int s = threadIdx.x; s < V; s += blockDim.x) {
+      for (int s = t0; s < V; s += NT) {
         Y[s] = caxpy(Y[s], -sig * cB, W[s]);
         W[s] = caxpy(cscale(cB, Z[s]), -sigp, load_input<R, MODE>(a, p_old, bp + s, beta, first));
       }
     } else {
-      for (int s = threadIdx.x; s < V; s += blockDim.x) {
+      for (int s = t0; s < V; s += NT) {
         Y[s] = caxpy(Y[s], -sig * cB, Zprev[s]);
         W[s] = caxpy(cscale(cB, Z[s]), -sigp, W[s]);
       }
@@ -183,7 +185,7 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
     __syncthreads();
     if constexpr (MB > 0) sweep(W, ij, uu);
     else apply_P(a.g, W, Ut);
-    for (int s = threadIdx.x; s < V; s += blockDim.x) {
+    for (int s = t0; s < V; s += NT) {
       T q = caxpy(Y[s], cB, W[s]);
       if (MODE == MODE_APPLY) {
         a.y[base + s] = q;
