@@ -49,6 +49,10 @@ WORKLOADS = {
     "hmc_mixed_L48_Nt480": dict(L=48, Ntau=480, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.00018, tol=1e-8,
                                 solver="mixed", seed=1, start="cold"),
 }
+# batched chains: 32 lattices, L in {12, 16, 20, 24} x 8, Ntau = 10 L, one trajectory of every chain per step
+BATCH_LATTICES = [(L, 10 * L) for L in (12, 16, 20, 24) for _ in range(8)]
+WORKLOADS["batched_32chains_L12-24"] = dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.0005, tol=1e-8,
+                                            solver="cg64", seed=100, start="cold", batched=True)
 DEFAULT_WORKLOAD = "hmc_fp64_L24_Nt240"
 
 # Algorithmic work of one launch of the fused M^dagger M kernel in CG mode, per site:
@@ -146,7 +150,8 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
 
 # CG iterations per trajectory used to scale oracle samples when no GPU run is
 # available (the reference arm); measured on the GPU with the same algorithm.
-ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 16500.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 40000.0}
+ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 11000.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 40000.0,
+                     "batched_32chains_L12-24": 11000.0}
 
 
 def run_reference(args, wl_name, wl, rank, world):
@@ -331,6 +336,70 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, wl_name, wl, rank, world, local_rank):
+    """All chains advance one trajectory per step through hqmc_batch_trajectory; the
+    same chains are then run one after another with hqmc_trajectory for comparison."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_16298_gb300 import hqmc, inputs
+
+    torch.cuda.set_device(local_rank)
+    lats = BATCH_LATTICES
+    seeds = [wl["seed"] + i + 1000 * rank for i in range(len(lats))]
+    # dt scaled with the volume as in the single-chain workload (|dH| ~ V dt^2)
+    dts = [wl["dt"] * ((24 * 24 * 240) / (L * L * N)) ** 0.5 for L, N in lats]
+    thetas = [torch.from_numpy(inputs.theta_ordered(L, N, s, tau_walk=0.0)).cuda() for (L, N), s in zip(lats, seeds)]
+    stream = torch.cuda.current_stream()
+    with hqmc.Batch(lats) as b:
+        for k in range(args.warmup):
+            b.trajectory(thetas, seeds, k, wl["nsteps"], dts, tol=wl["tol"])
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = b.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = []
+        for k in range(args.steps):
+            infos.append(b.trajectory(thetas, seeds, args.warmup + k, wl["nsteps"], dts, tol=wl["tol"]))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = b.launch_count() - l0
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * len(lats) / (ms / 1e3)
+    # the same chains, one trajectory each, run one after another
+    seq_ms = 0.0
+    for (L, N), s, dt, th in zip(lats, seeds, dts, thetas):
+        with hqmc.Config(L, N, variant=1) as cfg:
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hqmc.trajectory(cfg, th.clone(), seed=s, traj_counter=10 ** 6, nsteps=wl["nsteps"], dt=dt, tol=wl["tol"])
+            z.record(stream)
+            torch.cuda.synchronize()
+            seq_ms += a.elapsed_time(z)
+    if rank != 0:
+        return
+    flat = [i for step in infos for i in step]
+    line = {"metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl_name, "chains": len(lats), "lattices": "L in {12,16,20,24} x 8, Ntau = 10 L",
+                       "n_leapfrog": wl["nsteps"], "dt": "0.0005 * sqrt(138240 / sites)", "cg_tol": wl["tol"],
+                       "solver": "cg64 (batched: one fused launch + one update launch per CG iteration)"},
+            "gpu_launches": int(launches),
+            "sequential_traj_per_s": len(lats) / (seq_ms / 1e3),
+            "batched_over_sequential": value / (len(lats) / (seq_ms / 1e3)),
+            "acceptance": sum(i["accepted"] for i in flat) / len(flat),
+            "cg_iterations_per_traj": sum(i["cg_iterations"] for i in flat) / len(flat)}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(wl):
     """A short, fixed sequence for ncu captures: three fused M^dagger M applies and
     a 40-iteration CG solve at the workload's size (no JSON output)."""
@@ -377,6 +446,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.impl == "reference":
         run_reference(args, args.workload, wl, rank, world)
+    elif wl.get("batched"):
+        run_batched(args, args.workload, wl, rank, world, local_rank)
     else:
         run_ours(args, args.workload, wl, rank, world, local_rank)
     if world > 1 and args.impl == "ours":
