@@ -60,9 +60,13 @@ enum { HQMC_ACTION_COMPACT = 0, HQMC_ACTION_NONCOMPACT = 1 };
 
 /* Solver selection for hqmc_cg_solve / hqmc_leapfrog / hqmc_trajectory. */
 enum {
-    HQMC_SOLVER_CG64 = 0,  /* plain CG, every vector and reduction in FP64 */
-    HQMC_SOLVER_MIXED = 1  /* CG with M^dagger M in FP32 (complex float) and FP64 reliable
-                              residual updates every params.reliable_interval iterations */
+    HQMC_SOLVER_CG64 = 0,    /* plain CG, every vector and reduction in FP64 */
+    HQMC_SOLVER_MIXED = 1,   /* CG with M^dagger M in FP32 (complex float) and FP64 reliable
+                                residual updates every params.reliable_interval iterations */
+    HQMC_SOLVER_LEARNED = 2  /* the attached net (hqmc_set_preconditioner) corrects the initial
+                                guess, x <- x + K(theta)(phi - O x), kept only if it lowers the
+                                FP64 residual; then the mixed solver, whose FP64 true residual
+                                judges convergence */
 };
 
 /* Model and lattice (Results "Model"; Methods "Model and partition function"). */
@@ -96,7 +100,8 @@ typedef struct hqmc_solve_info {
     int fp64_fallback;         /* mixed solver: 1 if FP32 breakdowns, or a true residual cut
                                   by less than 10x over four reliable updates, handed the
                                   rest of the solve to the FP64 recurrence */
-    int reserved;
+    int net_guess_used;        /* learned solver: 1 if the net's correction of the initial
+                                  guess lowered the residual and was kept */
 } hqmc_solve_info;
 
 typedef struct hqmc_traj_info {
@@ -274,6 +279,36 @@ HQMC_API int hqmc_batch_cg_solve(hqmc_batch* b, const double* const* theta, cons
 HQMC_API int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* seeds, uint64_t traj_counter,
                                    int nsteps, const double* dt, double tol, int maxit, hqmc_traj_info* infos,
                                    void* stream);
+
+/* ---- learned preconditioner (spec extension; not in the paper) ----- */
+
+/* A 3D periodic convolution network on the space-time lattice: 4 layers with
+ * 1 -> 16 -> 16 -> 16 -> 1 complex channels; each layer is a 7-point stencil
+ * (centre, +-x, +-y, +-tau) whose neighbour values are parallel-transported by
+ * e^{i theta} (antiperiodic sign across tau = 0) and mixed by real 16x16
+ * matrices.  It is gauge covariant and linear in its input, K(theta) r.
+ * Weights are BF16 (FP32 master copy for training); arithmetic is FP32.
+ * Weight layout per layer: [7][c_out][c_in], layers in order, 3808 floats. */
+typedef struct hqmc_net hqmc_net;
+
+/* Net on the current device, initialised near the identity map (seeded). */
+HQMC_API int hqmc_net_create(uint64_t seed, hqmc_net** out);
+HQMC_API int hqmc_net_free(hqmc_net* net);
+HQMC_API int hqmc_net_num_weights(const hqmc_net* net);
+/* FP32 master weights to / from host memory (n == hqmc_net_num_weights). */
+HQMC_API int hqmc_net_get_weights(const hqmc_net* net, float* host, int n);
+HQMC_API int hqmc_net_set_weights(hqmc_net* net, const float* host, int n);
+/* z = K(theta) r (complex double in and out; computed in FP32).  The first net
+ * call on a config allocates its activation workspace (5 + 32 channel fields). */
+HQMC_API int hqmc_net_apply(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* r, void* z,
+                            void* stream);
+/* One Adam step (lr; betas 0.9, 0.999) on loss = ||K(theta) phi - x||^2 / ||x||^2
+ * for one (theta, phi, x) triple with x = (M^dagger M)^{-1} phi; *loss_host
+ * (nullable) receives the loss before the step (then the call synchronises). */
+HQMC_API int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* phi,
+                                 const void* x, double lr, double* loss_host, void* stream);
+/* Attaches (or with NULL detaches) the net used by HQMC_SOLVER_LEARNED. */
+HQMC_API int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net);
 
 /* ---- instrumentation ---------------------------------------------------- */
 

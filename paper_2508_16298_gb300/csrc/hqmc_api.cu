@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "hqmc.h"
 #include "kernels.h"
 
@@ -72,6 +74,13 @@ struct hqmc_config {
   CgState* st_h = nullptr;
   double* terms_h = nullptr;
   double* report_h = nullptr;
+
+  // learned preconditioner: attached net and its lazily allocated workspace
+  struct hqmc_net* net = nullptr;
+  float2* net_h[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // activations (1, 16, 16, 16, 1 channels)
+  float2* net_d[2] = {nullptr, nullptr};                               // back-propagated gradients (16 channels)
+  double* net_part = nullptr;                                          // weight-gradient and loss partials
+  double* net_scal = nullptr;                                          // device scalars (norms)
 
   int timing = 0;
   long long launches = 0;  // kernels enqueued by this config
@@ -191,10 +200,11 @@ int check_device(hqmc_config* cfg) {
 // link table (generic kernel) or theta as float (register-blocked kernel).
 // need32: tables for the FP32 fused kernel; table32: the float link table itself
 // (the FP32 apply of M reads it whatever the fused kernel uses).
-int links(hqmc_config* cfg, const double* theta, bool need64, bool need32, cudaStream_t s, bool table32 = false) {
+int links(hqmc_config* cfg, const double* theta, bool need64, bool need32, cudaStream_t s, bool table32 = false,
+          bool theta32 = false) {
   const bool blk32 = need32 && cfg->fused32.nby > 0;
   LK(1, launch_links(cfg->g, theta, cfg->t1, cfg->t2, need64 ? cfg->U64 : nullptr,
-                     ((need32 && !blk32) || table32) ? cfg->U32 : nullptr, blk32 ? cfg->th32 : nullptr, s));
+                     ((need32 && !blk32) || table32) ? cfg->U32 : nullptr, (blk32 || theta32) ? cfg->th32 : nullptr, s));
   return HQMC_OK;
 }
 
@@ -271,6 +281,58 @@ int read_state(hqmc_config* cfg, cudaStream_t s) {
   CK(cudaMemcpyAsync(cfg->st_h, cfg->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(cfg->report_h, cfg->report, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return HQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned preconditioner (see net.cu): 4 layers, channels 1 -> 16 -> 16 -> 16 -> 1.
+
+constexpr int kNetLayers = 4;
+constexpr int kNetCh = 16;
+constexpr int kNetChunks = 64;  // site chunks of the weight-gradient reduction
+
+}  // namespace
+
+struct hqmc_net {
+  int cin[kNetLayers] = {1, kNetCh, kNetCh, kNetCh};
+  int cout[kNetLayers] = {kNetCh, kNetCh, kNetCh, 1};
+  int off[kNetLayers + 1] = {0, 0, 0, 0, 0};
+  int total = 0;
+  float* w = nullptr;      // FP32 master weights (device)
+  float* m = nullptr;      // Adam moments
+  float* v = nullptr;
+  void* wb = nullptr;      // BF16 weights used by the layers
+  void* wt = nullptr;      // BF16 adjoint weights (backward stencil)
+  int steps = 0;
+  int device = 0;
+};
+
+namespace {
+
+int net_workspace(hqmc_config* cfg) {
+  if (cfg->net_h[0]) return HQMC_OK;
+  const size_t n = cfg->n;
+  const int ch[5] = {1, kNetCh, kNetCh, kNetCh, 1};
+  for (int l = 0; l < 5; ++l) RET(dalloc(cfg, &cfg->net_h[l], n * ch[l]));
+  RET(dalloc(cfg, &cfg->net_d[0], n * kNetCh));
+  RET(dalloc(cfg, &cfg->net_d[1], n * kNetCh));
+  RET(dalloc(cfg, &cfg->net_part, (size_t)kNetChunks * 7 * kNetCh * kNetCh + 4096));
+  RET(dalloc(cfg, &cfg->net_scal, 8));
+  return HQMC_OK;
+}
+
+// z = K(theta) r for complex-double r, z; the float theta table must be current.
+int net_forward(hqmc_config* cfg, hqmc_net* net, const double2* r, double2* z, cudaStream_t s) {
+  LK(1, launch_net_convert(r, cfg->net_h[0], 1, 1.0, cfg->n, s));
+  for (int l = 0; l < kNetLayers; ++l)
+    LK(1, launch_net_layer(cfg->g, cfg->th32, (const char*)net->wb + 2 * (size_t)net->off[l], net->cin[l], net->cout[l],
+                           cfg->net_h[l], cfg->net_h[l + 1], s));
+  if (z) LK(1, launch_net_convert(cfg->net_h[kNetLayers], z, 0, 1.0, cfg->n, s));
+  return HQMC_OK;
+}
+
+int theta_float(hqmc_config* cfg, const double* theta, cudaStream_t s) {
+  LK(1, launch_links(cfg->g, theta, cfg->t1, cfg->t2, nullptr, nullptr, cfg->th32, s));
   return HQMC_OK;
 }
 
@@ -381,8 +443,29 @@ int run_loop(hqmc_config* cfg, int solver, const double2* phi, double2* x, int* 
 }
 
 // CG on (M^dagger M) x = phi with the link tables already built for theta.
+// HQMC_SOLVER_LEARNED: x <- x + K(theta)(phi - O x) from the attached net, kept
+// only if it lowers the FP64 residual, then the mixed solver (plain CG with its
+// FP64 true residual stays the judge and the fallback).
 int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
           hqmc_solve_info* info, cudaStream_t s) {
+  int net_used = 0;
+  if (solver == HQMC_SOLVER_LEARNED) {
+    // candidate x1 = x + K r0 with r0 = phi - O x; the CG workspace is free here
+    RET(net_workspace(cfg));
+    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
+    RET(read_state(cfg, s));
+    const double rr0 = cfg->report_h[0];
+    RET(net_forward(cfg, cfg->net, cfg->vscratch, cfg->p64[1], s));                       // z = K r0
+    CK(cudaMemcpyAsync(cfg->p64[0], x, sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));  // keep x
+    LK(1, launch_kick(2 * cfg->n, (double*)x, (const double*)cfg->p64[1], 1.0, s));          // x += z
+    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
+    RET(read_state(cfg, s));
+    if (cfg->report_h[0] < rr0)
+      net_used = 1;
+    else
+      CK(cudaMemcpyAsync(x, cfg->p64[0], sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));
+    solver = HQMC_SOLVER_MIXED;
+  }
   const bool mixed = solver == HQMC_SOLVER_MIXED;
   hqmc_solve_info inf{};
   RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, GATE_ALWAYS, s));
@@ -422,6 +505,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   }
   const CgState& st = *cfg->st_h;
   inf.reliable_updates = mixed ? st.loops : 0;
+  inf.net_guess_used = net_used;
   inf.status = status;
   inf.iterations = st.k;
   inf.true_residual = st.bb > 0 ? std::sqrt(cfg->report_h[0] / st.bb) : 0.0;
@@ -430,6 +514,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   if (info) *info = inf;
   return status;
 }
+
 
 int force(hqmc_config* cfg, const double* theta, const double2* X, double* F, double* dSf, cudaStream_t s) {
   int slot;
@@ -444,11 +529,12 @@ int merge_status(int a, int b) { return a != HQMC_OK ? a : b; }
 
 int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, double2* X, int nsteps, double dt,
              double tol, int maxit, int solver, hqmc_traj_info* ti, cudaStream_t s) {
-  const bool mixed = solver == HQMC_SOLVER_MIXED;
+  const bool mixed = solver != HQMC_SOLVER_CG64;
+  const bool learned = solver == HQMC_SOLVER_LEARNED;
   const long long nb = 2 * cfg->n;
   hqmc_solve_info si;
   int status = HQMC_OK;
-  RET(links(cfg, theta, true, mixed, s));
+  RET(links(cfg, theta, true, mixed, s, false, learned));
   int rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
   if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
   status = merge_status(status, rc);
@@ -458,7 +544,7 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
   RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
   for (int n = 0; n < nsteps; ++n) {
     LK(1, launch_kick_drift(nb, p, theta, cfg->F, dt / 2, dt, s));
-    RET(links(cfg, theta, true, mixed, s));
+    RET(links(cfg, theta, true, mixed, s, false, learned));
     rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
     if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
     status = merge_status(status, rc);
@@ -473,8 +559,10 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
 }
 
 int check_solver(hqmc_config* cfg, int solver) {
-  if (solver != HQMC_SOLVER_CG64 && solver != HQMC_SOLVER_MIXED)
+  if (solver != HQMC_SOLVER_CG64 && solver != HQMC_SOLVER_MIXED && solver != HQMC_SOLVER_LEARNED)
     return fail(cfg, HQMC_EINVAL, "unknown solver %d", solver);
+  if (solver == HQMC_SOLVER_LEARNED && !cfg->net)
+    return fail(cfg, HQMC_EINVAL, "the learned solver needs a net attached with hqmc_set_preconditioner");
   return HQMC_OK;
 }
 
@@ -869,7 +957,7 @@ int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* 
   RET(check_solver(cfg, solver));
   RET(check_device(cfg));
   cudaStream_t s = (cudaStream_t)stream;
-  RET(links(cfg, theta, true, solver == HQMC_SOLVER_MIXED, s));
+  RET(links(cfg, theta, true, solver != HQMC_SOLVER_CG64, s, false, solver == HQMC_SOLVER_LEARNED));
   return solve(cfg, (const double2*)phi, (double2*)x, tol, maxit, solver, info, s);
 }
 
@@ -1474,6 +1562,162 @@ int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* s
   }
   BCK(cudaStreamSynchronize(s));
   return worst;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Learned preconditioner API.
+
+namespace {
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int net_upload(hqmc_net* net, const float* host) {
+  std::vector<__nv_bfloat16> hb(net->total);
+  for (int e = 0; e < net->total; ++e) hb[e] = __float2bfloat16(host[e]);
+  if (cudaMemcpy(net->w, host, net->total * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(net->wb, hb.data(), net->total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(net->m, 0, net->total * sizeof(float)) != cudaSuccess ||
+      cudaMemset(net->v, 0, net->total * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return HQMC_ECUDA;
+  }
+  net->steps = 0;
+  return HQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hqmc_net_create(uint64_t seed, hqmc_net** out) {
+  if (!out) return HQMC_EINVAL;
+  *out = nullptr;
+  hqmc_net* net = new (std::nothrow) hqmc_net();
+  if (!net) return HQMC_ENOMEM;
+  cudaGetDevice(&net->device);
+  for (int l = 0; l < kNetLayers; ++l) net->off[l + 1] = net->off[l] + 7 * net->cin[l] * net->cout[l];
+  net->total = net->off[kNetLayers];
+  const size_t n = net->total;
+  if (cudaMalloc((void**)&net->w, n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&net->m, n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&net->v, n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&net->wb, n * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc(&net->wt, n * sizeof(__nv_bfloat16)) != cudaSuccess) {
+    cudaGetLastError();
+    hqmc_net_free(net);
+    return HQMC_ENOMEM;
+  }
+  // start from the identity map r -> r (channel 0 carried by the centre taps)
+  // plus a small random perturbation of every weight
+  std::vector<float> w(n);
+  uint64_t st = seed ^ 0x5DEECE66Dull;
+  for (size_t e = 0; e < n; ++e) w[e] = (float)(((splitmix64(st) >> 11) * (1.0 / 9007199254740992.0)) - 0.5) * 0.02f;
+  for (int l = 0; l < kNetLayers; ++l) {
+    float* wl = w.data() + net->off[l];
+    const int ci = net->cin[l], co = net->cout[l];
+    for (int c = 0; c < co && c < ci; ++c) wl[(0 * co + c) * ci + c] += 1.0f;  // centre tap, c -> c
+  }
+  const int rc = net_upload(net, w.data());
+  if (rc != HQMC_OK) {
+    hqmc_net_free(net);
+    return rc;
+  }
+  *out = net;
+  return HQMC_OK;
+}
+
+int hqmc_net_free(hqmc_net* net) {
+  if (!net) return HQMC_OK;
+  cudaDeviceSynchronize();
+  cudaFree(net->w);
+  cudaFree(net->m);
+  cudaFree(net->v);
+  cudaFree(net->wb);
+  cudaFree(net->wt);
+  delete net;
+  return HQMC_OK;
+}
+
+int hqmc_net_num_weights(const hqmc_net* net) { return net ? net->total : 0; }
+
+int hqmc_net_get_weights(const hqmc_net* net, float* host, int n) {
+  if (!net || !host || n != net->total) return HQMC_EINVAL;
+  if (cudaMemcpy(host, net->w, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return HQMC_ECUDA;
+  return HQMC_OK;
+}
+
+int hqmc_net_set_weights(hqmc_net* net, const float* host, int n) {
+  if (!net || !host || n != net->total) return HQMC_EINVAL;
+  return net_upload(net, host);
+}
+
+int hqmc_net_apply(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* r, void* z, void* stream) {
+  if (!cfg || !net) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(r) || !aligned16(z)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  RET(net_workspace(cfg));
+  RET(theta_float(cfg, theta, s));
+  return net_forward(cfg, net, (const double2*)r, (double2*)z, s);
+}
+
+int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* phi, const void* x,
+                        double lr, double* loss_host, void* stream) {
+  if (!cfg || !net || !(lr >= 0)) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(phi) || !aligned16(x)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  RET(net_workspace(cfg));
+  RET(theta_float(cfg, theta, s));
+  RET(net_forward(cfg, net, (const double2*)phi, nullptr, s));  // activations h0..h4
+  // ||x||^2 on the device, then the loss and its gradient with respect to h4
+  LK(2, launch_action_terms(cfg->g, cfg->bp, theta, nullptr, (const double2*)x, (const double2*)x, cfg->act_grid,
+                            cfg->part_act, cfg->terms, s));
+  double* loss_part = cfg->net_part + (size_t)kNetChunks * 7 * kNetCh * kNetCh;
+  const int lblocks = 512;
+  LK(1, launch_net_loss(cfg->net_h[kNetLayers], (const double2*)x, cfg->terms + 2, cfg->net_d[0], loss_part, lblocks,
+                        cfg->n, s));
+  // backward: layer l uses d_{l+1} and h_l; the adjoint weights are taken before the update
+  net->steps++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)net->steps), c2 = 1.f - std::pow(b2, (float)net->steps);
+  int din = 0;
+  for (int l = kNetLayers - 1; l >= 0; --l) {
+    const int ci = net->cin[l], co = net->cout[l];
+    const int nw = 7 * ci * co;
+    LK(1, launch_net_wgrad(cfg->g, cfg->th32, ci, co, cfg->net_d[din], cfg->net_h[l], cfg->net_part, kNetChunks, s));
+    if (l > 0) {
+      void* wt = (char*)net->wt + 2 * (size_t)net->off[l];
+      LK(1, launch_net_adjoint_weights((char*)net->wb + 2 * (size_t)net->off[l], wt, ci, co, s));
+      LK(1, launch_net_layer(cfg->g, cfg->th32, wt, co, ci, cfg->net_d[din], cfg->net_d[din ^ 1], s));
+    }
+    LK(1, launch_net_adam(net->w + net->off[l], net->m + net->off[l], net->v + net->off[l], cfg->net_part, kNetChunks,
+                          nw, (char*)net->wb + 2 * (size_t)net->off[l], (float)lr, b1, b2, c1, c2, 1e-8f, 1.f, s));
+    din ^= 1;
+  }
+  if (loss_host) {
+    std::vector<double> lp(lblocks);
+    CK(cudaMemcpyAsync(cfg->vscratch, loss_part, lblocks * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(lp.data(), loss_part, lblocks * sizeof(double), cudaMemcpyDeviceToHost));
+    double sum = 0.0;
+    for (double v : lp) sum += v;
+    *loss_host = sum;
+  }
+  return HQMC_OK;
+}
+
+int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net) {
+  if (!cfg) return HQMC_EINVAL;
+  cfg->net = net;
+  return HQMC_OK;
 }
 
 }  // extern "C"

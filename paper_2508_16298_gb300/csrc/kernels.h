@@ -177,4 +177,16 @@ void philox_uniform_host(uint64_t seed, uint64_t counter, double* u);
 // FP64 FMA throughput probe (16 flops per thread per iteration).
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
 
+// Learned preconditioner (net.cu).  Weights are BF16 [7][cout][cin] per layer.
+cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, int cin, int cout, const float2* in,
+                             float2* out, cudaStream_t s);
+cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
+                             double* partials, int nchunks, cudaStream_t s);
+cudaError_t launch_net_loss(const float2* h, const double2* x, const double* xx, float2* d, double* part, int nblocks,
+                            long long n, cudaStream_t s);
+cudaError_t launch_net_adam(float* w, float* m, float* v, const double* partials, int nchunks, int nw, void* wb,
+                            float lr, float b1, float b2, float c1, float c2, float eps, float scale, cudaStream_t s);
+cudaError_t launch_net_adjoint_weights(const void* W, void* Wt, int cin, int cout, cudaStream_t s);
+cudaError_t launch_net_convert(const void* in, void* out, int to_float, double scale, long long n, cudaStream_t s);
+
 }  // namespace hqmc

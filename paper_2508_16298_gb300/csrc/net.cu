@@ -1,0 +1,260 @@
+// Learned preconditioner: a small 3D periodic convolution network on the
+// space-time lattice, gauge covariant and linear in its input, with BF16
+// weights and FP32 arithmetic.
+//
+// Layer l maps C_in complex channels to C_out complex channels:
+//   h'(x, c) = sum_{mu=0..6} sum_{c'} W[mu][c][c'] (T_mu h)(x, c')
+// with the seven stencil directions mu = 0 (centre), 1/2 = +x/-x, 3/4 = +y/-y,
+// 5/6 = +tau/-tau and the parallel transporters
+//   (T_{+x} h)(x) = e^{i theta_x(x)} h(x + x^),  (T_{-x} h)(x) = e^{-i theta_x(x - x^)} h(x - x^)
+// (y alike), and (T_{+-tau} h)(x) = s h(x +- tau^) with s = -1 across the
+// antiperiodic tau boundary.  Real weights commute with the U(1) phases, so the
+// net is covariant under theta_ij -> theta_ij + l_i - l_j, h -> e^{i l} h, and
+// without activations it is a linear map r -> K(theta) r, which is what a
+// (flexible) CG preconditioner must be.  T_mu^dagger = T_{mu-bar} (the
+// opposite direction), so the backward pass is the same stencil with
+// W'[mu-bar] = W[mu]^T.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace hqmc {
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Transport factor and neighbour index of direction mu at global site i.
+__device__ __forceinline__ void net_neighbour(const Geo& g, const float2* __restrict__ th32, long long i, int mu,
+                                              long long& j, float2& ph) {
+  const int V = g.V, L = g.L;
+  const int tau = (int)(i / V);
+  const int s = (int)(i - (long long)tau * V);
+  const int x = s % L, y = s / L;
+  float sn, cs;
+  switch (mu) {
+    case 0:
+      j = i;
+      ph = make_float2(1.f, 0.f);
+      break;
+    case 1: {
+      const int xp = (x + 1 == L) ? 0 : x + 1;
+      j = (long long)tau * V + xp + L * y;
+      __sincosf(__ldg(th32 + i).x, &sn, &cs);
+      ph = make_float2(cs, sn);
+    } break;
+    case 2: {
+      const int xm = (x == 0) ? L - 1 : x - 1;
+      j = (long long)tau * V + xm + L * y;
+      __sincosf(__ldg(th32 + j).x, &sn, &cs);
+      ph = make_float2(cs, -sn);
+    } break;
+    case 3: {
+      const int yp = (y + 1 == L) ? 0 : y + 1;
+      j = (long long)tau * V + x + L * yp;
+      __sincosf(__ldg(th32 + i).y, &sn, &cs);
+      ph = make_float2(cs, sn);
+    } break;
+    case 4: {
+      const int ym = (y == 0) ? L - 1 : y - 1;
+      j = (long long)tau * V + x + L * ym;
+      __sincosf(__ldg(th32 + j).y, &sn, &cs);
+      ph = make_float2(cs, -sn);
+    } break;
+    case 5: {
+      const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
+      j = (long long)tp * V + s;
+      ph = make_float2(tp == 0 ? -1.f : 1.f, 0.f);
+    } break;
+    default: {
+      const int tm = (tau == 0) ? g.Ntau - 1 : tau - 1;
+      j = (long long)tm * V + s;
+      ph = make_float2(tau == 0 ? -1.f : 1.f, 0.f);
+    } break;
+  }
+}
+
+// One layer, one thread per site.  Weights [7][COUT][CIN] (BF16) are widened to
+// FP32 in shared memory; every thread of a warp reads the same weight, a
+// broadcast.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) net_layer_kernel(Geo g, const float2* __restrict__ th32,
+                                                        const __nv_bfloat16* __restrict__ W,
+                                                        const float2* __restrict__ in, float2* __restrict__ out,
+                                                        long long n) {
+  __shared__ float w[7 * COUT * CIN];
+  for (int k = threadIdx.x; k < 7 * COUT * CIN; k += blockDim.x) w[k] = __bfloat162float(W[k]);
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float2 acc[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int mu = 0; mu < 7; ++mu) {
+      long long j;
+      float2 ph;
+      net_neighbour(g, th32, i, mu, j, ph);
+      const float2* hin = in + j * CIN;
+#pragma unroll
+      for (int cp = 0; cp < CIN; ++cp) {
+        const float2 v = cmulf(ph, hin[cp]);
+        const float* wc = w + (mu * COUT) * CIN + cp;
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) {
+          const float wv = wc[c * CIN];
+          acc[c].x = fmaf(wv, v.x, acc[c].x);
+          acc[c].y = fmaf(wv, v.y, acc[c].y);
+        }
+      }
+    }
+    float2* o = out + i * COUT;
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) o[c] = acc[c];
+  }
+}
+
+// Weight gradient: G[mu][c][c'] = sum_x Re(conj(d(x, c)) (T_mu h)(x, c')), one
+// thread per weight entry over a chunk of sites; partials[chunk][entry].
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) net_wgrad_kernel(Geo g, const float2* __restrict__ th32,
+                                                        const float2* __restrict__ d, const float2* __restrict__ h,
+                                                        double* __restrict__ partials, long long n, long long chunk) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 7 * COUT * CIN) return;
+  const int mu = e / (COUT * CIN);
+  const int c = (e / CIN) % COUT;
+  const int cp = e % CIN;
+  const long long i0 = (long long)blockIdx.y * chunk;
+  const long long i1 = (i0 + chunk < n) ? i0 + chunk : n;
+  float acc = 0.f;
+  double accd = 0.0;
+  int cnt = 0;
+  for (long long i = i0; i < i1; ++i) {
+    long long j;
+    float2 ph;
+    net_neighbour(g, th32, i, mu, j, ph);
+    const float2 v = cmulf(ph, h[j * CIN + cp]);
+    const float2 dd = d[i * COUT + c];
+    acc = fmaf(dd.x, v.x, fmaf(dd.y, v.y, acc));
+    if (++cnt == 256) {  // bounded float runs, summed in double
+      accd += acc;
+      acc = 0.f;
+      cnt = 0;
+    }
+  }
+  partials[(long long)blockIdx.y * (7 * COUT * CIN) + e] = accd + acc;
+}
+
+// loss = ||h - x||^2 / ||x||^2 (partials) and d = 2 (h - x) / ||x||^2; *xx = ||x||^2
+__global__ void net_loss_kernel(const float2* __restrict__ h, const double2* __restrict__ x, const double* xx,
+                                float2* __restrict__ d, double* __restrict__ part, long long n) {
+  __shared__ double red[32];
+  const double inv_xx = 1.0 / *xx;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ex = (double)h[i].x - x[i].x, ey = (double)h[i].y - x[i].y;
+    acc += ex * ex + ey * ey;
+    d[i] = make_float2((float)(2.0 * ex * inv_xx), (float)(2.0 * ey * inv_xx));
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t * inv_xx;
+}
+
+// Adam on the FP32 master weights; writes the BF16 copy used by the layers.
+__global__ void net_adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                                const double* __restrict__ partials, int nchunks, int nw, __nv_bfloat16* __restrict__ wb,
+                                float lr, float b1, float b2, float c1, float c2, float eps, float scale) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nw) return;
+  double gs = 0.0;
+  for (int k = 0; k < nchunks; ++k) gs += partials[(long long)k * nw + e];
+  const float gr = (float)gs * scale;
+  const float mm = b1 * m[e] + (1.f - b1) * gr;
+  const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
+  m[e] = mm;
+  v[e] = vv;
+  const float wn = w[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  w[e] = wn;
+  wb[e] = __float2bfloat16(wn);
+}
+
+// W'[mu-bar][c'][c] = W[mu][c][c'] for the backward stencil.
+__global__ void net_adjoint_weights_kernel(const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wt,
+                                           int cin, int cout) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 7 * cin * cout) return;
+  const int mu = e / (cout * cin);
+  const int c = (e / cin) % cout;
+  const int cp = e % cin;
+  const int mubar = mu == 0 ? 0 : (mu & 1) ? mu + 1 : mu - 1;
+  Wt[(mubar * cin + cp) * cout + c] = W[e];
+}
+
+// complex double <-> complex float with a scale
+__global__ void net_to_float_kernel(const double2* __restrict__ a, float2* __restrict__ b, double s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)(a[i].x * s), (float)(a[i].y * s));
+}
+__global__ void net_to_double_kernel(const float2* __restrict__ a, double2* __restrict__ b, double s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = make_double2((double)a[i].x * s, (double)a[i].y * s);
+}
+
+static inline int blocks_for(long long n, int t) {
+  long long b = (n + t - 1) / t;
+  return (int)(b > 8192 ? 8192 : (b < 1 ? 1 : b));
+}
+
+cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, int cin, int cout, const float2* in,
+                             float2* out, cudaStream_t s) {
+  const long long n = (long long)g.V * g.Ntau;
+  const __nv_bfloat16* w = (const __nv_bfloat16*)W;
+  const int nb = blocks_for(n, 256);
+  if (cin == 1 && cout == 16) net_layer_kernel<1, 16><<<nb, 256, 0, s>>>(g, th32, w, in, out, n);
+  else if (cin == 16 && cout == 16) net_layer_kernel<16, 16><<<nb, 256, 0, s>>>(g, th32, w, in, out, n);
+  else if (cin == 16 && cout == 1) net_layer_kernel<16, 1><<<nb, 256, 0, s>>>(g, th32, w, in, out, n);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
+                             double* partials, int nchunks, cudaStream_t s) {
+  const long long n = (long long)g.V * g.Ntau;
+  const long long chunk = (n + nchunks - 1) / nchunks;
+  const int ne = 7 * cin * cout;
+  dim3 grid((ne + 255) / 256, nchunks);
+  if (cin == 1 && cout == 16) net_wgrad_kernel<1, 16><<<grid, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
+  else if (cin == 16 && cout == 16) net_wgrad_kernel<16, 16><<<grid, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
+  else if (cin == 16 && cout == 1) net_wgrad_kernel<16, 1><<<grid, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_loss(const float2* h, const double2* x, const double* xx, float2* d, double* part, int nblocks,
+                            long long n, cudaStream_t s) {
+  net_loss_kernel<<<nblocks, 256, 0, s>>>(h, x, xx, d, part, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_adam(float* w, float* m, float* v, const double* partials, int nchunks, int nw, void* wb,
+                            float lr, float b1, float b2, float c1, float c2, float eps, float scale, cudaStream_t s) {
+  net_adam_kernel<<<(nw + 255) / 256, 256, 0, s>>>(w, m, v, partials, nchunks, nw, (__nv_bfloat16*)wb, lr, b1, b2, c1,
+                                                  c2, eps, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_adjoint_weights(const void* W, void* Wt, int cin, int cout, cudaStream_t s) {
+  const int ne = 7 * cin * cout;
+  net_adjoint_weights_kernel<<<(ne + 255) / 256, 256, 0, s>>>((const __nv_bfloat16*)W, (__nv_bfloat16*)Wt, cin, cout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_convert(const void* in, void* out, int to_float, double scale, long long n, cudaStream_t s) {
+  if (to_float)
+    net_to_float_kernel<<<blocks_for(n, 256), 256, 0, s>>>((const double2*)in, (float2*)out, scale, n);
+  else
+    net_to_double_kernel<<<blocks_for(n, 256), 256, 0, s>>>((const float2*)in, (double2*)out, scale, n);
+  return cudaGetLastError();
+}
+
+}  // namespace hqmc

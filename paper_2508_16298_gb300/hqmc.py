@@ -27,7 +27,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
 FP64, FP32 = 0, 1
 ACTION_COMPACT, ACTION_NONCOMPACT = 0, 1
-SOLVER_CG64, SOLVER_MIXED = 0, 1
+SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED = 0, 1, 2
 TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE = 0, 1, 2
 
 # Every function declared in include/hqmc.h.
@@ -36,7 +36,9 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_cg_solve", "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
-           "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory")
+           "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory",
+           "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
+           "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner")
 
 
 class Params(ctypes.Structure):
@@ -50,7 +52,7 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("true_residual", ctypes.c_double),
                 ("recursive_residual", ctypes.c_double), ("fp64_fallback", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("net_guess_used", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -96,6 +98,14 @@ _sig = {
                              ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_batch_trajectory": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), _u64, _i,
                                ctypes.POINTER(ctypes.c_double), _d, _i, ctypes.POINTER(TrajInfo), _vp], _i),
+    "hqmc_net_create": ([_u64, ctypes.POINTER(_vp)], _i),
+    "hqmc_net_free": ([_vp], _i),
+    "hqmc_net_num_weights": ([_vp], _i),
+    "hqmc_net_get_weights": ([_vp, ctypes.POINTER(ctypes.c_float), _i], _i),
+    "hqmc_net_set_weights": ([_vp, ctypes.POINTER(ctypes.c_float), _i], _i),
+    "hqmc_net_apply": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "hqmc_net_train_step": ([_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_double), _vp], _i),
+    "hqmc_set_preconditioner": ([_vp, _vp], _i),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -231,7 +241,7 @@ def apply_MdagM(cfg: Config, theta, x, y=None):
 
 def _solver(s) -> int:
     if isinstance(s, str):
-        return {"cg64": SOLVER_CG64, "mixed": SOLVER_MIXED}[s]
+        return {"cg64": SOLVER_CG64, "mixed": SOLVER_MIXED, "learned": SOLVER_LEARNED}[s]
     return int(s)
 
 
@@ -410,3 +420,66 @@ class Batch:
                                         nsteps, (ctypes.c_double * n)(*dts), tol, maxit, infos, _stream())
         self._check(rc, allow=(OK, ENOTCONV))
         return [i.as_dict() for i in infos]
+
+
+class Net:
+    """Learned preconditioner K(theta) (hqmc_net_*): 4 gauge-covariant linear stencil layers,
+    1 -> 16 -> 16 -> 16 -> 1 complex channels, BF16 weights, FP32 arithmetic."""
+
+    def __init__(self, seed: int = 0):
+        h = _vp()
+        rc = _lib.hqmc_net_create(seed, ctypes.byref(h))
+        if rc != OK:
+            raise HQMCError(rc, "net creation")
+        self._h = h
+        self.n_weights = int(_lib.hqmc_net_num_weights(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.hqmc_net_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_weights(self):
+        import numpy as np
+        w = np.empty(self.n_weights, dtype=np.float32)
+        rc = _lib.hqmc_net_get_weights(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.n_weights)
+        if rc != OK:
+            raise HQMCError(rc, "get weights")
+        return w
+
+    def set_weights(self, w):
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        rc = _lib.hqmc_net_set_weights(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size)
+        if rc != OK:
+            raise HQMCError(rc, "set weights")
+
+    def apply(self, cfg: Config, theta, r, z=None):
+        cfg._bonds(theta, "theta")
+        cfg._vec(r, "r")
+        z = torch.empty_like(r) if z is None else cfg._vec(z, "z")
+        cfg.check(_lib.hqmc_net_apply(cfg.handle, self._h, _ptr(theta), _ptr(r), _ptr(z), _stream()))
+        return z
+
+    def train_step(self, cfg: Config, theta, phi, x, lr: float = 1e-3, want_loss: bool = True):
+        cfg._bonds(theta, "theta")
+        cfg._vec(phi, "phi")
+        cfg._vec(x, "x")
+        loss = ctypes.c_double()
+        cfg.check(_lib.hqmc_net_train_step(cfg.handle, self._h, _ptr(theta), _ptr(phi), _ptr(x), lr,
+                                           ctypes.byref(loss) if want_loss else None, _stream()))
+        return loss.value if want_loss else None
+
+
+def set_preconditioner(cfg: Config, net):
+    cfg.check(_lib.hqmc_set_preconditioner(cfg.handle, None if net is None else net.handle))

@@ -1,0 +1,126 @@
+"""The learned preconditioner's CUDA kernels (inference and training) against the
+FP64 reference network of oracle/net.py, and the learned solver."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import net as onet
+from paper_2508_16298_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hq():
+    from paper_2508_16298_gb300 import build
+    build.build()
+    from paper_2508_16298_gb300 import hqmc
+    return hqmc
+
+
+def bf16(a):
+    """Round float32 values to the nearest bfloat16 (ties to even), kept as float32."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    b = (b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
+    return b.view(np.float32)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def random_flat(seed, scale=0.25):
+    n = sum(7 * ci * co for ci, co in onet.LAYERS)
+    return bf16(inputs.rng(seed).standard_normal(n) * scale)
+
+
+@pytest.mark.parametrize("L,N", [(4, 4), (8, 12), (24, 48)])
+def test_net_forward_matches_reference(hq, L, N):
+    w = random_flat(1)
+    th = inputs.theta_hot(L, N, 2)
+    r = inputs.complex_gaussian(L, N, 3)
+    ref = onet.apply(th, r, onet.split_flat(w, onet.LAYERS))
+    with hq.Config(L, N) as cfg:
+        k = hq.Net(seed=0)
+        k.set_weights(w)
+        z = k.apply(cfg, cuda(th), cuda(r)).cpu().numpy()
+        k.close()
+    assert rel(z, ref) < 1e-5
+
+
+def test_net_is_gauge_covariant(hq):
+    L, N = 8, 10
+    th = inputs.theta_hot(L, N, 4)
+    r = inputs.complex_gaussian(L, N, 5)
+    lam = inputs.rng(6).uniform(-np.pi, np.pi, size=(L, L))
+    thg = th.copy()
+    thg[..., 0] += lam[None] - np.roll(lam, -1, axis=1)[None]
+    thg[..., 1] += lam[None] - np.roll(lam, -1, axis=0)[None]
+    D = np.exp(1j * lam)[None]
+    with hq.Config(L, N) as cfg:
+        k = hq.Net(seed=0)
+        k.set_weights(random_flat(7))
+        a = k.apply(cfg, cuda(thg), cuda(D * r)).cpu().numpy()
+        b = D * k.apply(cfg, cuda(th), cuda(r)).cpu().numpy()
+        k.close()
+    assert rel(a, b) < 1e-5
+
+
+def test_first_adam_step_follows_the_reference_gradient(hq):
+    """Adam's first step is -lr * g / (|g| + eps): each weight moves against the sign of
+    its gradient.  Compare with the reference back-propagation on one triple."""
+    L, N = 6, 8
+    w = random_flat(8, 0.3)
+    th = inputs.theta_hot(L, N, 9)
+    phi, x = inputs.complex_gaussian(L, N, 10), inputs.complex_gaussian(L, N, 11)
+    ws = onet.split_flat(w, onet.LAYERS)
+    grads = np.concatenate([g.reshape(-1) for g in onet.loss_gradient(th, phi, x, ws)])
+    with hq.Config(L, N) as cfg:
+        k = hq.Net(seed=0)
+        k.set_weights(w)
+        loss = k.train_step(cfg, cuda(th), cuda(phi), cuda(x), lr=1e-3)
+        w1 = k.get_weights()
+        k.close()
+    assert abs(loss - onet.loss(th, phi, x, ws)) < 1e-5 * onet.loss(th, phi, x, ws)
+    step = w1 - w
+    big = np.abs(grads) > 1e-3 * np.max(np.abs(grads))
+    assert big.sum() > 100
+    assert np.all(np.sign(step[big]) == -np.sign(grads[big]))
+    assert np.allclose(np.abs(step[big]), 1e-3, rtol=1e-2)
+
+
+def test_training_lowers_the_loss_and_helps_the_solver(hq):
+    """Train on sampler triples (theta from the field, x solved by FP64 CG) and use the
+    net through the learned solver: the true residual still judges convergence."""
+    L, N = 8, 40
+    lat = oracle.Lattice(L, N)
+    with hq.Config(L, N) as cfg:
+        k = hq.Net(seed=1)
+        triples = []
+        for s in range(6):
+            th = cuda(inputs.theta_ordered(L, N, 20 + s, tau_walk=0.0))
+            phi = hq.apply_M(cfg, th, cuda(inputs.complex_gaussian(L, N, 40 + s)), dagger=True)
+            X, info = hq.cg_solve(cfg, th, phi, tol=1e-10)
+            triples.append((th, phi, X))
+        losses = []
+        for epoch in range(30):
+            for th, phi, X in triples:
+                losses.append(k.train_step(cfg, th, phi, X, lr=3e-3))
+        assert np.mean(losses[-6:]) < 0.5 * np.mean(losses[:6])
+        hq.set_preconditioner(cfg, k)
+        th = cuda(inputs.theta_ordered(L, N, 99, tau_walk=0.0))
+        phi = hq.apply_M(cfg, th, cuda(inputs.complex_gaussian(L, N, 98)), dagger=True)
+        Xl, il = hq.cg_solve(cfg, th, phi, tol=1e-8, solver="learned")
+        Xp, ip = hq.cg_solve(cfg, th, phi, tol=1e-8, solver="mixed")
+        hq.set_preconditioner(cfg, None)
+        k.close()
+    assert il["status"] == 0 and il["true_residual"] <= 1e-8
+    assert il["net_guess_used"] == 1
+    r = phi.cpu().numpy() - oracle.apply_MdagM(lat, th.cpu().numpy(), Xl.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(phi.cpu().numpy())
+    print("learned iterations", il["iterations"], "mixed iterations", ip["iterations"])
