@@ -58,8 +58,9 @@ DEFAULT_WORKLOAD = "hmc_fp64_L24_Nt240"
 # Algorithmic work of one launch of the fused M^dagger M kernel in CG mode, per site:
 #   flops: 2 sweeps x 7 factor passes x 8 flops + 22 (direction update, combination, <p, Op>)
 #   bytes (FP64): links 32 + r 16 + p_old 16 + p_new 16 + q 16
+#   bytes (FP32, register-blocked): theta as float 8 + r 8 + p_old 8 + p_new 8 + q 8
 MDAGM_FLOPS_PER_SITE = 134
-MDAGM_BYTES_PER_SITE = {"cg64": 96, "mixed": 48}
+MDAGM_BYTES_PER_SITE = {"cg64": 96, "mixed": 40, "learned": 40}
 
 
 def _peaks():
@@ -261,7 +262,7 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     flush.zero_()
     hqmc.set_timing(cfg, True)
     hqmc.trajectory(cfg, theta, seed=seed, traj_counter=args.warmup + args.steps, **kw)
-    n_md, md_ms = hqmc.get_timing(cfg, hqmc.TIMER_MDAGM)
+    n_md, md_ms = hqmc.get_timing(cfg, hqmc.TIMER_MDAGM if wl["solver"] == "cg64" else hqmc.TIMER_MDAGM32)
     hqmc.set_timing(cfg, False)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -297,16 +298,23 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     achieved_gbs = MDAGM_BYTES_PER_SITE[wl["solver"]] * sites / (md_avg_ms * 1e-3) / 1e9
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
+    fp32 = wl["solver"] != "cg64"
     shape = cfg.launch_shape(hqmc.FP64 if wl["solver"] == "cg64" else hqmc.FP32)
     kname = (f"mdagm_block_kernel<{'double' if wl['solver'] == 'cg64' else 'float'}, CG direction, nby={shape['variant']}>"
              if shape["variant"] > 0 else
              f"mdagm_kernel<{'double' if wl['solver'] == 'cg64' else 'float'}, CG direction, mb={-shape['variant']}>")
-    roofline = {"kernel": kname, "cluster": shape["cluster"], "bound": "alu", "achieved": achieved_tflops,
-                "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_tflops,
-                "traffic": None,
-                "peak_note": "FP64 FMA rate measured on this GPU by hqmc_probe_fp64_rate",
-                "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / hbm,
-                "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms}
+    if fp32:  # the FP32 fused kernel is bounded by HBM bandwidth
+        roofline = {"kernel": kname, "cluster": shape["cluster"], "bound": "hbm", "achieved": achieved_gbs,
+                    "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm, "traffic": None,
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "tflops_algorithmic": achieved_tflops, "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms}
+    else:
+        roofline = {"kernel": kname, "cluster": shape["cluster"], "bound": "alu", "achieved": achieved_tflops,
+                    "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_tflops,
+                    "traffic": None,
+                    "peak_note": "FP64 FMA rate measured on this GPU by hqmc_probe_fp64_rate",
+                    "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / hbm,
+                    "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms}
 
     # ---- oracle on the host cores: bounded sample --------------------------
     import oracle

@@ -312,7 +312,10 @@ HQMC_API int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net);
 
 /* ---- instrumentation ---------------------------------------------------- */
 
-enum { HQMC_TIMER_MDAGM = 0, HQMC_TIMER_CG_UPDATE = 1, HQMC_TIMER_FORCE = 2, HQMC_TIMER_COUNT = 3 };
+/* Timed kernel classes: the fused M^dagger M in FP64 (applies, CG directions,
+ * residuals), the fused M^dagger M in FP32, the CG vector update, the force. */
+enum { HQMC_TIMER_MDAGM = 0, HQMC_TIMER_CG_UPDATE = 1, HQMC_TIMER_FORCE = 2, HQMC_TIMER_MDAGM32 = 3,
+       HQMC_TIMER_COUNT = 4 };
 
 /* Enables (1) or disables (0) CUDA-event timing of kernel launches and resets
  * the counters.  Events are recorded on the launching stream around every

@@ -267,9 +267,10 @@ int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, con
   a.part_out = cfg->part_mdagm;
   a.st = cfg->st;
   int slot;
-  RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
+  const int tcls = sizeof(R) == 8 ? HQMC_TIMER_MDAGM : HQMC_TIMER_MDAGM32;
+  RET(timer_begin(cfg, tcls, s, &slot));
   LK(1, (launch_fused<R, MODE_CGDIR>(cfg, a, s)));
-  RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
+  RET(timer_end(cfg, tcls, s, slot));
   RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
   LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, fused_shape<R>(cfg).grid,
                          cfg->part_ew, cfg->st, s));
@@ -941,9 +942,9 @@ int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void*
     a.U = cfg->U32;
     a.x = (const float2*)x;
     a.y = (float2*)y;
-    RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
+    RET(timer_begin(cfg, HQMC_TIMER_MDAGM32, s, &slot));
     LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
-    RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
+    RET(timer_end(cfg, HQMC_TIMER_MDAGM32, s, slot));
   }
   return HQMC_OK;
 }

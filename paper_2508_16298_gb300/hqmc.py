@@ -28,7 +28,7 @@ OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPOR
 FP64, FP32 = 0, 1
 ACTION_COMPACT, ACTION_NONCOMPACT = 0, 1
 SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED = 0, 1, 2
-TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE = 0, 1, 2
+TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE, TIMER_MDAGM32 = 0, 1, 2, 3
 
 # Every function declared in include/hqmc.h.
 EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_error", "hqmc_num_sites",
