@@ -82,7 +82,9 @@ typedef struct hqmc_params {
     int autotune;          /* 1: time every admissible launch shape of the fused M^dagger M in
                               hqmc_make_config and keep the fastest; 0: built-in choice */
     int variant;           /* fused M^dagger M kernel: 0 any, 1 generic only, 2 register-blocked
-                              only (HQMC_EUNSUPPORTED if no strip shape fits L) */
+                              only (HQMC_EUNSUPPORTED if no strip shape fits L), 3 FP32 on the
+                              persistent tau-walking kernel (HQMC_EUNSUPPORTED if it does not fit
+                              L; FP64 as for 0) */
 } hqmc_params;
 
 /* Opaque configuration: geometry, launch shapes and the device workspace
@@ -98,7 +100,7 @@ typedef struct hqmc_solve_info {
     double true_residual;      /* ||phi - (M^dagger M) x|| / ||phi||, computed in FP64 */
     double recursive_residual; /* the recurrence's estimate at exit */
     int fp64_fallback;         /* mixed solver: 1 if FP32 breakdowns, or a true residual cut
-                                  by less than 10x over four reliable updates, handed the
+                                  by less than 2x over eight reliable updates, handed the
                                   rest of the solve to the FP64 recurrence */
     int net_guess_used;        /* learned solver: 1 if the net's correction of the initial
                                   guess lowered the residual and was kept */
@@ -140,7 +142,9 @@ HQMC_API long long hqmc_num_sites(const hqmc_config* cfg);
 HQMC_API long long hqmc_launch_count(const hqmc_config* cfg);
 
 /* Launch shape of the fused M^dagger M for one precision (host query):
- * *variant > 0: register-blocked kernel with strips of *variant 2x2 blocks;
+ * *variant >= 100: persistent tau-walking kernel (FP32) with strips of
+ * *variant - 100 2x2 blocks, one contiguous range of slices per CTA;
+ * 0 < *variant < 100: register-blocked kernel with strips of *variant 2x2 blocks;
  * *variant <= 0: generic kernel holding -*variant bonds per family in registers
  * (0: links re-read from memory).  *cluster: CTAs (slices) per cluster;
  * *threads: block size; *tuned_us: autotuner's time of one apply (0 if not

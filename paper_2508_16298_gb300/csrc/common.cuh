@@ -44,6 +44,12 @@ template <class T, class R> __device__ __forceinline__ T cscale(R s, T b) { retu
 template <class T> __device__ __forceinline__ double cdot_re(T a, T b) {
   return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
 }
+// Re(conj(a) * b) in the vector's own precision.  FP32 kernels sum a thread's
+// few terms this way and promote once: FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this GPU, so a per-site double accumulation
+// would dominate an FP32 kernel.
+__device__ __forceinline__ float cdot_re_own(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+__device__ __forceinline__ double cdot_re_own(double2 a, double2 b) { return cdot_re(a, b); }
 
 // Slice geometry.
 struct Geo {
@@ -238,13 +244,15 @@ struct CgState {
   int loops;         // loop bodies executed in this solve
   int loop_cap;      // hard bound on loop bodies (termination guard of the device-side loop)
   int n_rel;         // mixed solver: reliable updates done
-  double rr_rel[4];  // mixed solver: true <r,r> at the last four reliable updates (ring)
+  double rr_rel[8];  // mixed solver: true <r,r> at the last eight reliable updates (ring)
 };
 
 // CG_REC_CONVERGED: the recursive residual met tol; the true residual still has
 // to be checked.  CG_CONVERGED: the true FP64 residual met tol.
-// CG_STAGNATED (mixed solver): four reliable updates cut the true residual by
-// less than 10x, i.e. FP32 rounding stalls the recurrence on this field.
+// CG_STAGNATED (mixed solver): eight reliable updates cut the true residual by
+// less than 2x, i.e. FP32 rounding stalls the recurrence on this field.  (Plain
+// CG on these ill-conditioned fields may gain less than 10x in 200 iterations,
+// so a tighter test would abandon FP32 on healthy solves.)
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4, CG_REC_CONVERGED = 5,
        CG_STAGNATED = 6 };
 

@@ -52,6 +52,8 @@ struct hqmc_config {
   SliceLaunch sl32{};  // fused M^dagger M in FP32 (same grid and clusters, own block shape)
   SliceLaunch slb64{}; // register-blocked fused M^dagger M, FP64 (nby = 0: not available)
   SliceLaunch slb32{}; // register-blocked fused M^dagger M, FP32 (nby = 0: not available)
+  SliceLaunch slw32{}; // tau-walking fused M^dagger M, FP32 (walk = 0: not available)
+  int num_sms = 0;
   SliceLaunch fused64{}, fused32{};  // shapes used for APPLY / CG direction (nby > 0: register-blocked)
   float tuned_us64 = 0.f, tuned_us32 = 0.f;  // autotuner: time of one FP64 / FP32 apply (0: not tuned)
   SliceLaunch sl1{};   // apply_M and force (one CTA per slice, no cluster)
@@ -215,10 +217,17 @@ const SliceLaunch& fused_shape(const hqmc_config* cfg) {
 }
 
 template <class R, int MODE>
-cudaError_t launch_fused(hqmc_config* cfg, const MdagmArgs<R>& a, cudaStream_t s) {
-  const SliceLaunch& sh = fused_shape<R>(cfg);
+cudaError_t launch_shape(const SliceLaunch& sh, const MdagmArgs<R>& a, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    if (sh.walk) return launch_mdagm_walk<MODE>(sh, a, s);
+  }
   if (sh.nby > 0) return launch_mdagm_block<R, MODE>(sh, a, s);
   return launch_mdagm<R, MODE>(sh, a, s);
+}
+
+template <class R, int MODE>
+cudaError_t launch_fused(hqmc_config* cfg, const MdagmArgs<R>& a, cudaStream_t s) {
+  return launch_shape<R, MODE>(fused_shape<R>(cfg), a, s);
 }
 
 template <class R, int MODE>
@@ -585,7 +594,7 @@ int time_shape(hqmc_config* cfg, const SliceLaunch& sh, float* us) {
     a.x = (const C2<R>*)cfg->p32[0];
     a.y = (C2<R>*)cfg->q32;
   }
-  auto go = [&]() { return sh.nby > 0 ? launch_mdagm_block<R, MODE_APPLY>(sh, a, 0) : launch_mdagm<R, MODE_APPLY>(sh, a, 0); };
+  auto go = [&]() { return launch_shape<R, MODE_APPLY>(sh, a, 0); };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -635,11 +644,29 @@ int autotune(hqmc_config* cfg) {
         cand.push_back(b);
       }
     }
+    if (!dbl && cfg->slw32.walk) {
+      // tau-walking kernel: one to a few CTAs per SM, never more CTAs than slices
+      const int bps = mdagm_walk_blocks_per_sm(cfg->slw32);
+      for (int m = 1; m <= bps && m <= 4; ++m) {
+        SliceLaunch w = cfg->slw32;
+        w.grid = std::min(N, m * cfg->num_sms);
+        cand.push_back(w);
+        if (w.grid == N) break;
+      }
+    }
+    if (!dbl && cfg->p.variant == 3) {  // the tau-walking kernel only
+      std::vector<SliceLaunch> keep;
+      for (const SliceLaunch& c : cand)
+        if (c.walk) keep.push_back(c);
+      cand.swap(keep);
+    }
     float best = 1e30f;
     SliceLaunch chosen = dbl ? cfg->fused64 : cfg->fused32;
     for (const SliceLaunch& c : cand) {
       const int rb = dbl ? 8 : 4;
-      const int nclus = c.nby > 0 ? mdagm_block_max_active_clusters(c, rb) : (dbl ? mdagm_max_active_clusters(c) : 1);
+      const int nclus = c.walk ? 1
+                        : c.nby > 0 ? mdagm_block_max_active_clusters(c, rb)
+                                    : (dbl ? mdagm_max_active_clusters(c) : 1);
       if (c.cluster > 1 && nclus <= 0) continue;
       float us = -1.f;
       RET(dbl ? time_shape<double>(cfg, c, &us) : time_shape<float>(cfg, c, &us));
@@ -689,8 +716,8 @@ int hqmc_get_launch_shape(const hqmc_config* cfg, int precision, int* variant, i
                           float* tuned_us) {
   if (!cfg || (precision != HQMC_FP64 && precision != HQMC_FP32)) return HQMC_EINVAL;
   const SliceLaunch& sh = precision == HQMC_FP64 ? cfg->fused64 : cfg->fused32;
-  if (variant) *variant = sh.nby > 0 ? sh.nby : -sh.mb;
-  if (cluster) *cluster = sh.cluster;
+  if (variant) *variant = sh.walk ? 100 + sh.nby : sh.nby > 0 ? sh.nby : -sh.mb;
+  if (cluster) *cluster = sh.walk ? 1 : sh.cluster;
   if (threads) *threads = sh.threads;
   if (tuned_us) *tuned_us = precision == HQMC_FP64 ? cfg->tuned_us64 : cfg->tuned_us32;
   return HQMC_OK;
@@ -705,7 +732,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
       !std::isfinite(p->J) || !std::isfinite(p->K))
     return HQMC_EINVAL;
   if (p->action != HQMC_ACTION_COMPACT && p->action != HQMC_ACTION_NONCOMPACT) return HQMC_EINVAL;
-  if (p->variant < 0 || p->variant > 2) return HQMC_EINVAL;
+  if (p->variant < 0 || p->variant > 3) return HQMC_EINVAL;
   const long long n = (long long)p->L * p->L * p->Ntau;
   if (n > (1LL << 31) - 1) return HQMC_EINVAL;
 
@@ -808,17 +835,49 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     };
     pick_block(8, &cfg->slb64);
     pick_block(4, &cfg->slb32);
+    cfg->num_sms = prop.multiProcessorCount;
+    // tau-walking FP32 kernel: the smallest strip height whose block fits, one CTA per SM
+    cfg->slw32 = cfg->sl32;
+    cfg->slw32.walk = 0;
+    {
+      const int Lh = L / 2;
+      for (int nby = 1; nby <= 3 && !cfg->slw32.walk; ++nby) {
+        if (Lh % nby) continue;
+        const int th = Lh * Lh / nby;
+        if (th > walk_thread_cap(nby) || walk_smem_bytes(cfg->g, MODE_CGDIR) > prop.sharedMemPerBlockOptin) continue;
+        SliceLaunch c = cfg->sl32;
+        c.nby = nby;
+        c.threads = th;
+        c.cluster = 1;
+        c.walk = 1;
+        c.grid = std::min(p->Ntau, cfg->num_sms);
+        if (prepare_mdagm_walk<MODE_CGDIR>(c) != cudaSuccess || prepare_mdagm_walk<MODE_APPLY>(c) != cudaSuccess ||
+            mdagm_walk_blocks_per_sm(c) < 1) {
+          cudaGetLastError();
+          continue;
+        }
+        cfg->slw32 = c;
+      }
+    }
     // variant 1 keeps the generic kernel, 2 demands the register-blocked one
     if (p->variant == 1) {
       cfg->slb64.nby = 0;
       cfg->slb32.nby = 0;
-    } else if (p->variant == 2 && (cfg->slb64.nby == 0 || cfg->slb32.nby == 0)) {
-      rc = fail(cfg, HQMC_EUNSUPPORTED, "no register-blocked shape fits L=%d", L);
+      cfg->slw32.walk = 0;
+    } else if (p->variant == 2) {
+      cfg->slw32.walk = 0;
+      if (cfg->slb64.nby == 0 || cfg->slb32.nby == 0) {
+        rc = fail(cfg, HQMC_EUNSUPPORTED, "no register-blocked shape fits L=%d", L);
+        break;
+      }
+    } else if (p->variant == 3 && !cfg->slw32.walk) {
+      rc = fail(cfg, HQMC_EUNSUPPORTED, "no tau-walking shape fits L=%d", L);
       break;
     }
-    // default shapes: the register-blocked kernel where it fits (the autotuner may override)
+    // default shapes: FP32 the tau-walking kernel, else the register-blocked one,
+    // where they fit (the autotuner may override)
     cfg->fused64 = cfg->slb64.nby > 0 ? cfg->slb64 : cfg->sl;
-    cfg->fused32 = cfg->slb32.nby > 0 ? cfg->slb32 : cfg->sl32;
+    cfg->fused32 = cfg->slw32.walk ? cfg->slw32 : cfg->slb32.nby > 0 ? cfg->slb32 : cfg->sl32;
     if (rc != HQMC_OK) break;
     if (prepare_mdagm<double, MODE_APPLY>(cfg->sl) != cudaSuccess ||
         prepare_mdagm<double, MODE_RESID>(cfg->sl) != cudaSuccess ||

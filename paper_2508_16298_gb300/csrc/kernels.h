@@ -28,6 +28,7 @@ struct SliceLaunch {
   int grid;      // CTAs, a multiple of cluster, >= Ntau
   int mb;        // bonds of each family per thread held in registers (1..4; 0: links from global)
   int nby;       // register-blocked kernel: 2x2 blocks stacked per thread strip (0: not used)
+  int walk;      // 1: persistent tau-walking kernel (FP32): `grid` CTAs, each a contiguous range of slices
 };
 
 enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_CGDIR = 2 };
@@ -71,6 +72,16 @@ cudaError_t prepare_mdagm_block(const SliceLaunch& sl);
 // Largest block for a strip of nby 2x2 blocks in this precision (0: not available).
 int block_thread_cap(int real_bytes, int nby);
 int mdagm_block_max_active_clusters(const SliceLaunch& sl, int real_bytes);
+
+// Persistent tau-walking fused M^dagger M in FP32 (APPLY and CGDIR modes;
+// sl.nby in 1..3, sl.grid CTAs <= Ntau, one contiguous slice range each).
+template <int MODE>
+cudaError_t launch_mdagm_walk(const SliceLaunch& sl, const MdagmArgs<float>& a, cudaStream_t s);
+template <int MODE>
+cudaError_t prepare_mdagm_walk(const SliceLaunch& sl);
+int walk_thread_cap(int nby);
+size_t walk_smem_bytes(const Geo& g, int mode);
+int mdagm_walk_blocks_per_sm(const SliceLaunch& sl);
 
 // Fused M^dagger M over many chains in one launch (generic kernel, links from
 // memory): CTA b runs cluster tile b / C = (chain, first slice) of `tiles`.

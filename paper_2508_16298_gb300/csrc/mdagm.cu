@@ -185,13 +185,14 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
     __syncthreads();
     if constexpr (MB > 0) sweep(W, ij, uu);
     else apply_P(a.g, W, Ut);
+    R accq = 0;  // CG direction: the thread's terms in the vector's precision (cdot_re_own)
     for (int s = t0; s < V; s += NT) {
       T q = caxpy(Y[s], cB, W[s]);
       if (MODE == MODE_APPLY) {
         a.y[base + s] = q;
       } else if (MODE == MODE_CGDIR) {
         a.y[base + s] = q;
-        acc0 += cdot_re(p_new[base + s], q);
+        accq += cdot_re_own(p_new[base + s], q);
       } else {  // MODE_RESID (R = double): r = b - O x
         const double2 bv = a.b[base + s];
         const double2 rv = make_double2(bv.x - (double)q.x, bv.y - (double)q.y);
@@ -203,6 +204,7 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
         acc1 += bv.x * bv.x + bv.y * bv.y;
       }
     }
+    if (MODE == MODE_CGDIR) acc0 = (double)accq;
   }
   if (MODE != MODE_APPLY) {
     const double t0 = block_sum(acc0, red);

@@ -3,27 +3,15 @@
 //
 // Same mathematics and cluster structure as mdagm.cu (one CTA per slice,
 // z_{tau-1} = P_{tau-1} x_{tau-1} read from the left neighbour's shared memory),
-// but each thread keeps a 2 x H strip of the slice (H = 2*NBY rows) in
-// registers and applies whole factors there:
-//
-//   "D" alignment: columns x0 = 2i+1, x1 = 2i+2, rows base+1 .. base+H
-//                  -> the family-4 bonds (odd tail y) are internal;
-//   "C" alignment: the same columns, rows base .. base+H-1
-//                  -> families 3 (even tail y) and 2 (odd tail x) are internal.
-//
-// A sweep P = F4 F3 F2 F1 F2 F3 F4 (rightmost first) is then
-//   F4 [D] | shift to C | F3 F2 [C] | F1 across columns | F2 F3 [C] | shift to D | F4 [D]
-// where a shift moves the strip one row (only one row crosses to the
-// neighbouring thread) and F1 exchanges the strip's sites with the left and
-// right neighbours.  Three shared-memory exchanges and three barriers per
-// sweep replace the seven full-slice passes of the generic kernel.
+// but each thread keeps a strip of the slice in registers (strip.cuh) and
+// applies whole factors there.
 //
 // Links: FP32 computes U = t_f e^{i theta} from a float copy of theta wrapped
 // to [-pi, pi) (8 bytes per site instead of 16 for a float link table);
 // FP64 reads the precomputed complex-double link table.
 #include <cooperative_groups.h>
 
-#include "kernels.h"
+#include "strip.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -34,188 +22,6 @@ __device__ __forceinline__ void bcluster_arrive() {
 }
 __device__ __forceinline__ void bcluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
-// Link factors of one strip (tanh of the factor angle folded in).
-template <class T, int NBY>
-struct StripLinks {
-  T u4[NBY][2];   // family 4: y-bonds with tail on D rows 0, 2, ... (odd y)
-  T u3[NBY][2];   // family 3: y-bonds with tail on C rows 0, 2, ... (even y)
-  T u2[2 * NBY];  // family 2: x-bond x0 -> x1 on every C row
-  T u1l[2 * NBY]; // family 1: x-bond 2i -> x0 (this strip holds its head)
-  T u1r[2 * NBY]; // family 1: x-bond x1 -> 2i+3 (this strip holds its tail)
-};
-
-// Per-thread geometry of the strip.
-struct StripGeo {
-  int L;
-  int x0, x1;  // owned columns 2i+1, (2i+2) mod L
-  int xl, xr;  // columns 2i and (2i+3) mod L of the family-1 partners
-  int base;    // first C row (2*jj*NBY)
-  int ytop;    // last D row (base + H) mod L
-};
-
-template <int NBY>
-__device__ __forceinline__ StripGeo strip_geo(int L) {
-  const int Lh = L >> 1;
-  const int i = threadIdx.x % Lh, jj = threadIdx.x / Lh;
-  StripGeo s;
-  s.L = L;
-  s.x0 = 2 * i + 1;
-  s.x1 = (2 * i + 2 == L) ? 0 : 2 * i + 2;
-  s.xl = 2 * i;
-  s.xr = (2 * i + 3 >= L) ? 2 * i + 3 - L : 2 * i + 3;
-  s.base = 2 * jj * NBY;
-  const int top = s.base + 2 * NBY;
-  s.ytop = (top >= L) ? top - L : top;
-  return s;
-}
-
-__device__ __forceinline__ int drow(const StripGeo& s, int r, int H) { return r < H - 1 ? s.base + 1 + r : s.ytop; }
-
-template <class T>
-__device__ __forceinline__ T link_from_theta(float th, float t) {
-  float sn, cs;
-  __sincosf(th, &sn, &cs);
-  return mk(t * cs, t * sn);
-}
-
-// FP32: from theta (float2 (theta_x, theta_y) per site, wrapped to [-pi, pi)).
-template <int NBY>
-__device__ __forceinline__ void load_strip_links(const StripGeo& s, const float2* __restrict__ th, float t1, float t2,
-                                                 StripLinks<float2, NBY>& k) {
-  constexpr int H = 2 * NBY;
-  const int L = s.L;
-#pragma unroll
-  for (int b = 0; b < NBY; ++b) {
-    const int yd = drow(s, 2 * b, H), yc = s.base + 2 * b;
-    k.u4[b][0] = link_from_theta<float2>(__ldg(th + yd * L + s.x0).y, t2);
-    k.u4[b][1] = link_from_theta<float2>(__ldg(th + yd * L + s.x1).y, t2);
-    k.u3[b][0] = link_from_theta<float2>(__ldg(th + yc * L + s.x0).y, t2);
-    k.u3[b][1] = link_from_theta<float2>(__ldg(th + yc * L + s.x1).y, t2);
-  }
-#pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const int yc = s.base + r;
-    k.u2[r] = link_from_theta<float2>(__ldg(th + yc * L + s.x0).x, t2);
-    k.u1l[r] = link_from_theta<float2>(__ldg(th + yc * L + s.xl).x, t1);
-    k.u1r[r] = link_from_theta<float2>(__ldg(th + yc * L + s.x1).x, t1);
-  }
-}
-
-// FP64: from the link table (two complex links per site, t_f folded in).
-template <int NBY>
-__device__ __forceinline__ void load_strip_links(const StripGeo& s, const double2* __restrict__ U,
-                                                 StripLinks<double2, NBY>& k) {
-  constexpr int H = 2 * NBY;
-  const int L = s.L;
-#pragma unroll
-  for (int b = 0; b < NBY; ++b) {
-    const int yd = drow(s, 2 * b, H), yc = s.base + 2 * b;
-    k.u4[b][0] = __ldg(U + 2 * (yd * L + s.x0) + 1);
-    k.u4[b][1] = __ldg(U + 2 * (yd * L + s.x1) + 1);
-    k.u3[b][0] = __ldg(U + 2 * (yc * L + s.x0) + 1);
-    k.u3[b][1] = __ldg(U + 2 * (yc * L + s.x1) + 1);
-  }
-#pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const int yc = s.base + r;
-    k.u2[r] = __ldg(U + 2 * (yc * L + s.x0));
-    k.u1l[r] = __ldg(U + 2 * (yc * L + s.xl));
-    k.u1r[r] = __ldg(U + 2 * (yc * L + s.x1));
-  }
-}
-
-// (vi, vj) <- (vi + u vj, vj + conj(u) vi)
-template <class T>
-__device__ __forceinline__ void bond2(T& vi, T& vj, const T& u) {
-  const T a = vi, b = vj;
-  vi = cfma(a, u, b);
-  vj = cfmac(b, u, a);
-}
-
-// v <- P v on the strip; v is in D alignment on entry and exit.
-template <class T, int NBY>
-__device__ __forceinline__ void strip_sweep(T (&v)[2 * NBY][2], const StripLinks<T, NBY>& k, const StripGeo& s,
-                                            T* __restrict__ E0, T* __restrict__ E1, int& eb) {
-  constexpr int H = 2 * NBY;
-  const int L = s.L;
-  // F4 in D
-#pragma unroll
-  for (int b = 0; b < NBY; ++b) {
-    bond2(v[2 * b][0], v[2 * b + 1][0], k.u4[b][0]);
-    bond2(v[2 * b][1], v[2 * b + 1][1], k.u4[b][1]);
-  }
-  // D -> C: hand the last D row up, take C row 0 from the strip below
-  {
-    T* E = eb ? E1 : E0;
-    eb ^= 1;
-    E[s.ytop * L + s.x0] = v[H - 1][0];
-    E[s.ytop * L + s.x1] = v[H - 1][1];
-    __syncthreads();
-#pragma unroll
-    for (int r = H - 1; r > 0; --r) {
-      v[r][0] = v[r - 1][0];
-      v[r][1] = v[r - 1][1];
-    }
-    v[0][0] = E[s.base * L + s.x0];
-    v[0][1] = E[s.base * L + s.x1];
-  }
-  // F3, F2 in C
-#pragma unroll
-  for (int b = 0; b < NBY; ++b) {
-    bond2(v[2 * b][0], v[2 * b + 1][0], k.u3[b][0]);
-    bond2(v[2 * b][1], v[2 * b + 1][1], k.u3[b][1]);
-  }
-#pragma unroll
-  for (int r = 0; r < H; ++r) bond2(v[r][0], v[r][1], k.u2[r]);
-  // F1 across columns: x0 is the head of (2i -> x0), x1 the tail of (x1 -> 2i+3)
-  {
-    T* E = eb ? E1 : E0;
-    eb ^= 1;
-#pragma unroll
-    for (int r = 0; r < H; ++r) {
-      E[(s.base + r) * L + s.x0] = v[r][0];
-      E[(s.base + r) * L + s.x1] = v[r][1];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < H; ++r) {
-      const T pl = E[(s.base + r) * L + s.xl];
-      const T pr = E[(s.base + r) * L + s.xr];
-      v[r][0] = cfmac(v[r][0], k.u1l[r], pl);
-      v[r][1] = cfma(v[r][1], k.u1r[r], pr);
-    }
-  }
-  // F2, F3 in C
-#pragma unroll
-  for (int r = 0; r < H; ++r) bond2(v[r][0], v[r][1], k.u2[r]);
-#pragma unroll
-  for (int b = 0; b < NBY; ++b) {
-    bond2(v[2 * b][0], v[2 * b + 1][0], k.u3[b][0]);
-    bond2(v[2 * b][1], v[2 * b + 1][1], k.u3[b][1]);
-  }
-  // C -> D: hand C row 0 down, take the last D row from the strip above
-  {
-    T* E = eb ? E1 : E0;
-    eb ^= 1;
-    E[s.base * L + s.x0] = v[0][0];
-    E[s.base * L + s.x1] = v[0][1];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < H - 1; ++r) {
-      v[r][0] = v[r + 1][0];
-      v[r][1] = v[r + 1][1];
-    }
-    v[H - 1][0] = E[s.ytop * L + s.x0];
-    v[H - 1][1] = E[s.ytop * L + s.x1];
-  }
-  // F4 in D
-#pragma unroll
-  for (int b = 0; b < NBY; ++b) {
-    bond2(v[2 * b][0], v[2 * b + 1][0], k.u4[b][0]);
-    bond2(v[2 * b][1], v[2 * b + 1][1], k.u4[b][1]);
-  }
 }
 
 template <class R, int MODE>
@@ -263,46 +69,7 @@ __global__ void __launch_bounds__((BlockThreads<R, NBY>::max), 1) mdagm_block_ke
   const bool active = tau < N;
 
   if (MODE == MODE_CGDIR) {
-    if (threadIdx.x < 32) {
-      CgState* st = a.st;
-      const int lane = threadIdx.x;
-      const int done = *(volatile int*)&st->done;
-      const int k = *(volatile int*)&st->k;
-      const int seg = st->seg_start;
-      int flags = 0;
-      double beta = 0.0;
-      int new_done = CG_RUNNING;
-      if (done != CG_RUNNING) {
-        flags = 1;
-      } else if (k >= st->maxit) {
-        flags = 1;
-        new_done = CG_MAXIT;
-      } else if (k == seg) {
-        flags = 2;
-      } else {
-        const double rr = warp_sum_partials(a.part_in, a.n_part_in);
-        if (!isfinite(rr)) {
-          flags = 1;
-          new_done = CG_NONFINITE;
-        } else if (rr <= st->tol2bb) {
-          flags = 1;
-          new_done = CG_REC_CONVERGED;
-        } else {
-          beta = rr / st->rr[(k - 1) & 1];
-        }
-        if (blockIdx.x == 0 && lane == 0) st->rr[k & 1] = rr;
-      }
-      if (blockIdx.x == 0 && lane == 0) {
-        if (new_done != CG_RUNNING) st->done = new_done;
-        if (!(flags & 1)) st->k2 = k;
-      }
-      if (lane == 0) {
-        s_flags = flags;
-        s_beta = (R)beta;
-        s_k = k;
-      }
-    }
-    __syncthreads();
+    cgdir_head<R>(a, s_flags, s_beta, s_k);
     if (s_flags & 1) return;  // uniform over the whole grid: no cluster barrier is pending
   }
   const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);
@@ -366,7 +133,7 @@ __global__ void __launch_bounds__((BlockThreads<R, NBY>::max), 1) mdagm_block_ke
   bcluster_wait();
   const T* Zprev = (rank == 0) ? Zh : cl.map_shared_rank(Zpub, rank - 1);
 
-  double acc = 0.0;
+  R acc = 0;  // FP32: the thread's few terms in float (cdot_re_own)
   if (active) {
     const R sig = (tau == 0) ? R(-1) : R(1);
     const R sigp = (tau == N - 1) ? R(-1) : R(1);
@@ -386,13 +153,13 @@ __global__ void __launch_bounds__((BlockThreads<R, NBY>::max), 1) mdagm_block_ke
         const T xt = (MODE == MODE_CGDIR) ? p_new[bt + s] : a.x[bt + s];
         const T q = caxpy(caxpy(xt, -sig * cB, Zprev[s]), cB, v[r][c]);
         a.y[bt + s] = q;
-        if (MODE == MODE_CGDIR) acc += cdot_re(xt, q);
+        if (MODE == MODE_CGDIR) acc += cdot_re_own(xt, q);
       }
     }
   }
   bcluster_arrive();  // finished reading the neighbour's shared memory
   if (MODE == MODE_CGDIR) {
-    const double t0 = block_sum(acc, red);
+    const double t0 = block_sum((double)acc, red);
     if (threadIdx.x == 0) a.part_out[blockIdx.x] = t0;
   }
   bcluster_wait();  // keep z_tau alive until the right neighbour has read it

@@ -1,0 +1,324 @@
+// Persistent tau-walking fused M^dagger M in FP32 (Methods, "Matrix-free
+// representation of M^dagger M v"; checkerboard of Eq. (eq24)).
+//
+// With B_tau = cB P_tau and z_tau = P_tau x_tau, row tau of M^dagger M is
+//   y_tau = t_tau + cB P_tau w_tau,
+//   t_tau = x_tau - s_tau cB z_{tau-1},   w_tau = cB z_tau - s'_tau x_{tau+1},
+// (s_0 = -1 and s'_{Ntau-1} = -1 carry the antiperiodic wrap; all others +1).
+// Each CTA owns a contiguous range [tb, te) of slices and walks it in order, so
+// the z_{tau-1} that row tau needs is the one it computed in the previous
+// step: a range of n slices costs 2n + 1 sweeps (one halo sweep at tb - 1) and
+// no inter-CTA exchange.  The slice is held in register strips (strip.cuh).
+//
+// Memory: step j reads theta_j and the vector slices at j + 1 once, through a
+// bulk asynchronous copy (cp.async.bulk, completion on an mbarrier) into a
+// shared-memory stage.  Each thread copies what it needs out of the stage
+// (its links and x_{j+1}), then one thread refills the stage for step j + 1
+// while the block runs the two sweeps of step j, so HBM streams under the
+// compute.  The vector read for the halo row tb - 1 is the only direct load.
+//
+// CG-direction mode forms p = r + beta p_old on the fly, writes p and q = O p,
+// and accumulates <p, q> = Re sum_tau [<x_tau, t_tau> + cB <z_tau, w_tau>]
+// (P is Hermitian, so <x, P w> = <P x, w>), one partial per CTA.
+//
+// Waits on the mbarrier are bounded (about one second of %globaltimer); on a
+// timeout the block writes NaN into its outputs, so the solve reports a
+// non-finite residual instead of hanging.
+#include "strip.cuh"
+
+namespace hqmc {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase with the given parity to complete; false after ~1 s.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+}  // namespace
+
+// Block sizes that leave room for the strip in registers.
+template <int NBY> struct WalkThreads {
+  static constexpr int max = NBY == 1 ? 768 : (NBY == 2 ? 512 : 384);
+};
+
+int walk_thread_cap(int nby) {
+  return nby == 1 ? WalkThreads<1>::max : nby == 2 ? WalkThreads<2>::max : nby == 3 ? WalkThreads<3>::max : 0;
+}
+
+// Shared memory: stage (theta + 1 or 2 vector slices), x_{j+1} copy, 2 exchange buffers.
+size_t walk_smem_bytes(const Geo& g, int mode) {
+  const int nv = mode == MODE_CGDIR ? 2 : 1;
+  return (size_t)(1 + nv + 1 + 2) * g.V * sizeof(float2);
+}
+
+template <int MODE, int NBY>
+__global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(const MdagmArgs<float> a) {
+  using T = float2;
+  constexpr int H = 2 * NBY;
+  constexpr int NV = MODE == MODE_CGDIR ? 2 : 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int V = a.g.V, N = a.g.Ntau, L = a.g.L;
+  float2* Sth = reinterpret_cast<float2*>(smem_raw);  // stage: theta_j
+  T* Sv0 = Sth + V;                                   // stage: x_{j+1}, or r_{j+1}
+  T* Sv1 = Sv0 + V;                                   // stage (CG direction): p_old_{j+1}
+  T* X1 = Sv0 + NV * V;                               // x_{j+1}, each thread's own sites (slot-major)
+  T* E0 = X1 + V;                                     // exchange buffers
+  T* E1 = E0 + V;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ double red[32];
+  __shared__ int s_flags;
+  __shared__ float s_beta;
+  __shared__ int s_k;
+
+  if (MODE == MODE_CGDIR) {
+    cgdir_head<float>(a, s_flags, s_beta, s_k);
+    if (s_flags & 1) return;  // uniform over the grid
+  }
+  const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);
+  const float beta = (MODE == MODE_CGDIR) ? s_beta : 0.f;
+  const T* p_old = nullptr;
+  T* p_new = nullptr;
+  if (MODE == MODE_CGDIR) {
+    p_old = (s_k & 1) ? a.pbuf[1] : a.pbuf[0];
+    p_new = (s_k & 1) ? a.pbuf[0] : a.pbuf[1];
+  }
+  const T* vsrc = MODE == MODE_CGDIR ? a.r : a.x;
+
+  const int G = gridDim.x;
+  const int tb = (int)((long long)blockIdx.x * N / G);
+  const int te = (int)((long long)(blockIdx.x + 1) * N / G);
+  auto wrap = [N](int j) { return j < 0 ? j + N : (j >= N ? j - N : j); };
+
+  const uint32_t slice_bytes = (uint32_t)V * (uint32_t)sizeof(T);
+  const uint32_t stage_bytes = slice_bytes * (1 + ((MODE == MODE_CGDIR && !first) ? 2 : 1));
+  auto issue = [&](int j) {  // stage of step j: theta_j and the vectors of slice j + 1
+    const size_t sj = (size_t)wrap(j) * V, sn = (size_t)wrap(j + 1) * V;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&bar, stage_bytes);
+    bulk_load(Sth, a.th32 + sj, slice_bytes, &bar);
+    bulk_load(Sv0, vsrc + sn, slice_bytes, &bar);
+    if (MODE == MODE_CGDIR && !first) bulk_load(Sv1, p_old + sn, slice_bytes, &bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    issue(tb - 1);
+  }
+
+  const StripGeo sg = strip_geo<NBY>(L);
+  const float cB = a.cB;
+  const float t1 = (float)a.t1, t2 = (float)a.t2;
+  int eb = 0;
+  T v[H][2], t[H][2];
+  StripLinks<T, NBY> lk;
+  double acc = 0.0;
+
+  {  // x_{tb-1}, the halo row (p is formed exactly as its owner forms it)
+    const size_t base = (size_t)wrap(tb - 1) * V;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      const int y = drow(sg, r, H);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const size_t gi = base + y * L + (c ? sg.x1 : sg.x0);
+        T xv = vsrc[gi];
+        if (MODE == MODE_CGDIR && !first) xv = caxpy(xv, beta, p_old[gi]);
+        v[r][c] = xv;
+      }
+    }
+  }
+  __syncthreads();  // the mbarrier is initialised before anyone waits on it
+
+  uint32_t parity = 0;
+  bool ok = true;
+  for (int j = tb - 1; j < te; ++j) {
+    ok = ok && mbar_wait_bounded(&bar, parity);
+    parity ^= 1;
+    if (ok) {
+      load_strip_links_smem<NBY>(sg, Sth, t1, t2, lk);
+      const size_t bn = (size_t)wrap(j + 1) * V;
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        const int y = drow(sg, r, H);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int s = y * L + (c ? sg.x1 : sg.x0);
+          T xv = Sv0[s];
+          if (MODE == MODE_CGDIR && !first) xv = caxpy(xv, beta, Sv1[s]);
+          X1[(2 * r + c) * blockDim.x + threadIdx.x] = xv;
+          if (MODE == MODE_CGDIR && j + 1 < te) p_new[bn + s] = xv;
+        }
+      }
+    }
+    if (!__syncthreads_and(ok)) {  // uniform: every thread leaves together
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0 && j + 1 < te) issue(j + 1);
+
+    float accj = 0.f;  // this step's terms, in float (cdot_re_own)
+    if (MODE == MODE_CGDIR && j >= tb) {
+#pragma unroll
+      for (int r = 0; r < H; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) accj += cdot_re_own(v[r][c], t[r][c]);
+    }
+    strip_sweep(v, lk, sg, E0, E1, eb);  // z_j
+    const float sn = (wrap(j + 1) == 0) ? -1.f : 1.f;  // s_{j+1}
+    if (j < tb) {  // halo step: only t_{tb} is needed
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        const int y = drow(sg, r, H);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const T xn = X1[(2 * r + c) * blockDim.x + threadIdx.x];
+          t[r][c] = caxpy(xn, -sn * cB, v[r][c]);
+          v[r][c] = xn;
+        }
+      }
+      continue;
+    }
+    const float sp = (wrap(j) == N - 1) ? -1.f : 1.f;  // s'_j
+    T tn[H][2];
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      const int y = drow(sg, r, H);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T xn = X1[(2 * r + c) * blockDim.x + threadIdx.x];
+        const T w = caxpy(cscale(cB, v[r][c]), -sp, xn);
+        if (MODE == MODE_CGDIR) accj += cB * cdot_re_own(v[r][c], w);
+        tn[r][c] = caxpy(xn, -sn * cB, v[r][c]);
+        v[r][c] = w;
+      }
+    }
+    strip_sweep(v, lk, sg, E0, E1, eb);  // P_j w_j
+    const size_t bj = (size_t)wrap(j) * V;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      const int y = drow(sg, r, H);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int s = y * L + (c ? sg.x1 : sg.x0);
+        a.y[bj + s] = caxpy(t[r][c], cB, v[r][c]);
+        t[r][c] = tn[r][c];
+        v[r][c] = X1[(2 * r + c) * blockDim.x + threadIdx.x];
+      }
+    }
+    acc += (double)accj;
+  }
+
+  if (!ok) {
+    // A stage never arrived: poison this block's outputs so the caller sees a
+    // non-finite result, then give the copy in flight a bounded chance to land.
+    const T nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    for (int j = tb; j < te; ++j)
+      for (int s = threadIdx.x; s < V; s += blockDim.x) a.y[(size_t)j * V + s] = nan2;
+    acc = __longlong_as_double(0x7ff8000000000000ll);
+    mbar_wait_bounded(&bar, parity ^ 1);
+  }
+  if (MODE == MODE_CGDIR) {
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) a.part_out[blockIdx.x] = tot;
+  }
+}
+
+template <int MODE, int NBY>
+static cudaError_t walk_launch(const SliceLaunch& sl, const MdagmArgs<float>& a, cudaStream_t s) {
+  const size_t smem = walk_smem_bytes(sl.g, MODE);
+  mdagm_walk_kernel<MODE, NBY><<<sl.grid, sl.threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int NBY>
+static cudaError_t walk_prepare(const SliceLaunch& sl) {
+  return raise_smem_limit(mdagm_walk_kernel<MODE, NBY>, walk_smem_bytes(sl.g, MODE));
+}
+
+template <int MODE>
+cudaError_t launch_mdagm_walk(const SliceLaunch& sl, const MdagmArgs<float>& a, cudaStream_t s) {
+  if (sl.grid < 1 || sl.grid > sl.g.Ntau) return cudaErrorInvalidValue;
+  switch (sl.nby) {
+    case 1: return walk_launch<MODE, 1>(sl, a, s);
+    case 2: return walk_launch<MODE, 2>(sl, a, s);
+    case 3: return walk_launch<MODE, 3>(sl, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MODE>
+cudaError_t prepare_mdagm_walk(const SliceLaunch& sl) {
+  switch (sl.nby) {
+    case 1: return walk_prepare<MODE, 1>(sl);
+    case 2: return walk_prepare<MODE, 2>(sl);
+    case 3: return walk_prepare<MODE, 3>(sl);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// CTAs of this shape the device keeps resident per SM (0: none fit).
+int mdagm_walk_blocks_per_sm(const SliceLaunch& sl) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  const size_t smem = walk_smem_bytes(sl.g, MODE_CGDIR);
+  switch (sl.nby) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 1>, sl.threads, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 2>, sl.threads, smem); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 3>, sl.threads, smem); break;
+    default: break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template cudaError_t launch_mdagm_walk<MODE_APPLY>(const SliceLaunch&, const MdagmArgs<float>&, cudaStream_t);
+template cudaError_t launch_mdagm_walk<MODE_CGDIR>(const SliceLaunch&, const MdagmArgs<float>&, cudaStream_t);
+template cudaError_t prepare_mdagm_walk<MODE_APPLY>(const SliceLaunch&);
+template cudaError_t prepare_mdagm_walk<MODE_CGDIR>(const SliceLaunch&);
+
+}  // namespace hqmc

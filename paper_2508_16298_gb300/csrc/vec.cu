@@ -24,24 +24,27 @@ __global__ void links_kernel(Geo g, const double* __restrict__ theta, double t1,
     const int s = (int)(i % g.V);
     const int x = s % g.L;
     const double2 th = reinterpret_cast<const double2*>(theta)[i];
-    double sx, cx, sy, cy;
-    sincos(th.x, &sx, &cx);
-    sincos(th.y, &sy, &cy);
-    const double tx = (x & 1) ? t2 : t1;
-    const double2 ux = make_double2(tx * cx, tx * sx);
-    const double2 uy = make_double2(t2 * cy, t2 * sy);
-    if (U64) {
-      U64[2 * i] = ux;
-      U64[2 * i + 1] = uy;
-    }
-    if (U32) {
-      U32[2 * i] = make_float2((float)ux.x, (float)ux.y);
-      U32[2 * i + 1] = make_float2((float)uy.x, (float)uy.y);
+    if (U64 || U32) {  // FP64 sincos is costly on this GPU: only when a link table is wanted
+      double sx, cx, sy, cy;
+      sincos(th.x, &sx, &cx);
+      sincos(th.y, &sy, &cy);
+      const double tx = (x & 1) ? t2 : t1;
+      const double2 ux = make_double2(tx * cx, tx * sx);
+      const double2 uy = make_double2(t2 * cy, t2 * sy);
+      if (U64) {
+        U64[2 * i] = ux;
+        U64[2 * i + 1] = uy;
+      }
+      if (U32) {
+        U32[2 * i] = make_float2((float)ux.x, (float)ux.y);
+        U32[2 * i + 1] = make_float2((float)uy.x, (float)uy.y);
+      }
     }
     if (th32) {
-      // 2 pi periodicity of the links: wrap before rounding to float
-      const double w = 6.283185307179586;
-      th32[i] = make_float2((float)(th.x - w * rint(th.x / w)), (float)(th.y - w * rint(th.y / w)));
+      // 2 pi periodicity of the links: wrap before rounding to float (any
+      // representative of theta mod 2 pi gives the same link)
+      const double w = 6.283185307179586, iw = 0.15915494309189535;
+      th32[i] = make_float2((float)(th.x - w * rint(th.x * iw)), (float)(th.y - w * rint(th.y * iw)));
     }
   }
 }
@@ -95,7 +98,7 @@ __device__ __forceinline__ void cg_update_body(const UpdArgs<R>& u, const int j,
   if (s_stop) return;
   const R alpha = (R)s_alpha;
   const C2<R>* __restrict__ p = ((s_k + 1) & 1) ? u.p1 : u.p0;
-  double acc = 0.0;
+  R acc = 0;  // FP32: a thread's few terms in float (cdot_re_own)
   for (long long i = j * (long long)blockDim.x + threadIdx.x; i < u.n; i += (long long)nblocks * blockDim.x) {
     const C2<R> pv = p[i];
     C2<R> rv = caxpy(u.r[i], -alpha, u.q[i]);
@@ -107,9 +110,9 @@ __device__ __forceinline__ void cg_update_body(const UpdArgs<R>& u, const int j,
       float2* xf = reinterpret_cast<float2*>(u.x);
       xf[i] = caxpy(xf[i], (float)alpha, make_float2(pv.x, pv.y));
     }
-    acc += cdot_re(rv, rv);
+    acc += cdot_re_own(rv, rv);
   }
-  const double t = block_sum(acc, red);
+  const double t = block_sum((double)acc, red);
   if (threadIdx.x == 0) {
     u.part_rr[j] = t;
     if (j == 0) st->k = st->k2 + 1;
@@ -204,8 +207,8 @@ __global__ void resid_finalize_kernel(const double* __restrict__ part, int n, in
     bool stalled = false;
     if (mode == FIN_RELIABLE) {
       const int nr = st->n_rel;
-      stalled = nr >= 4 && rr > 1e-2 * st->rr_rel[nr & 3];
-      st->rr_rel[nr & 3] = rr;
+      stalled = nr >= 8 && rr > 0.25 * st->rr_rel[nr & 7];
+      st->rr_rel[nr & 7] = rr;
       st->n_rel = nr + 1;
     }
     // the iteration budget is the one set at the start of the solve

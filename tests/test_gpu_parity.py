@@ -65,14 +65,26 @@ def test_apply_M_fp64(hq, L, N, dagger):
     assert rel(y, oracle.apply_M(lat, th, x, dagger=dagger)) < 1e-12
 
 
-@pytest.mark.parametrize("L,N", [(4, 5), (8, 40), (12, 7), (24, 240), (48, 480), (66, 660)])
-@pytest.mark.parametrize("variant", [1, 0])
+FP32_CASES = [(4, 5), (6, 2), (8, 40), (10, 9), (12, 7), (24, 240), (48, 480), (66, 660)]
+
+
+@pytest.mark.parametrize("L,N", FP32_CASES)
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_apply_fp32(hq, L, N, variant):
+    """variant 1: generic kernel; 2: register-blocked; 3: persistent tau-walking
+    (Ntau below, equal to and above the SM count: one slice per CTA and uneven ranges)."""
     lat = oracle.Lattice(L, N)
     th = inputs.theta_hot(L, N, seed=5000 + L)
     x = inputs.complex_gaussian(L, N, seed=6000 + L).astype(np.complex64)
     xo = x.astype(np.complex128)
-    with hq.Config(L, N, variant=variant) as cfg:
+    try:
+        cfg = hq.Config(L, N, variant=variant)
+    except hq.HQMCError as e:
+        assert e.status == hq.EUNSUPPORTED and variant == 2  # no FP64 strip shape at this L
+        pytest.skip("no register-blocked shape for this L")
+    with cfg:
+        if variant == 3:
+            assert cfg.launch_shape(hq.FP32)["variant"] > 100
         y = hq.apply_MdagM(cfg, cuda(th), cuda(x)).cpu().numpy()
         ym = hq.apply_M(cfg, cuda(th), cuda(x), dagger=True).cpu().numpy()
     assert y.dtype == np.complex64
@@ -331,7 +343,7 @@ def test_cg_with_each_kernel_variant(hq):
     th = inputs.theta_hot(L, N, seed=191)
     phi = inputs.complex_gaussian(L, N, seed=192)
     Xo, it_o, _, _ = oracle.cg(lat, th, phi, tol=1e-12)
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         with hq.Config(L, N, variant=variant) as cfg:
             X, info = hq.cg_solve(cfg, cuda(th), cuda(phi), tol=1e-12)
             Xm, infom = hq.cg_solve(cfg, cuda(th), cuda(phi), tol=1e-9, solver="mixed")
