@@ -4,9 +4,17 @@ A step is one HMC trajectory of the whole path (Philox draws, phi = M^dagger R,
 N_lf + 1 CG solves of (M^dagger M) X = phi, forces, leapfrog, Metropolis) on a
 seeded synthetic gauge field; the chain continues from step to step.
 
-Default workload (plain FP64 GPU HMC): L = 24, Ntau = 240 (138,240 sites),
-dtau = 0.1, t = 1, J = 1, compact action, CG to a true FP64 residual of 1e-8,
-20 leapfrog steps of dt = 0.0005.  Start (inputs.theta_ordered with tau_walk=0):
+Default workload (learned + mixed precision against plain FP64): L = 66,
+Ntau = 660 (2,874,960 sites), dtau = 0.1, t = 1, J = 1, compact action, CG to a
+true FP64 residual of 1e-8, 20 leapfrog steps of dt = 0.0005 * sqrt(138240 /
+sites).  Before timing, the chain runs 16 mixed-precision trajectories and after
+each forms one (theta, phi, x) triple; the net is trained on them (Adam, 12
+epochs).  The timed steps use the learned solver; the same chain state is then
+advanced with plain FP64 CG (same draws, dt, N_lf, tolerance) for the
+comparison, and the fused M^dagger M apply is timed alone with L2 flushed.
+
+Workload hmc_fp64_L24_Nt240 (plain FP64 GPU HMC): L = 24, Ntau = 240 (138,240
+sites), CG to 1e-8, 20 leapfrog steps of dt = 0.0005.  Start (inputs.theta_ordered with tau_walk=0):
 the pi-flux background favoured by half-filled fermions plus N(0, 0.3^2) on every
 bond, the same at every tau, under a random gauge transformation.  A start
 i.i.d. on every bond and slice makes M^dagger M so singular at this size that
@@ -53,14 +61,21 @@ WORKLOADS = {
 BATCH_LATTICES = [(L, 10 * L) for L in (12, 16, 20, 24) for _ in range(8)]
 WORKLOADS["batched_32chains_L12-24"] = dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.0005, tol=1e-8,
                                             solver="cg64", seed=100, start="cold", batched=True)
-DEFAULT_WORKLOAD = "hmc_fp64_L24_Nt240"
+# learned + mixed precision at L = 66, Ntau = 660 against plain FP64 on the same chain state: the net is
+# trained (untimed) on (theta, phi, x) triples the sampler produces at this size; dt keeps |dH| ~ V dt^2
+# as at L = 24
+WORKLOADS["hmc_learned_fp32_L66_Nt660"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, J=1.0, nsteps=20,
+                                               dt=round(0.0005 * (138240 / 2874960) ** 0.5, 7), tol=1e-8,
+                                               solver="plearned", seed=1, start="cold", compare="cg64",
+                                               triples=16, epochs=12, lr=1e-3)
+DEFAULT_WORKLOAD = "hmc_learned_fp32_L66_Nt660"
 
 # Algorithmic work of one launch of the fused M^dagger M kernel in CG mode, per site:
 #   flops: 2 sweeps x 7 factor passes x 8 flops + 22 (direction update, combination, <p, Op>)
 #   bytes (FP64): links 32 + r 16 + p_old 16 + p_new 16 + q 16
 #   bytes (FP32, register-blocked): theta as float 8 + r 8 + p_old 8 + p_new 8 + q 8
 MDAGM_FLOPS_PER_SITE = 134
-MDAGM_BYTES_PER_SITE = {"cg64": 96, "mixed": 40, "learned": 40}
+MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pmixed": 40, "plearned": 40}
 
 
 def _peaks():
@@ -129,14 +144,21 @@ class ClockSampler:
 
 
 def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10):
-    """Times the FP64 CPU oracle on a bounded sample of one trajectory: max_iters CG
-    iterations and one force evaluation at the workload's size, scaled to one
-    trajectory with its_per_traj CG iterations and nsteps + 1 forces."""
+    """Times the FP64 CPU oracle on a bounded sample of one trajectory: max_iters
+    iterations of the workload's CG (preconditioned with the oracle's tau-line
+    preconditioner when the workload's solver is) and one force evaluation at the
+    workload's size, scaled to one trajectory with its_per_traj CG iterations and
+    nsteps + 1 forces."""
     import oracle
+    from oracle import precond as opc
 
     lat = oracle.Lattice(wl["L"], wl["Ntau"], dtau=wl["dtau"], t=wl["t"], J=wl["J"])
+    pc = wl["solver"].startswith("p")
     t0 = time.perf_counter()
-    X, it, _, _ = oracle.cg(lat, theta, phi, tol=1e-30, maxit=max_iters)
+    if pc:
+        X, it, _ = opc.pcg(lat, theta, phi, opc.coefficients(lat), tol=1e-30, maxit=max_iters)
+    else:
+        X, it, _, _ = oracle.cg(lat, theta, phi, tol=1e-30, maxit=max_iters)
     t1 = time.perf_counter()
     oracle.fermion_dS(lat, theta, X)
     oracle.bosonic_dS(lat, theta)
@@ -144,15 +166,18 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
     t_iter = (t1 - t0) / (it + 2)  # it iterations plus the initial and final residual applications
     t_force = t2 - t1
     t_traj = its_per_traj * t_iter + (wl["nsteps"] + 1) * t_force
+    kind = "preconditioned CG" if pc else "CG"
     return {"traj_s": t_traj, "t_iter_s": t_iter, "t_force_s": t_force, "cores": oracle.num_threads(),
-            "sample": f"{it} oracle CG iterations + 1 force at L={wl['L']}, Ntau={wl['Ntau']}, "
-                      f"scaled to {its_per_traj:.0f} CG iterations and {wl['nsteps'] + 1} forces per trajectory"}
+            "sample": f"{it} oracle {kind} iterations + 1 force at L={wl['L']}, Ntau={wl['Ntau']}, "
+                      f"scaled to {its_per_traj:.0f} iterations and {wl['nsteps'] + 1} forces per trajectory"}
 
 
 # CG iterations per trajectory used to scale oracle samples when no GPU run is
 # available (the reference arm); measured on the GPU with the same algorithm.
-ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 11000.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 40000.0,
-                     "batched_32chains_L12-24": 11000.0}
+ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 11000.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 16500.0,
+                     "batched_32chains_L12-24": 11000.0, "hmc_learned_fp32_L66_Nt660": 2640.0}
+# oracle CG iterations per bounded sample (the largest lattices take about a second per iteration on the host)
+ORACLE_SAMPLE_ITERS = {"hmc_learned_fp32_L66_Nt660": 4, "hmc_mixed_L48_Nt480": 6}
 
 
 def run_reference(args, wl_name, wl, rank, world):
@@ -167,9 +192,10 @@ def run_reference(args, wl_name, wl, rank, world):
     R = inputs.complex_gaussian(wl["L"], wl["Ntau"], wl["seed"] + 1)
     phi = oracle.apply_M(lat, theta, R, dagger=True)
     its = ITS_PER_TRAJ_HINT[wl_name]
+    n_it = ORACLE_SAMPLE_ITERS.get(wl_name, 10)
     for _ in range(args.warmup):
-        oracle_sample(wl, its, theta, phi, max_iters=2)
-    samples = [oracle_sample(wl, its, theta, phi) for _ in range(args.steps)]
+        oracle_sample(wl, its, theta, phi, max_iters=1)
+    samples = [oracle_sample(wl, its, theta, phi, max_iters=n_it) for _ in range(args.steps)]
     t = statistics.median(s["traj_s"] for s in samples)
     value = 1.0 / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world,
@@ -193,6 +219,17 @@ def start_theta(wl, seed):
     return inputs.theta_warm(wl["L"], wl["Ntau"], seed, J=wl["J"], dtau=wl["dtau"])
 
 
+SOLVER_TEXT = {
+    "cg64": "cg64: FP64 CG",
+    "pcg64": "pcg64: FP64 CG preconditioned with the tau-line preconditioner",
+    "mixed": "mixed: FP32 M^dagger M in CG, FP64 reliable updates every 50 iterations",
+    "pmixed": "pmixed: the mixed solver preconditioned with the tau-line preconditioner (FP32)",
+    "learned": "learned: net-corrected initial guess (kept if it lowers the FP64 residual), then the mixed solver",
+    "plearned": "plearned: net-corrected initial guess (kept if it lowers the FP64 residual), then the mixed "
+                "solver preconditioned with the tau-line preconditioner (FP32)",
+}
+
+
 def config_of(wl_name, wl):
     return {"workload": wl_name, "L": wl["L"], "Ntau": wl["Ntau"], "sites": wl["L"] * wl["L"] * wl["Ntau"],
             "dtau": wl["dtau"], "t": wl["t"], "J": wl["J"], "action": "compact",
@@ -202,8 +239,66 @@ def config_of(wl_name, wl):
                                  "J*dtau/2) + random gauge transformation",
                       "cold": "pi-flux + N(0, 0.3^2) per bond, tau-independent, + random gauge transformation"}
                      [wl["start"]],
-            "n_leapfrog": wl["nsteps"], "dt": wl["dt"], "cg_tol": wl["tol"], "solver": wl["solver"],
+            "n_leapfrog": wl["nsteps"], "dt": wl["dt"], "cg_tol": wl["tol"],
+            "solver": SOLVER_TEXT[wl["solver"]],
             "l2": "flushed between timed steps (512 MiB write; step times exclude the flush)"}
+
+
+def kernel_name(shape, prec):
+    v = shape["variant"]
+    if v >= 100:
+        return f"mdagm_walk_kernel<{prec}, CG direction, nby={v - 100}> (tau-walking, {shape['threads']} threads)"
+    if v > 0:
+        return f"mdagm_block_kernel<{prec}, CG direction, nby={v}> (cluster {shape['cluster']})"
+    return f"mdagm_kernel<{prec}, CG direction, mb={-v}> (cluster {shape['cluster']})"
+
+
+def train_net(hqmc, inputs, cfg, wl, theta, seed, dev):
+    """Untimed set-up of the learned solver: the chain runs `triples` mixed-precision
+    trajectories; after each, phi = M^dagger R with a fresh R and x = (M^dagger M)^{-1} phi
+    (FP64 residual 1e-8) form one training triple; the net then takes `epochs` Adam
+    passes over them.  Returns the net and a short report."""
+    import torch
+    L, N = wl["L"], wl["Ntau"]
+    kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver="pmixed")
+    trips = []
+    t0 = time.perf_counter()
+    for k in range(wl["triples"]):
+        hqmc.trajectory(cfg, theta, seed=seed, traj_counter=10 ** 6 + k, **kw)
+        R = torch.from_numpy(inputs.complex_gaussian(L, N, seed * 7919 + k)).to(dev)
+        phi = hqmc.apply_M(cfg, theta, R, dagger=True)
+        x, _ = hqmc.cg_solve(cfg, theta, phi, tol=wl["tol"], solver="pmixed")
+        trips.append((theta.clone(), phi, x))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = hqmc.Net(seed=seed)
+    first = last = None
+    for ep in range(wl["epochs"]):
+        losses = [net.train_step(cfg, th, ph, x, lr=wl["lr"]) for th, ph, x in trips]
+        first = statistics.mean(losses) if first is None else first
+        last = statistics.mean(losses)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    hqmc.set_preconditioner(cfg, net)
+    return net, {"triples": len(trips), "epochs": wl["epochs"], "sampler_s": round(t1 - t0, 2),
+                 "train_s": round(t2 - t1, 2), "loss_first_epoch": round(first, 4), "loss_last_epoch": round(last, 4),
+                 "loss": "||K(theta) phi - x||^2 / ||x||^2"}
+
+
+def time_apply(hqmc, cfg, theta, x, flush, timer, reps=20):
+    """Average device time of the fused M^dagger M kernel alone (library event timer)
+    over reps applies, L2 flushed before each."""
+    import torch
+    y = torch.empty_like(x)
+    hqmc.apply_MdagM(cfg, theta, x, y=y)
+    hqmc.set_timing(cfg, True)
+    hqmc.get_timing(cfg, timer)
+    for k in range(reps):
+        flush.fill_(float(k))
+        hqmc.apply_MdagM(cfg, theta, x, y=y)
+    n, ms = hqmc.get_timing(cfg, timer)
+    hqmc.set_timing(cfg, False)
+    return 1e3 * ms / max(n, 1)
 
 
 def run_ours(args, wl_name, wl, rank, world, local_rank):
@@ -217,21 +312,26 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     L, N = wl["L"], wl["Ntau"]
+    sites = L * L * N
     cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True)
     seed = wl["seed"] + 1000 * rank
     theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver=wl["solver"])
+    learned = None
+    net = None
+    if wl["solver"] in ("learned", "plearned"):
+        net, learned = train_net(hqmc, inputs, cfg, wl, theta, seed, dev)
 
     for k in range(args.warmup):
         hqmc.trajectory(cfg, theta, seed=seed, traj_counter=k, **kw)
     fp64_tflops = hqmc.probe_fp64_rate(cfg) if rank == 0 else None
+    theta_start = theta.clone()  # chain state at the start of the timed region (for the FP64 arm)
 
     # ---- device-resident timed region --------------------------------------
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos = []
-    gpu_id = None
     try:
         props = torch.cuda.get_device_properties(dev)
         gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else str(local_rank)
@@ -259,10 +359,13 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     # ---- dominant kernel: CUDA events around every launch of the fused M^dagger M
     # during one more trajectory (event timing runs the CG loop bodies from the
     # host, since per-launch events cannot sit inside the device-side loop) ----
+    fp32 = wl["solver"] not in ("cg64", "pcg64")
     flush.zero_()
     hqmc.set_timing(cfg, True)
     hqmc.trajectory(cfg, theta, seed=seed, traj_counter=args.warmup + args.steps, **kw)
-    n_md, md_ms = hqmc.get_timing(cfg, hqmc.TIMER_MDAGM if wl["solver"] == "cg64" else hqmc.TIMER_MDAGM32)
+    n_md, md_ms = hqmc.get_timing(cfg, hqmc.TIMER_MDAGM32 if fp32 else hqmc.TIMER_MDAGM)
+    n_up, up_ms = hqmc.get_timing(cfg, hqmc.TIMER_CG_UPDATE)
+    n_pc, pc_ms = hqmc.get_timing(cfg, hqmc.TIMER_PRECOND)
     hqmc.set_timing(cfg, False)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -278,7 +381,7 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         th_dev = theta_h.to(dev, non_blocking=True)
-        info = hqmc.trajectory(cfg, th_dev, seed=seed, traj_counter=args.warmup + args.steps + 1 + k, **kw)
+        hqmc.trajectory(cfg, th_dev, seed=seed, traj_counter=args.warmup + args.steps + 1 + k, **kw)
         theta_h.copy_(th_dev, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -288,45 +391,85 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
         e2e_s = float(t.item())
     e2e_value = world * e2e_steps / e2e_s
 
+    # ---- plain FP64 on the same chain state (same draws, dt, N_lf, tolerance) -----
+    compare = None
+    if wl.get("compare"):
+        kw64 = dict(kw, solver=wl["compare"])
+        th64 = theta_start.clone()
+        hqmc.trajectory(cfg, th64.clone(), seed=seed, traj_counter=10 ** 7, **kw64)  # warm-up
+        n64 = min(2, args.steps)
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
+        inf64 = []
+        for k in range(n64):
+            flush.zero_()
+            ev64[k][0].record(stream)
+            inf64.append(hqmc.trajectory(cfg, th64, seed=seed, traj_counter=args.warmup + k, **kw64))
+            ev64[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms64 = [a.elapsed_time(b) for a, b in ev64]
+        v64 = n64 / (sum(ms64) / 1e3)
+        compare = {"solver": wl["compare"], "traj_per_s": v64, "speedup": (value / world) / v64,
+                   "steps": n64, "same_draws_as_steps": list(range(n64)),
+                   "acceptance": statistics.mean(i["accepted"] for i in inf64),
+                   "cg_iterations_per_traj": statistics.mean(i["cg_iterations"] for i in inf64),
+                   "dH": [round(i["dH"], 6) for i in inf64],
+                   "max_true_residual": max(i["max_true_residual"] for i in inf64),
+                   "step_ms": [round(m, 3) for m in ms64]}
+
+    # ---- the fused M^dagger M apply alone, L2 flushed: FP32 against HBM, FP64 against the FP64 rate
+    x32 = torch.from_numpy(inputs.complex_gaussian(L, N, 77).astype(np.complex64)).to(dev)
+    x64 = torch.from_numpy(inputs.complex_gaussian(L, N, 78)).to(dev)
+    us32 = time_apply(hqmc, cfg, theta, x32, flush, hqmc.TIMER_MDAGM32)
+    us64 = time_apply(hqmc, cfg, theta, x64, flush, hqmc.TIMER_MDAGM)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    apply = {"sites": sites,
+             "fp32": {"kernel": kernel_name(cfg.launch_shape(hqmc.FP32), "float").replace("CG direction", "apply"),
+                      "us": round(us32, 2), "bytes_per_site": 24, "gbs": 24 * sites / us32 / 1e3,
+                      "frac_of_measured_hbm": 24 * sites / us32 / 1e3 / hbm},
+             "fp64": {"kernel": kernel_name(cfg.launch_shape(hqmc.FP64), "double").replace("CG direction", "apply"),
+                      "us": round(us64, 2), "flops_per_site": 126, "tflops": 126 * sites / us64 / 1e6,
+                      "frac_of_fp64_rate": 126 * sites / us64 / 1e6 / fp64_tflops if fp64_tflops else None},
+             "method": "20 applies, L2 flushed before each (512 MiB write), kernel time from the library's CUDA events"}
+
     if rank != 0:
         return
     its = [i["cg_iterations"] for i in infos]
     its_per_traj = statistics.mean(its)
     md_avg_ms = md_ms / max(n_md, 1)
-    sites = L * L * N
     achieved_tflops = MDAGM_FLOPS_PER_SITE * sites / (md_avg_ms * 1e-3) / 1e12
     achieved_gbs = MDAGM_BYTES_PER_SITE[wl["solver"]] * sites / (md_avg_ms * 1e-3) / 1e9
-    peaks = _peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    fp32 = wl["solver"] != "cg64"
-    shape = cfg.launch_shape(hqmc.FP64 if wl["solver"] == "cg64" else hqmc.FP32)
-    kname = (f"mdagm_block_kernel<{'double' if wl['solver'] == 'cg64' else 'float'}, CG direction, nby={shape['variant']}>"
-             if shape["variant"] > 0 else
-             f"mdagm_kernel<{'double' if wl['solver'] == 'cg64' else 'float'}, CG direction, mb={-shape['variant']}>")
+    shape = cfg.launch_shape(hqmc.FP32 if fp32 else hqmc.FP64)
+    kname = kernel_name(shape, "float" if fp32 else "double")
     if fp32:  # the FP32 fused kernel is bounded by HBM bandwidth
-        roofline = {"kernel": kname, "cluster": shape["cluster"], "bound": "hbm", "achieved": achieved_gbs,
+        roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved_gbs,
                     "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm, "traffic": None,
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                    "tflops_algorithmic": achieved_tflops, "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms}
+                    "bytes_per_site": MDAGM_BYTES_PER_SITE[wl["solver"]], "sites_per_launch": sites,
+                    "tflops_algorithmic": achieved_tflops, "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms,
+                    "cg_update_avg_us": 1e3 * up_ms / max(n_up, 1),
+                    "precond_avg_us": 1e3 * pc_ms / n_pc if n_pc else None}
     else:
-        roofline = {"kernel": kname, "cluster": shape["cluster"], "bound": "alu", "achieved": achieved_tflops,
+        roofline = {"kernel": kname, "bound": "alu", "achieved": achieved_tflops,
                     "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_tflops,
                     "traffic": None,
                     "peak_note": "FP64 FMA rate measured on this GPU by hqmc_probe_fp64_rate",
+                    "flops_per_site": MDAGM_FLOPS_PER_SITE, "sites_per_launch": sites,
                     "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / hbm,
-                    "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms}
+                    "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms, "cg_update_avg_us": 1e3 * up_ms / max(n_up, 1),
+                    "precond_avg_us": 1e3 * pc_ms / n_pc if n_pc else None}
 
     # ---- oracle on the host cores: bounded sample --------------------------
     import oracle
     lat = oracle.Lattice(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"])
     th_np = start_theta(wl, wl["seed"])
     phi_np = oracle.apply_M(lat, th_np, inputs.complex_gaussian(L, N, wl["seed"] + 1), dagger=True)
-    cb = oracle_sample(wl, its_per_traj, th_np, phi_np)
+    cb = oracle_sample(wl, its_per_traj, th_np, phi_np, max_iters=ORACLE_SAMPLE_ITERS.get(wl_name, 10))
 
     line = {
         "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
         "config": config_of(wl_name, wl),
         "e2e": {"value": e2e_value, "unit": "traj/s", "h2d_bytes_per_step": bytes_theta,
                 "d2h_bytes_per_step": bytes_theta, "steps": e2e_steps},
@@ -340,8 +483,16 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
         "dH": [round(i["dH"], 6) for i in infos],
         "max_true_residual": max(i["max_true_residual"] for i in infos),
         "step_ms": [round(s, 3) for s in step_ms],
+        "apply": apply,
     }
+    if compare:
+        line["vs_plain_fp64"] = compare
+    if learned:
+        line["learned"] = learned
     print(json.dumps(line), flush=True)
+    if net is not None:
+        hqmc.set_preconditioner(cfg, None)
+        net.close()
 
 
 def run_batched(args, wl_name, wl, rank, world, local_rank):
@@ -409,8 +560,14 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
 
 
 def run_profile_case(wl):
-    """A short, fixed sequence for ncu captures: three fused M^dagger M applies and
-    a 40-iteration CG solve at the workload's size (no JSON output)."""
+    """A short, fixed sequence for ncu captures at the workload's size, with the CG
+    loop driven from the host (kernels inside a graph with conditional nodes cannot
+    be profiled one by one) and the default launch shapes (an autotuner timed under
+    a profiler would not pick the bench's shapes): three fused M^dagger M applies in
+    the workload's precision, then one trajectory of 2 leapfrog steps with the
+    workload's solver and dt (the learned one with a freshly initialised net; its
+    cost does not depend on the weights).  Prints no JSON."""
+    import numpy as np
     import torch
 
     import __graft_entry__
@@ -418,16 +575,23 @@ def run_profile_case(wl):
     from paper_2508_16298_gb300 import hqmc, inputs
 
     L, N = wl["L"], wl["Ntau"]
-    with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True) as cfg:
-        # event timing makes the CG loop host-driven, so a profiler sees each kernel
-        # (kernels inside a graph with conditional nodes cannot be profiled one by one)
+    with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"]) as cfg:
         hqmc.set_timing(cfg, True)
         theta = torch.from_numpy(start_theta(wl, wl["seed"])).cuda()
         x = torch.from_numpy(inputs.complex_gaussian(L, N, 2)).cuda()
+        xa = x.to(torch.complex64) if wl["solver"] not in ("cg64", "pcg64") else x
         for _ in range(3):
-            hqmc.apply_MdagM(cfg, theta, x)
-        hqmc.cg_solve(cfg, theta, x, tol=1e-30, maxit=40, solver=wl["solver"], raise_on_fail=False)
+            hqmc.apply_MdagM(cfg, theta, xa)
+        net = None
+        if wl["solver"] in ("learned", "plearned"):
+            net = hqmc.Net(seed=1)
+            hqmc.set_preconditioner(cfg, net)
+        hqmc.trajectory(cfg, theta, seed=wl["seed"], traj_counter=0, nsteps=2, dt=wl["dt"], tol=wl["tol"],
+                        solver=wl["solver"])
         torch.cuda.synchronize()
+        if net is not None:
+            hqmc.set_preconditioner(cfg, None)
+            net.close()
     print("profile case done", flush=True)
 
 

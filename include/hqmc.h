@@ -63,10 +63,16 @@ enum {
     HQMC_SOLVER_CG64 = 0,    /* plain CG, every vector and reduction in FP64 */
     HQMC_SOLVER_MIXED = 1,   /* CG with M^dagger M in FP32 (complex float) and FP64 reliable
                                 residual updates every params.reliable_interval iterations */
-    HQMC_SOLVER_LEARNED = 2  /* the attached net (hqmc_set_preconditioner) corrects the initial
+    HQMC_SOLVER_LEARNED = 2, /* the attached net (hqmc_set_preconditioner) corrects the initial
                                 guess, x <- x + K(theta)(phi - O x), kept only if it lowers the
                                 FP64 residual; then the mixed solver, whose FP64 true residual
                                 judges convergence */
+    /* The same three with the tau-line preconditioner Otilde^{-1} of hqmc_apply_precond in the
+     * preconditioned CG of Methods Eq. (pCG): directions from z = Otilde^{-1} r, step lengths
+     * from <r, z>; convergence is still judged on ||r|| and the FP64 true residual. */
+    HQMC_SOLVER_PCG64 = 3,
+    HQMC_SOLVER_PMIXED = 4,
+    HQMC_SOLVER_PLEARNED = 5
 };
 
 /* Model and lattice (Results "Model"; Methods "Model and partition function"). */
@@ -170,6 +176,24 @@ HQMC_API int hqmc_apply_M(hqmc_config* cfg, const double* theta, const void* x, 
  * - s'_tau B_tau x_{tau+1} with s_0 = -1, s'_{Ntau-1} = -1, else +1. */
 HQMC_API int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void* y,
                      int precision, void* stream);
+
+/* Tau-line preconditioner (Methods, "CG method and preconditioner").  It is built
+ * once per config from O = M^dagger M at the pi-flux field (theta_y(x,y) = pi (x mod 2),
+ * theta_x = 0), where every site is equivalent.  The same-site part of O there is the
+ * tau-line matrix T = a - b (S + S^dagger), with a = 1 + sum_j |B_js|^2, b = B_ss and
+ * S the antiperiodic tau shift.  Its bulk Cholesky factor is
+ * L = sqrt(b/rho)(1 - rho S) with rho + 1/rho = a/b.  The Neumann series of L^{-1}
+ * keeps the entries sqrt(rho/b) rho^m >= 1e-3 (m <= W), so on every site's tau line
+ *     z = Otilde^{-1} r = (rho/b) F_W^dagger F_W r,   F_W = sum_{m=0}^{W} rho^m S^m,
+ * which is Hermitian positive definite.
+ *   r, z: device vectors (complex double for HQMC_FP64, complex float for HQMC_FP32),
+ *   16-byte aligned, not overlapping.  The call uses config workspace (the FP64 or
+ *   FP32 CG direction buffer) and is stream-ordered like every other call. */
+HQMC_API int hqmc_apply_precond(hqmc_config* cfg, const void* r, void* z, int precision, void* stream);
+
+/* The preconditioner's coefficients (host query): a, b, rho and W as above.  Any
+ * output may be NULL. */
+HQMC_API int hqmc_get_precond(const hqmc_config* cfg, double* a, double* b, double* rho, int* W);
 
 /* y = (M^dagger M) x in FP64 without a config and without allocating device
  * memory.  The paper has no counterpart: this entry point exists for callers
@@ -317,9 +341,10 @@ HQMC_API int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net);
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Timed kernel classes: the fused M^dagger M in FP64 (applies, CG directions,
- * residuals), the fused M^dagger M in FP32, the CG vector update, the force. */
+ * residuals), the fused M^dagger M in FP32, the CG vector update, the force,
+ * and the two passes of the tau-line preconditioner inside CG iterations. */
 enum { HQMC_TIMER_MDAGM = 0, HQMC_TIMER_CG_UPDATE = 1, HQMC_TIMER_FORCE = 2, HQMC_TIMER_MDAGM32 = 3,
-       HQMC_TIMER_COUNT = 4 };
+       HQMC_TIMER_PRECOND = 4, HQMC_TIMER_COUNT = 5 };
 
 /* Enables (1) or disables (0) CUDA-event timing of kernel launches and resets
  * the counters.  Events are recorded on the launching stream around every

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libhqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["mdagm.cu", "mdagm_block.cu", "mdagm_walk.cu", "vec.cu", "force.cu", "hqmc_api.cu", "hqmc_static.cu", "net.cu"]
+SOURCES = ["mdagm.cu", "mdagm_block.cu", "mdagm_walk.cu", "vec.cu", "force.cu", "hqmc_api.cu", "hqmc_static.cu", "net.cu", "precond.cu"]
 
 
 def nvcc() -> str:

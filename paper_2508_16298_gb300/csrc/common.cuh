@@ -245,6 +245,7 @@ struct CgState {
   int loop_cap;      // hard bound on loop bodies (termination guard of the device-side loop)
   int n_rel;         // mixed solver: reliable updates done
   double rr_rel[8];  // mixed solver: true <r,r> at the last eight reliable updates (ring)
+  double rr_rec;     // preconditioned CG: last recursive <r,r> (rr[] holds <r, Otilde^{-1} r> there)
 };
 
 // CG_REC_CONVERGED: the recursive residual met tol; the true residual still has

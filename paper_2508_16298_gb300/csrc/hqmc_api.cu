@@ -23,6 +23,8 @@ constexpr int kMaxL = 68;             // 3 complex-double slices must fit in 227
 constexpr int kBodyIters64 = 16;      // FP64 CG iterations per loop body
 constexpr int kDefaultReliable = 50;  // mixed solver residual-update period (iterations per body)
 constexpr int kMaxBreakdowns = 8;     // mixed solver: FP32 breakdown restarts before the FP64 fallback
+constexpr size_t kMaxLineSmem = 227 * 1024;  // tau-line preconditioner tile: opt-in shared memory per block
+constexpr double kLineTruncation = 1e-3;  // entries of the factor's inverse below this are dropped (Methods)
 constexpr size_t kMaxGraphs = 8;      // cached solve graphs per config
 
 struct TimerClass {
@@ -54,6 +56,13 @@ struct hqmc_config {
   SliceLaunch slb32{}; // register-blocked fused M^dagger M, FP32 (nby = 0: not available)
   SliceLaunch slw32{}; // tau-walking fused M^dagger M, FP32 (walk = 0: not available)
   int num_sms = 0;
+  // tau-line preconditioner: coefficients from the pi-flux field, launch shape, workspace
+  double pc_a = 0, pc_b = 0;
+  LineCoef lc{};
+  LineLaunch ll64{}, ll32{};
+  double2* z64 = nullptr;
+  float2* z32 = nullptr;
+  double* part_rz = nullptr;
   SliceLaunch fused64{}, fused32{};  // shapes used for APPLY / CG direction (nby > 0: register-blocked)
   float tuned_us64 = 0.f, tuned_us32 = 0.f;  // autotuner: time of one FP64 / FP32 apply (0: not tuned)
   SliceLaunch sl1{};   // apply_M and force (one CTA per slice, no cluster)
@@ -262,13 +271,31 @@ int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, 
   return HQMC_OK;
 }
 
+// Solver ids: CG64 / MIXED / LEARNED, and the same three with the tau-line
+// preconditioner (PCG64 / PMIXED / PLEARNED).
+bool solver_pc(int solver) { return solver >= HQMC_SOLVER_PCG64; }
+int solver_base(int solver) { return solver_pc(solver) ? solver - HQMC_SOLVER_PCG64 : solver; }
+bool solver_fp32(int solver) { return solver_base(solver) != HQMC_SOLVER_CG64; }
+
+// z = Otilde^{-1} r and the partials of <r, z>, gated on a running solve
+// (st = NULL: always).
+template <class R>
+int precondition(hqmc_config* cfg, const C2<R>* r, C2<R>* z, const CgState* st, cudaStream_t s) {
+  LK(1, launch_line_precond<R>(cfg->g, cfg->lc, sizeof(R) == 8 ? cfg->ll64 : cfg->ll32, r, z, cfg->part_rz, st, s));
+  return HQMC_OK;
+}
+
 template <class R>
 int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, const C2<R>* U, void* x,
-                 bool x_double, cudaStream_t s) {
+                 bool x_double, bool pc, C2<R>* z, cudaStream_t s) {
   MdagmArgs<R> a = mdagm_args<R, MODE_CGDIR>(cfg);
   a.U = U;
   a.y = q;
-  a.r = r;
+  a.r = pc ? z : r;  // preconditioned CG: the direction is built from z = Otilde^{-1} r
+  if (pc) {
+    a.part_rz = cfg->part_rz;
+    a.n_part_rz = sizeof(R) == 8 ? cfg->ll64.gx * cfg->ll64.gy : cfg->ll32.gx * cfg->ll32.gy;
+  }
   a.pbuf[0] = pbuf[0];
   a.pbuf[1] = pbuf[1];
   a.part_in = cfg->part_ew;
@@ -284,6 +311,11 @@ int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, con
   LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, fused_shape<R>(cfg).grid,
                          cfg->part_ew, cfg->st, s));
   RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
+  if (pc) {
+    RET(timer_begin(cfg, HQMC_TIMER_PRECOND, s, &slot));
+    RET(precondition<R>(cfg, r, z, cfg->st, s));
+    RET(timer_end(cfg, HQMC_TIMER_PRECOND, s, slot));
+  }
   return HQMC_OK;
 }
 
@@ -352,21 +384,25 @@ int theta_float(hqmc_config* cfg, const double* theta, cudaStream_t s) {
 // Mixed: reliable_interval FP32 iterations, then the FP64 reliable update
 // x += xh, r = phi - O x (whenever the solve is still active).
 int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, cudaStream_t s, int* nkernels) {
-  const bool mixed = solver == HQMC_SOLVER_MIXED;
+  const bool mixed = solver_fp32(solver);
+  const bool pc = solver_pc(solver);
   const int iters = mixed ? cfg->reliable : kBodyIters64;
   for (int c = 0; c < iters; ++c) {
     if (mixed)
-      RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, s));
+      RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, pc, cfg->z32, s));
     else
-      RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, s));
+      RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, pc, cfg->z64, s));
   }
   if (mixed) {
     LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, cfg->st, GATE_ACTIVE, s));
     RET(residual(cfg, phi, x, cfg->r32, true, FIN_RELIABLE, 0.0, 0, GATE_ACTIVE, s));
+    if (pc) RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));
   } else {
     RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, 0.0, 0, GATE_REC, s));
+    // after a restart z must follow the new r; otherwise this recomputes the same z
+    if (pc) RET(precondition<double>(cfg, cfg->r64, cfg->z64, cfg->st, s));
   }
-  *nkernels = 2 * iters + (mixed ? 3 : 2);
+  *nkernels = (pc ? 3 : 2) * iters + (mixed ? 3 : 2) + (pc ? 1 : 0);
   return HQMC_OK;
 }
 
@@ -459,7 +495,8 @@ int run_loop(hqmc_config* cfg, int solver, const double2* phi, double2* x, int* 
 int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
           hqmc_solve_info* info, cudaStream_t s) {
   int net_used = 0;
-  if (solver == HQMC_SOLVER_LEARNED) {
+  const bool pc = solver_pc(solver);
+  if (solver_base(solver) == HQMC_SOLVER_LEARNED) {
     // candidate x1 = x + K r0 with r0 = phi - O x; the CG workspace is free here
     RET(net_workspace(cfg));
     RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
@@ -474,12 +511,16 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
       net_used = 1;
     else
       CK(cudaMemcpyAsync(x, cfg->p64[0], sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));
-    solver = HQMC_SOLVER_MIXED;
+    solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
   }
-  const bool mixed = solver == HQMC_SOLVER_MIXED;
+  const bool mixed = solver_fp32(solver);
   hqmc_solve_info inf{};
   RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, GATE_ALWAYS, s));
   if (mixed) CK(cudaMemsetAsync(cfg->xh32, 0, sizeof(float2) * cfg->n, s));
+  if (pc) {
+    if (mixed) RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));
+    else RET(precondition<double>(cfg, cfg->r64, cfg->z64, cfg->st, s));
+  }
   int cur = solver, loops_seen = 0, status = HQMC_OK;
   for (;;) {
     RET(run_loop(cfg, cur, phi, x, &loops_seen, s));
@@ -490,7 +531,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
       break;
     }
     if (st.done == CG_CONVERGED) break;
-    if ((st.done == CG_BREAKDOWN || st.done == CG_STAGNATED) && cur == HQMC_SOLVER_MIXED) {
+    if ((st.done == CG_BREAKDOWN || st.done == CG_STAGNATED) && solver_fp32(cur)) {
       // <p, O32 p> <= 0 or a stalled residual: FP32 rounding cannot resolve the
       // lowest modes of this field.  Fold in the correction and restart from the
       // FP64 residual; after repeated breakdowns, or at once on stagnation,
@@ -498,17 +539,19 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
       inf.restarts++;
       LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
       if (st.done == CG_STAGNATED || inf.restarts > kMaxBreakdowns) {
-        cur = HQMC_SOLVER_CG64;
+        cur = pc ? HQMC_SOLVER_PCG64 : HQMC_SOLVER_CG64;
         inf.fp64_fallback = 1;
         RET(residual(cfg, phi, x, cfg->r64, false, FIN_RESTART, tol, maxit, GATE_ALWAYS, s));
+        if (pc) RET(precondition<double>(cfg, cfg->r64, cfg->z64, cfg->st, s));
       } else {
         RET(residual(cfg, phi, x, cfg->r32, true, FIN_RESTART, tol, maxit, GATE_ALWAYS, s));
+        if (pc) RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));
       }
       continue;
     }
     // MAXIT, NONFINITE, or a breakdown of the FP64 recurrence: report the true residual of x
     status = st.done == CG_MAXIT ? HQMC_ENOTCONV : st.done == CG_BREAKDOWN ? HQMC_EBREAKDOWN : HQMC_ENONFINITE;
-    if (cur == HQMC_SOLVER_MIXED) LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
+    if (solver_fp32(cur)) LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
     RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
     RET(read_state(cfg, s));
     break;
@@ -519,7 +562,8 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   inf.status = status;
   inf.iterations = st.k;
   inf.true_residual = st.bb > 0 ? std::sqrt(cfg->report_h[0] / st.bb) : 0.0;
-  inf.recursive_residual = st.bb > 0 ? std::sqrt(st.rr[st.k & 1] / st.bb) : 0.0;
+  const double rr_rec = (pc && st.k > st.seg_start) ? st.rr_rec : st.rr[st.k & 1];
+  inf.recursive_residual = st.bb > 0 ? std::sqrt(rr_rec / st.bb) : 0.0;
   if (status == HQMC_OK && !(inf.true_residual <= tol)) status = inf.status = HQMC_ENOTCONV;
   if (info) *info = inf;
   return status;
@@ -539,8 +583,8 @@ int merge_status(int a, int b) { return a != HQMC_OK ? a : b; }
 
 int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, double2* X, int nsteps, double dt,
              double tol, int maxit, int solver, hqmc_traj_info* ti, cudaStream_t s) {
-  const bool mixed = solver != HQMC_SOLVER_CG64;
-  const bool learned = solver == HQMC_SOLVER_LEARNED;
+  const bool mixed = solver_fp32(solver);
+  const bool learned = solver_base(solver) == HQMC_SOLVER_LEARNED;
   const long long nb = 2 * cfg->n;
   hqmc_solve_info si;
   int status = HQMC_OK;
@@ -569,10 +613,45 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
 }
 
 int check_solver(hqmc_config* cfg, int solver) {
-  if (solver != HQMC_SOLVER_CG64 && solver != HQMC_SOLVER_MIXED && solver != HQMC_SOLVER_LEARNED)
+  if (solver < HQMC_SOLVER_CG64 || solver > HQMC_SOLVER_PLEARNED)
     return fail(cfg, HQMC_EINVAL, "unknown solver %d", solver);
-  if (solver == HQMC_SOLVER_LEARNED && !cfg->net)
+  if (solver_base(solver) == HQMC_SOLVER_LEARNED && !cfg->net)
     return fail(cfg, HQMC_EINVAL, "the learned solver needs a net attached with hqmc_set_preconditioner");
+  return HQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients of the tau-line preconditioner (Methods, "CG method and
+// preconditioner"), once per config, from the pi-flux field: one column of B
+// gives b = B_ss and a = 1 + sum_j |B_js|^2 (every site is equivalent there);
+// rho + 1/rho = a/b is the bulk Cholesky ratio of a - b (S + S^dagger), and the
+// Neumann series of its factor keeps the powers whose entries sqrt(rho/b) rho^m
+// are >= 1e-3.  (M e)_1 = -B_0 e_0 for the unit vector e at slice 0, site 0.
+int line_coefficients(hqmc_config* cfg) {
+  const Geo& g = cfg->g;
+  LK(1, launch_pi_flux(g, cfg->th0, 0));
+  CK(cudaMemset(cfg->p64[0], 0, sizeof(double2) * cfg->n));
+  const double2 one = make_double2(1.0, 0.0);
+  CK(cudaMemcpy(cfg->p64[0], &one, sizeof(double2), cudaMemcpyHostToDevice));
+  LK(1, launch_links(g, cfg->th0, cfg->t1, cfg->t2, cfg->U64, nullptr, nullptr, 0));
+  LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, cfg->p64[0], cfg->q64, 0, 0));
+  std::vector<double2> col(g.V);
+  CK(cudaMemcpy(col.data(), cfg->q64 + g.V, sizeof(double2) * g.V, cudaMemcpyDeviceToHost));
+  double norm2 = 0.0;
+  for (const double2& c : col) norm2 += c.x * c.x + c.y * c.y;
+  const double b = -col[0].x, a = 1.0 + norm2;
+  if (!(b > 0.0) || !(a > 2.0 * b)) return fail(cfg, HQMC_EUNSUPPORTED, "tau-line coefficients a=%g b=%g", a, b);
+  const double q = a / b, rho = 0.5 * (q - std::sqrt(q * q - 4.0)), pref = std::sqrt(rho / b);
+  int W = 0;
+  while (pref * std::pow(rho, W + 1) >= kLineTruncation && W < 4096) ++W;
+  cfg->pc_a = a;
+  cfg->pc_b = b;
+  cfg->lc = LineCoef{rho, std::pow(rho, W + 1), rho / b, W};
+  if (line_smem_bytes(8, W) > kMaxLineSmem)
+    return fail(cfg, HQMC_EUNSUPPORTED, "tau-line preconditioner width W=%d too large", W);
+  CK(prepare_line_precond<double>(W));
+  CK(prepare_line_precond<float>(W));
+  CK(cudaDeviceSynchronize());
   return HQMC_OK;
 }
 
@@ -919,6 +998,12 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     if ((rc = dalloc(cfg, &cfg->part_resid, 2 * ((size_t)p->Ntau + 8)))) break;
     if ((rc = dalloc(cfg, &cfg->part_ew, (size_t)cfg->ew_grid))) break;
     if ((rc = dalloc(cfg, &cfg->part_act, 4 * (size_t)cfg->act_grid))) break;
+    cfg->ll64 = line_launch(cfg->g, 8);
+    cfg->ll32 = line_launch(cfg->g, 4);
+    if ((rc = dalloc(cfg, &cfg->z64, n))) break;
+    if ((rc = dalloc(cfg, &cfg->z32, n))) break;
+    if ((rc = dalloc(cfg, &cfg->part_rz,
+                     (size_t)std::max(cfg->ll64.gx * cfg->ll64.gy, cfg->ll32.gx * cfg->ll32.gy)))) break;
     if ((rc = dalloc(cfg, &cfg->terms, 8))) break;
     if ((rc = dalloc(cfg, &cfg->report, 2))) break;
     if ((rc = dalloc(cfg, &cfg->st, 1))) break;
@@ -939,6 +1024,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
       rc = fail(cfg, HQMC_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
       break;
     }
+    if ((rc = line_coefficients(cfg)) != HQMC_OK) break;
     if (p->autotune && (rc = autotune(cfg)) != HQMC_OK) break;
   } while (0);
   if (rc != HQMC_OK) {
@@ -1008,6 +1094,30 @@ int hqmc_apply_MdagM(hqmc_config* cfg, const double* theta, const void* x, void*
   return HQMC_OK;
 }
 
+int hqmc_apply_precond(hqmc_config* cfg, const void* r, void* z, int precision, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(r) || !aligned16(z)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (precision != HQMC_FP64 && precision != HQMC_FP32) return fail(cfg, HQMC_EINVAL, "bad precision");
+  const size_t vb = cfg->n * (precision == HQMC_FP64 ? sizeof(double2) : sizeof(float2));
+  if (overlap(r, vb, z, vb)) return fail(cfg, HQMC_EINVAL, "r and z overlap");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == HQMC_FP64)
+    RET(precondition<double>(cfg, (const double2*)r, (double2*)z, nullptr, s));
+  else
+    RET(precondition<float>(cfg, (const float2*)r, (float2*)z, nullptr, s));
+  return HQMC_OK;
+}
+
+int hqmc_get_precond(const hqmc_config* cfg, double* a, double* b, double* rho, int* W) {
+  if (!cfg) return HQMC_EINVAL;
+  if (a) *a = cfg->pc_a;
+  if (b) *b = cfg->pc_b;
+  if (rho) *rho = cfg->lc.rho;
+  if (W) *W = cfg->lc.W;
+  return HQMC_OK;
+}
+
 int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* x, double tol, int maxit, int solver,
                   hqmc_solve_info* info, void* stream) {
   if (!cfg) return HQMC_EINVAL;
@@ -1017,7 +1127,7 @@ int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* 
   RET(check_solver(cfg, solver));
   RET(check_device(cfg));
   cudaStream_t s = (cudaStream_t)stream;
-  RET(links(cfg, theta, true, solver != HQMC_SOLVER_CG64, s, false, solver == HQMC_SOLVER_LEARNED));
+  RET(links(cfg, theta, true, solver_fp32(solver), s, false, solver_base(solver) == HQMC_SOLVER_LEARNED));
   return solve(cfg, (const double2*)phi, (double2*)x, tol, maxit, solver, info, s);
 }
 

@@ -54,7 +54,82 @@ struct MdagmArgs {
   double t1, t2;           // tanh(a), tanh(a/2)
   int teff;                // generic kernel: threads that take part in the site loops (0: the whole block);
                            // a batch sets each chain's own block size so sums group sites as in its own launch
+  const double* part_rz;   // CGDIR, preconditioned CG: partials of <r, z> (z = Otilde^{-1} r; x/r read z)
+  int n_part_rz;
 };
+
+// First step of a CG-direction launch (one warp): read the CG state, decide
+// whether this iteration runs, and compute beta = <r,r>_k / <r,r>_{k-1} from
+// the update kernel's partials.  The writer block records the outcome in the state.
+// Preconditioned CG (a.part_rz set, Eq. (pCG)): <r,r> still decides
+// convergence, while rz = <r, Otilde^{-1} r> takes its place in beta and, kept in
+// st->rr, in the step length.
+// s_flags: bit 0 = skip the launch (uniform over the grid), bit 1 = first
+// iteration of a recurrence segment (p = r, or p = z).
+template <class R>
+__device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, int& s_flags, R& s_beta,
+                                           int& s_k) {
+  if (threadIdx.x < 32) {
+    CgState* st = a.st;
+    const int lane = threadIdx.x;
+    const int done = *(volatile int*)&st->done;
+    const int k = *(volatile int*)&st->k;
+    const int seg = st->seg_start;
+    int flags = 0;
+    double beta = 0.0;
+    int new_done = CG_RUNNING;
+    if (done != CG_RUNNING) {
+      flags = 1;
+    } else if (k >= st->maxit) {
+      flags = 1;
+      new_done = CG_MAXIT;
+    } else if (k == seg) {
+      flags = 2;
+      if (a.part_rz) {
+        const double rz = warp_sum_partials(a.part_rz, a.n_part_rz);
+        if (!isfinite(rz) || !(rz > 0.0)) {
+          flags = 1;
+          new_done = isfinite(rz) ? CG_BREAKDOWN : CG_NONFINITE;
+        } else if (writer && lane == 0) {
+          st->rr[k & 1] = rz;
+        }
+      }
+    } else {
+      const double rr = warp_sum_partials(a.part_in, a.n_part_in);
+      const double rz = a.part_rz ? warp_sum_partials(a.part_rz, a.n_part_rz) : rr;
+      if (!isfinite(rr) || !isfinite(rz)) {
+        flags = 1;
+        new_done = CG_NONFINITE;
+      } else if (rr <= st->tol2bb) {
+        flags = 1;
+        new_done = CG_REC_CONVERGED;
+      } else if (!(rz > 0.0)) {
+        flags = 1;
+        new_done = CG_BREAKDOWN;
+      } else {
+        beta = rz / st->rr[(k - 1) & 1];
+      }
+      if (writer && lane == 0) {
+        if (!a.part_rz) {
+          st->rr[k & 1] = rr;
+        } else {
+          st->rr_rec = rr;
+          if (!(flags & 1)) st->rr[k & 1] = rz;
+        }
+      }
+    }
+    if (writer && lane == 0) {
+      if (new_done != CG_RUNNING) st->done = new_done;
+      if (!(flags & 1)) st->k2 = k;
+    }
+    if (lane == 0) {
+      s_flags = flags;
+      s_beta = (R)beta;
+      s_k = k;
+    }
+  }
+  __syncthreads();
+}
 
 // Fused M^dagger M (three modes).
 template <class R, int MODE>
@@ -82,6 +157,28 @@ cudaError_t prepare_mdagm_walk(const SliceLaunch& sl);
 int walk_thread_cap(int nby);
 size_t walk_smem_bytes(const Geo& g, int mode);
 int mdagm_walk_blocks_per_sm(const SliceLaunch& sl);
+
+// Tau-line preconditioner (precond.cu): z = (rho/b) F_W^dagger F_W r per site.
+struct LineCoef {
+  double rho;    // bulk Cholesky ratio of the pi-flux tau-line matrix
+  double rhoW1;  // rho^(W+1)
+  double scale;  // rho / b
+  int W;         // powers of rho S kept in the truncated Neumann series
+};
+struct LineLaunch {
+  int chunk;  // slices per tile
+  int block;  // threads per block
+  int gx, gy; // grid: site tiles x slice tiles (gx * gy partials of <r, z>)
+};
+LineLaunch line_launch(const Geo& g, int real_bytes);
+size_t line_smem_bytes(int real_bytes, int W);
+template <class R>
+cudaError_t prepare_line_precond(int W);
+// z = Otilde^{-1} r and partials of <r, z>; gated on st->done == CG_RUNNING unless st is NULL.
+template <class R>
+cudaError_t launch_line_precond(const Geo& g, const LineCoef& lc, const LineLaunch& ll, const C2<R>* r, C2<R>* z,
+                                double* part_rz, const CgState* st, cudaStream_t s);
+cudaError_t launch_pi_flux(const Geo& g, double* theta, cudaStream_t s);
 
 // Fused M^dagger M over many chains in one launch (generic kernel, links from
 // memory): CTA b runs cluster tile b / C = (chain, first slice) of `tiles`.

@@ -61,48 +61,7 @@ __device__ __forceinline__ void mdagm_body(const MdagmArgs<R>& a, const int tau,
   const bool active = tau < N;
 
   if (MODE == MODE_CGDIR) {
-    // Direction step of CG: beta = <r_k, r_k> / <r_{k-1}, r_{k-1}> from the
-    // update kernel's partials; every CTA reaches the same decision.
-    if (threadIdx.x < 32) {
-      CgState* st = a.st;
-      const int lane = threadIdx.x;
-      const int done = *(volatile int*)&st->done;
-      const int k = *(volatile int*)&st->k;
-      const int seg = st->seg_start;
-      int flags = 0;
-      double beta = 0.0;
-      int new_done = CG_RUNNING;
-      if (done != CG_RUNNING) {
-        flags = 1;
-      } else if (k >= st->maxit) {
-        flags = 1;
-        new_done = CG_MAXIT;
-      } else if (k == seg) {
-        flags = 2;
-      } else {
-        const double rr = warp_sum_partials(a.part_in, a.n_part_in);
-        if (!isfinite(rr)) {
-          flags = 1;
-          new_done = CG_NONFINITE;
-        } else if (rr <= st->tol2bb) {
-          flags = 1;
-          new_done = CG_REC_CONVERGED;
-        } else {
-          beta = rr / st->rr[(k - 1) & 1];
-        }
-        if (slot == 0 && lane == 0) st->rr[k & 1] = rr;
-      }
-      if (slot == 0 && lane == 0) {
-        if (new_done != CG_RUNNING) st->done = new_done;
-        if (!(flags & 1)) st->k2 = k;
-      }
-      if (lane == 0) {
-        s_flags = flags;
-        s_beta = (R)beta;
-        s_k = k;
-      }
-    }
-    __syncthreads();
+    cgdir_head<R>(a, slot == 0, s_flags, s_beta, s_k);  // every CTA reaches the same decision
     if (s_flags & 1) return;  // uniform over the whole grid: no cluster barrier is pending
   }
   if (MODE == MODE_RESID && a.gate != GATE_ALWAYS) {

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__((BlockThreads<R, NBY>::max), 1) mdagm_block_ke
   const bool active = tau < N;
 
   if (MODE == MODE_CGDIR) {
-    cgdir_head<R>(a, s_flags, s_beta, s_k);
+    cgdir_head<R>(a, blockIdx.x == 0, s_flags, s_beta, s_k);
     if (s_flags & 1) return;  // uniform over the whole grid: no cluster barrier is pending
   }
   const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
   __shared__ int s_k;
 
   if (MODE == MODE_CGDIR) {
-    cgdir_head<float>(a, s_flags, s_beta, s_k);
+    cgdir_head<float>(a, blockIdx.x == 0, s_flags, s_beta, s_k);
     if (s_flags & 1) return;  // uniform over the grid
   }
   const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);

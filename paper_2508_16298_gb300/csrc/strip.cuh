@@ -176,7 +176,6 @@ template <class T, int NBY>
 __device__ __forceinline__ void strip_sweep(T (&v)[2 * NBY][2], const StripLinks<T, NBY>& k, const StripGeo& s,
                                             T* __restrict__ E0, T* __restrict__ E1, int& eb) {
   constexpr int H = 2 * NBY;
-  const int L = s.L;
   // F4 in D
 #pragma unroll
   for (int b = 0; b < NBY; ++b) {
@@ -253,55 +252,6 @@ __device__ __forceinline__ void strip_sweep(T (&v)[2 * NBY][2], const StripLinks
     bond2(v[2 * b][0], v[2 * b + 1][0], k.u4[b][0]);
     bond2(v[2 * b][1], v[2 * b + 1][1], k.u4[b][1]);
   }
-}
-
-// First step of a CG-direction launch (one warp): read the CG state, decide
-// whether this iteration runs, and compute beta = <r,r>_k / <r,r>_{k-1} from
-// the update kernel's partials.  Block 0 records the outcome in the state.
-// s_flags: bit 0 = skip the launch (uniform over the grid), bit 1 = first
-// iteration of a recurrence segment (p = r).
-template <class R>
-__device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, int& s_flags, R& s_beta, int& s_k) {
-  if (threadIdx.x < 32) {
-    CgState* st = a.st;
-    const int lane = threadIdx.x;
-    const int done = *(volatile int*)&st->done;
-    const int k = *(volatile int*)&st->k;
-    const int seg = st->seg_start;
-    int flags = 0;
-    double beta = 0.0;
-    int new_done = CG_RUNNING;
-    if (done != CG_RUNNING) {
-      flags = 1;
-    } else if (k >= st->maxit) {
-      flags = 1;
-      new_done = CG_MAXIT;
-    } else if (k == seg) {
-      flags = 2;
-    } else {
-      const double rr = warp_sum_partials(a.part_in, a.n_part_in);
-      if (!isfinite(rr)) {
-        flags = 1;
-        new_done = CG_NONFINITE;
-      } else if (rr <= st->tol2bb) {
-        flags = 1;
-        new_done = CG_REC_CONVERGED;
-      } else {
-        beta = rr / st->rr[(k - 1) & 1];
-      }
-      if (blockIdx.x == 0 && lane == 0) st->rr[k & 1] = rr;
-    }
-    if (blockIdx.x == 0 && lane == 0) {
-      if (new_done != CG_RUNNING) st->done = new_done;
-      if (!(flags & 1)) st->k2 = k;
-    }
-    if (lane == 0) {
-      s_flags = flags;
-      s_beta = (R)beta;
-      s_k = k;
-    }
-  }
-  __syncthreads();
 }
 
 }  // namespace hqmc

@@ -27,13 +27,16 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
 FP64, FP32 = 0, 1
 ACTION_COMPACT, ACTION_NONCOMPACT = 0, 1
-SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED = 0, 1, 2
-TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE, TIMER_MDAGM32 = 0, 1, 2, 3
+SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED, SOLVER_PCG64, SOLVER_PMIXED, SOLVER_PLEARNED = range(6)
+SOLVERS = {"cg64": SOLVER_CG64, "mixed": SOLVER_MIXED, "learned": SOLVER_LEARNED, "pcg64": SOLVER_PCG64,
+           "pmixed": SOLVER_PMIXED, "plearned": SOLVER_PLEARNED}
+TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE, TIMER_MDAGM32, TIMER_PRECOND = 0, 1, 2, 3, 4
 
 # Every function declared in include/hqmc.h.
 EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_error", "hqmc_num_sites",
            "hqmc_launch_count", "hqmc_get_launch_shape",
-           "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_cg_solve", "hqmc_force", "hqmc_action_terms",
+           "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_apply_precond", "hqmc_get_precond", "hqmc_cg_solve",
+           "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
            "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory",
@@ -79,6 +82,9 @@ _sig = {
                                ctypes.POINTER(ctypes.c_float)], _i),
     "hqmc_apply_M": ([_vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "hqmc_apply_MdagM": ([_vp, _vp, _vp, _vp, _i, _vp], _i),
+    "hqmc_apply_precond": ([_vp, _vp, _vp, _i, _vp], _i),
+    "hqmc_get_precond": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     "hqmc_cg_solve": ([_vp, _vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_force": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hqmc_action_terms": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
@@ -239,9 +245,25 @@ def apply_MdagM(cfg: Config, theta, x, y=None):
     return y
 
 
+def apply_precond(cfg: Config, r, z=None):
+    """z = Otilde^{-1} r, the tau-line preconditioner; complex64 r selects FP32."""
+    cfg._vec(r, "r", (torch.complex128, torch.complex64))
+    z = torch.empty_like(r) if z is None else cfg._vec(z, "z", (r.dtype,))
+    cfg.check(_lib.hqmc_apply_precond(cfg.handle, _ptr(r), _ptr(z), _prec(r), _stream()))
+    return z
+
+
+def get_precond(cfg: Config) -> dict:
+    """Coefficients of the tau-line preconditioner: a, b (pi-flux O), rho, W."""
+    a, b, rho, W = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), _i()
+    cfg.check(_lib.hqmc_get_precond(cfg.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(rho),
+                                    ctypes.byref(W)))
+    return {"a": a.value, "b": b.value, "rho": rho.value, "W": W.value}
+
+
 def _solver(s) -> int:
     if isinstance(s, str):
-        return {"cg64": SOLVER_CG64, "mixed": SOLVER_MIXED, "learned": SOLVER_LEARNED}[s]
+        return SOLVERS[s]
     return int(s)
 
 
