@@ -16,6 +16,8 @@ reproduced on the host:
   stream 0: momenta, element = site i   -> p[2i], p[2i+1]  (N(0, 1/2) each)
   stream 1: pseudofermion, element = i  -> R[i] = (g0 + i g1)/sqrt(2)  (CN(0, 1))
   stream 2: Metropolis, element 0       -> u (uniform in [0, 1))
+  stream 3: stochastic-estimation vectors, element = i, traj_counter = counter + k
+            -> xi_k[i] = (g0 + i g1)/sqrt(2)  (CN(0, 1))
 
 Two uniforms per call: u_a from words (0, 1) and u_b from words (2, 3), each
 ((w_hi >> 5) * 2^26 + (w_lo >> 6)) * 2^-53.  Gaussians by Box-Muller:
@@ -92,3 +94,10 @@ def draw_pseudofermion(seed: int, traj_counter: int, L: int, Ntau: int) -> np.nd
 def draw_metropolis(seed: int, traj_counter: int) -> float:
     w = _words(seed, 2, traj_counter, 1)
     return float(_u53(w[0], w[1])[0])
+
+
+def draw_random_vector(seed: int, counter: int, k: int, L: int, Ntau: int) -> np.ndarray:
+    """xi_k ~ CN(0, 1) on every site for stochastic estimation, shape (Ntau, L, L)."""
+    n = L * L * Ntau
+    g0, g1 = _gauss_pairs(seed, 3, counter + k, n)
+    return ((g0 + 1j * g1) * np.sqrt(0.5)).reshape(Ntau, L, L)
