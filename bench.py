@@ -68,6 +68,9 @@ WORKLOADS["hmc_learned_fp32_L66_Nt660"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, 
                                                dt=round(0.0005 * (138240 / 2874960) ** 0.5, 7), tol=1e-8,
                                                solver="plearned", seed=1, start="cold", compare="cg64",
                                                triples=16, epochs=12, lr=1e-3)
+# stochastic estimation (Methods): 40 CN(0,1) vectors on one field, M^{-1} xi by preconditioned mixed CG
+WORKLOADS["estimate_L66_Nt660_40rv"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, J=1.0, nsteps=0, dt=0.0, tol=1e-8,
+                                            solver="pmixed", seed=1, start="cold", estimate=True, nrv=40)
 DEFAULT_WORKLOAD = "hmc_learned_fp32_L66_Nt660"
 
 # Algorithmic work of one launch of the fused M^dagger M kernel in CG mode, per site:
@@ -175,9 +178,10 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
 # CG iterations per trajectory used to scale oracle samples when no GPU run is
 # available (the reference arm); measured on the GPU with the same algorithm.
 ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 11000.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 16500.0,
-                     "batched_32chains_L12-24": 11000.0, "hmc_learned_fp32_L66_Nt660": 2640.0}
+                     "batched_32chains_L12-24": 11000.0, "hmc_learned_fp32_L66_Nt660": 2640.0,
+                     "estimate_L66_Nt660_40rv": 250.0}
 # oracle CG iterations per bounded sample (the largest lattices take about a second per iteration on the host)
-ORACLE_SAMPLE_ITERS = {"hmc_learned_fp32_L66_Nt660": 4, "hmc_mixed_L48_Nt480": 6}
+ORACLE_SAMPLE_ITERS = {"hmc_learned_fp32_L66_Nt660": 4, "hmc_mixed_L48_Nt480": 6, "estimate_L66_Nt660_40rv": 4}
 
 
 def run_reference(args, wl_name, wl, rank, world):
@@ -193,18 +197,22 @@ def run_reference(args, wl_name, wl, rank, world):
     phi = oracle.apply_M(lat, theta, R, dagger=True)
     its = ITS_PER_TRAJ_HINT[wl_name]
     n_it = ORACLE_SAMPLE_ITERS.get(wl_name, 10)
+    unit = "traj/s"
+    if wl.get("estimate"):  # a unit of work is one random vector: its solve, no force
+        wl = dict(wl, nsteps=-1)
+        unit = "random vectors/s"
     for _ in range(args.warmup):
         oracle_sample(wl, its, theta, phi, max_iters=1)
     samples = [oracle_sample(wl, its, theta, phi, max_iters=n_it) for _ in range(args.steps)]
     t = statistics.median(s["traj_s"] for s in samples)
     value = 1.0 / t
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl_name, wl),
-            "cpu_baseline": {"value": value, "unit": "traj/s", "cores": samples[0]["cores"], "kind": "oracle",
+            "config": config_of(wl_name, WORKLOADS[wl_name]),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": samples[0]["cores"], "kind": "oracle",
                              "sample": samples[0]["sample"]},
-            "e2e": {"value": value, "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -559,6 +567,75 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_estimate(args, wl_name, wl, rank, world, local_rank):
+    """A step is one stochastic estimate: nrv vector draws, R = M^dagger xi, nrv solves of
+    (M^dagger M) X = R and the mean-diagonal estimate (hqmc_estimate)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_16298_gb300 import hqmc, inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    L, N, nrv = wl["L"], wl["Ntau"], wl["nrv"]
+    cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True)
+    seed = wl["seed"] + 1000 * rank
+    theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for k in range(args.warmup):
+        hqmc.estimate(cfg, theta, nrv, seed=seed, counter=nrv * k, tol=wl["tol"], solver=wl["solver"])
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    gid = str(local_rank)
+    clocks = ClockSampler(gid)
+    clocks.start()
+    l0 = cfg.launch_count()
+    ms, gs, its = [], [], []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g, infos, _, _ = hqmc.estimate(cfg, theta, nrv, seed=seed, counter=nrv * (args.warmup + k), tol=wl["tol"],
+                                       solver=wl["solver"])
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        gs.append(g)
+        its.append(sum(i["iterations"] for i in infos))
+    launches = cfg.launch_count() - l0
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * nrv / (total_ms / 1e3)
+    if rank != 0:
+        return
+    cb = oracle_sample(dict(wl, nsteps=-1), statistics.mean(its) / nrv, start_theta(wl, wl["seed"]),
+                       inputs.complex_gaussian(L, N, 3), max_iters=ORACLE_SAMPLE_ITERS.get(wl_name, 4))
+    cb["sample"] = cb["sample"].replace("and 0 forces per trajectory", "per random vector")
+    line = {"metric": METRIC, "value": value, "unit": "random vectors/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": wl_name, "L": L, "Ntau": N, "sites": L * L * N, "nrv": nrv, "cg_tol": wl["tol"],
+                       "solver": SOLVER_TEXT[wl["solver"]], "start": "cold (see hmc workloads)",
+                       "l2": "flushed between timed steps"},
+            "gpu_launches": int(launches),
+            "cpu_baseline": {"value": 1.0 / cb["traj_s"], "unit": "random vectors/s", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "clocks": clk,
+            "estimate_g": [[round(g.real, 6), round(g.imag, 6)] for g in gs],
+            "exact_re_g": 0.5,
+            "iterations_per_vector": statistics.mean(its) / nrv,
+            "step_ms": [round(m, 3) for m in ms]}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(wl):
     """A short, fixed sequence for ncu captures at the workload's size, with the CG
     loop driven from the host (kernels inside a graph with conditional nodes cannot
@@ -620,6 +697,8 @@ def main():
         run_reference(args, args.workload, wl, rank, world)
     elif wl.get("batched"):
         run_batched(args, args.workload, wl, rank, world, local_rank)
+    elif wl.get("estimate"):
+        run_estimate(args, args.workload, wl, rank, world, local_rank)
     else:
         run_ours(args, args.workload, wl, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

@@ -230,6 +230,24 @@ HQMC_API int hqmc_apply_MdagM_static(const hqmc_params* p, const double* theta, 
 HQMC_API int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* x,
                   double tol, int maxit, int solver, hqmc_solve_info* info, void* stream);
 
+/* Stochastic estimation of fermionic observables (Methods, "Stochastic estimation
+ * of fermionic observables").  For k = 0..nrv-1 a random vector xi_k ~ CN(0, 1) is
+ * drawn per site from Philox4x32-10 (key = seed, counter = (site, 3, counter + k)),
+ * R_k = M^dagger xi_k is formed, and X_k = (M^dagger M)^{-1} R_k = M^{-1} xi_k is
+ * solved with `solver` to `tol` (each solve starting from the previous X).
+ * (M^{-1} xi)_i conj(xi_j) is an unbiased estimate of (M^{-1})_ij.
+ * Outputs (each nullable):
+ *   Gxi:    device, nrv x N complex double, the X_k;
+ *   xi:     device, nrv x N complex double, the draws;
+ *   g_host: host double[2], the estimate of the mean diagonal of M^{-1},
+ *           (1 / (nrv N)) sum_k <xi_k, X_k> (re, im); its real part has expectation
+ *           exactly 1/2 at half filling on this bipartite lattice;
+ *   infos:  host, nrv solve infos.
+ * Returns HQMC_ENOTCONV if any solve missed tol.  Synchronises the stream. */
+HQMC_API int hqmc_estimate(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv,
+                           double tol, int maxit, int solver, void* Gxi, void* xi, double* g_host,
+                           hqmc_solve_info* infos, void* stream);
+
 /* ---- force (Supplement SI, Eqs. (force&CG) and (fermion_force)) -------- */
 
 /* Given X = (M^dagger M)^{-1} phi (complex double), writes the total force

@@ -1131,6 +1131,51 @@ int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* 
   return solve(cfg, (const double2*)phi, (double2*)x, tol, maxit, solver, info, s);
 }
 
+int hqmc_estimate(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
+                  int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || (Gxi && !aligned16(Gxi)) || (xi && !aligned16(xi)))
+    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (nrv < 1) return fail(cfg, HQMC_EINVAL, "nrv must be >= 1");
+  if (!(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "tol must be > 0 and maxit >= 0");
+  const size_t vb = (size_t)cfg->n * sizeof(double2);
+  if (Gxi && xi && overlap(Gxi, vb * nrv, xi, vb * nrv)) return fail(cfg, HQMC_EINVAL, "Gxi and xi overlap");
+  RET(check_solver(cfg, solver));
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  RET(links(cfg, theta, true, solver_fp32(solver), s, false, solver_base(solver) == HQMC_SOLVER_LEARNED));
+  double sum_re = 0.0, sum_im = 0.0;
+  int status = HQMC_OK;
+  double2* prev = nullptr;
+  for (int k = 0; k < nrv; ++k) {
+    double2* v = xi ? (double2*)xi + (size_t)k * cfg->n : cfg->Rw;           // xi_k
+    double2* X = Gxi ? (double2*)Gxi + (size_t)k * cfg->n : cfg->Xw;          // M^{-1} xi_k
+    LK(1, launch_draw_vector(cfg->n, seed, 3u, counter + (uint64_t)k, v, s));
+    LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, v, cfg->eta, 1, s));  // R = M^dagger xi
+    if (k == 0)
+      CK(cudaMemsetAsync(X, 0, vb, s));
+    else if (prev != X)
+      CK(cudaMemcpyAsync(X, prev, vb, cudaMemcpyDeviceToDevice, s));           // start from the previous solution
+    hqmc_solve_info si{};
+    const int rc = solve(cfg, cfg->eta, X, tol, maxit, solver, &si, s);
+    if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
+    status = merge_status(status, rc);
+    if (infos) infos[k] = si;
+    LK(2, launch_cdot(cfg->n, v, X, cfg->act_grid, cfg->part_act, cfg->terms + 4, s));
+    CK(cudaMemcpyAsync(cfg->terms_h + 4, cfg->terms + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    sum_re += cfg->terms_h[4];
+    sum_im += cfg->terms_h[5];
+    prev = X;
+  }
+  if (g_host) {
+    const double norm = 1.0 / ((double)nrv * (double)cfg->n);
+    g_host[0] = sum_re * norm;
+    g_host[1] = sum_im * norm;
+  }
+  return status;
+}
+
 int hqmc_force(hqmc_config* cfg, const double* theta, const void* X, double* F, double* dSf, void* stream) {
   if (!cfg) return HQMC_EINVAL;
   if (!aligned16(theta) || !aligned16(X) || !aligned16(F) || (dSf && !aligned16(dSf)))

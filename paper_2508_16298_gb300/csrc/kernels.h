@@ -282,6 +282,12 @@ cudaError_t launch_action_terms(const Geo& g, const BosonParams& bp, const doubl
 cudaError_t launch_draw(long long n_sites, uint64_t seed, uint64_t counter, double* p, double2* R,
                         cudaStream_t s);
 void philox_uniform_host(uint64_t seed, uint64_t counter, double* u);
+// v ~ CN(0, 1) per site from Philox stream `stream` (3: stochastic-estimation vectors).
+cudaError_t launch_draw_vector(long long n_sites, uint64_t seed, uint32_t stream, uint64_t counter, double2* v,
+                               cudaStream_t s);
+// out[0] + i out[1] = <a, b> = sum conj(a_i) b_i; part holds 2 * grid doubles.
+cudaError_t launch_cdot(long long n, const double2* a, const double2* b, int grid, double* part, double* out,
+                        cudaStream_t s);
 // FP64 FMA throughput probe (16 flops per thread per iteration).
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
 

@@ -540,6 +540,60 @@ cudaError_t launch_draw(long long n_sites, uint64_t seed, uint64_t counter, doub
   return cudaGetLastError();
 }
 
+// v ~ CN(0, 1) per site from Philox stream `stream` at traj_counter `counter`.
+__global__ void draw_vector_kernel(long long n, uint64_t seed, uint32_t stream, uint64_t counter,
+                                   double2* __restrict__ v) {
+  const double h = 0.70710678118654752440;  // sqrt(1/2)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double g0, g1;
+    gauss_pair(seed, stream, counter, (uint32_t)i, &g0, &g1);
+    v[i] = make_double2(g0 * h, g1 * h);
+  }
+}
+
+cudaError_t launch_draw_vector(long long n_sites, uint64_t seed, uint32_t stream, uint64_t counter, double2* v,
+                               cudaStream_t s) {
+  draw_vector_kernel<<<ew_blocks(n_sites, 256, 4096), 256, 0, s>>>(n_sites, seed, stream, counter, v);
+  return cudaGetLastError();
+}
+
+// <a, b> = sum conj(a_i) b_i (complex), as per-block partials in a fixed order
+// and one warp that sums them: out[0] = Re, out[1] = Im.
+__global__ void cdot_partials_kernel(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
+                                     double* __restrict__ part) {
+  __shared__ double red[32];
+  double re = 0.0, im = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    re += x.x * y.x + x.y * y.y;
+    im += x.x * y.y - x.y * y.x;
+  }
+  double t = block_sum(re, red);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = t;
+  t = block_sum(im, red);
+  if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = t;
+}
+
+__global__ void cdot_finalize_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  for (int c = 0; c < 2; ++c) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += 32) acc += part[2 * k + c];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) out[c] = acc;
+  }
+}
+
+cudaError_t launch_cdot(long long n, const double2* a, const double2* b, int grid, double* part, double* out,
+                        cudaStream_t s) {
+  cdot_partials_kernel<<<grid, 256, 0, s>>>(n, a, b, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cdot_finalize_kernel<<<1, 32, 0, s>>>(part, grid, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // FP64 throughput probe: every thread runs 8 independent FMA chains, so the
 // FP64 pipe, not latency, limits the rate.  Used only to measure the FP64

@@ -36,6 +36,7 @@ TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE, TIMER_MDAGM32, TIMER_PRECOND = 0, 1, 
 EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_error", "hqmc_num_sites",
            "hqmc_launch_count", "hqmc_get_launch_shape",
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_apply_precond", "hqmc_get_precond", "hqmc_cg_solve",
+           "hqmc_estimate",
            "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
@@ -86,6 +87,8 @@ _sig = {
     "hqmc_get_precond": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     "hqmc_cg_solve": ([_vp, _vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
+    "hqmc_estimate": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _i, _d, _i, _i, _vp, _vp,
+                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_force": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hqmc_action_terms": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_draw": ([_vp, _u64, _u64, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
@@ -279,6 +282,26 @@ def cg_solve(cfg: Config, theta, phi, x=None, tol: float = 1e-8, maxit: int = 10
     if raise_on_fail:
         cfg.check(rc)
     return x, info.as_dict()
+
+
+def estimate(cfg: Config, theta, nrv: int, seed: int = 0, counter: int = 0, tol: float = 1e-8,
+             maxit: int = 100000, solver="cg64", want_vectors: bool = False, raise_on_fail: bool = True):
+    """Stochastic estimation with nrv CN(0, 1) vectors (hqmc_estimate).  Returns
+    (g, infos, Gxi, xi): g the complex estimate of the mean diagonal of M^{-1}, the
+    per-vector solve infos, and (if want_vectors) M^{-1} xi_k and xi_k as tensors of
+    shape (nrv, Ntau, L, L)."""
+    cfg._bonds(theta, "theta")
+    Gxi = xi = None
+    if want_vectors:
+        Gxi = torch.empty((nrv, cfg.Ntau, cfg.L, cfg.L), dtype=torch.complex128, device=theta.device)
+        xi = torch.empty_like(Gxi)
+    g = (ctypes.c_double * 2)()
+    infos = (SolveInfo * nrv)()
+    rc = _lib.hqmc_estimate(cfg.handle, _ptr(theta), seed, counter, nrv, tol, maxit, _solver(solver), _ptr(Gxi),
+                            _ptr(xi), g, infos, _stream())
+    if raise_on_fail:
+        cfg.check(rc, allow=(OK, ENOTCONV))
+    return complex(g[0], g[1]), [i.as_dict() for i in infos], Gxi, xi
 
 
 def force(cfg: Config, theta, X, F=None, dSf=None):

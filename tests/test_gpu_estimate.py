@@ -1,0 +1,66 @@
+"""Stochastic estimation (hqmc_estimate, through the C ABI) against the FP64
+oracle of oracle/estimate.py and the exact half-filling value Re (M^{-1})_ii = 1/2."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import estimate as oest
+from oracle import philox
+from paper_2508_16298_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hq():
+    from paper_2508_16298_gb300 import build
+    build.build()
+    from paper_2508_16298_gb300 import hqmc
+    return hqmc
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("L,N,solver,tol", [(4, 6, "cg64", 1e-12), (8, 40, "pcg64", 1e-12), (8, 40, "pmixed", 1e-9)])
+def test_estimate_matches_oracle(hq, L, N, solver, tol):
+    lat = oracle.Lattice(L, N)
+    th = inputs.theta_hot(L, N, 21)
+    g_o, X_o, xi_o = oest.estimate(lat, th, seed=5, counter=100, nrv=3, tol=1e-13)
+    with hq.Config(L, N) as cfg:
+        g, infos, Gxi, xi = hq.estimate(cfg, cuda(th), 3, seed=5, counter=100, tol=tol, solver=solver,
+                                        want_vectors=True)
+    assert all(i["status"] == 0 and i["true_residual"] <= tol for i in infos)
+    for k in range(3):
+        assert np.max(np.abs(xi[k].cpu().numpy() - philox.draw_random_vector(5, 100, k, L, N))) < 1e-13
+    # ||X - X_o|| <= kappa * tol; kappa < 1e4 on these lattices
+    scale = np.max(np.abs(X_o))
+    assert np.max(np.abs(Gxi.cpu().numpy() - X_o)) < max(1e-7, 1e4 * tol) * scale
+    assert abs(g - g_o) < max(1e-9, 1e4 * tol)
+
+
+def test_estimate_is_centred_on_one_half(hq):
+    """40 vectors on a tau-smooth L = 24 field: Re g within 5 standard errors of the
+    exact 1/2 (standard error from the per-vector estimates)."""
+    L, N, nrv = 24, 240, 40
+    th = inputs.theta_ordered(L, N, 31, tau_walk=0.0)
+    with hq.Config(L, N) as cfg:
+        g, infos, Gxi, xi = hq.estimate(cfg, cuda(th), nrv, seed=7, tol=1e-8, solver="pmixed", want_vectors=True)
+        per = (xi.conj() * Gxi).sum(dim=(1, 2, 3)).cpu().numpy() / (L * L * N)
+    assert all(i["status"] == 0 for i in infos)
+    assert abs(per.mean() - g) < 1e-12
+    sem = per.real.std(ddof=1) / np.sqrt(nrv)
+    assert abs(g.real - 0.5) < 5 * sem and sem < 0.01
+
+
+def test_estimate_edge_cases(hq):
+    L, N = 4, 6
+    th = cuda(inputs.theta_hot(L, N, 41))
+    with hq.Config(L, N) as cfg:
+        with pytest.raises(hq.HQMCError) as e:
+            hq.estimate(cfg, th, 0)
+        assert e.value.status == hq.EINVAL
+        g, infos, _, _ = hq.estimate(cfg, th, 2, tol=1e-14, maxit=2, raise_on_fail=False)
+        assert all(i["status"] == hq.ENOTCONV for i in infos)
