@@ -496,8 +496,12 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
           hqmc_solve_info* info, cudaStream_t s) {
   int net_used = 0;
   const bool pc = solver_pc(solver);
+  bool started = false;  // the FP64 residual that starts the recurrence is already in place
   if (solver_base(solver) == HQMC_SOLVER_LEARNED) {
-    // candidate x1 = x + K r0 with r0 = phi - O x; the CG workspace is free here
+    // candidate x1 = x + K r0 with r0 = phi - O x; the CG workspace is free here.
+    // The FP64 residual of x1 is computed as the start of the mixed recurrence, so a
+    // kept candidate costs no extra residual; a rejected one restores x and starts again.
+    solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
     RET(net_workspace(cfg));
     RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
     RET(read_state(cfg, s));
@@ -505,17 +509,19 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
     RET(net_forward(cfg, cfg->net, cfg->vscratch, cfg->p64[1], s));                       // z = K r0
     CK(cudaMemcpyAsync(cfg->p64[0], x, sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));  // keep x
     LK(1, launch_kick(2 * cfg->n, (double*)x, (const double*)cfg->p64[1], 1.0, s));          // x += z
-    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
+    RET(residual(cfg, phi, x, cfg->r32, true, FIN_START, tol, maxit, GATE_ALWAYS, s));
     RET(read_state(cfg, s));
-    if (cfg->report_h[0] < rr0)
+    if (cfg->report_h[0] < rr0) {
       net_used = 1;
-    else
+      started = true;
+    } else {
       CK(cudaMemcpyAsync(x, cfg->p64[0], sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));
-    solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
+    }
   }
   const bool mixed = solver_fp32(solver);
   hqmc_solve_info inf{};
-  RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, GATE_ALWAYS, s));
+  if (!started)
+    RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, GATE_ALWAYS, s));
   if (mixed) CK(cudaMemsetAsync(cfg->xh32, 0, sizeof(float2) * cfg->n, s));
   if (pc) {
     if (mixed) RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));

@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
     parity ^= 1;
     if (ok) {
       load_strip_links_smem<NBY>(sg, Sth, t1, t2, lk);
-      const size_t bn = (size_t)wrap(j + 1) * V;
 #pragma unroll
       for (int r = 0; r < H; ++r) {
         const int y = drow(sg, r, H);
@@ -188,7 +187,21 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
           T xv = Sv0[s];
           if (MODE == MODE_CGDIR && !first) xv = caxpy(xv, beta, Sv1[s]);
           X1[(2 * r + c) * blockDim.x + threadIdx.x] = xv;
-          if (MODE == MODE_CGDIR && j + 1 < te) p_new[bn + s] = xv;
+        }
+      }
+      if (MODE == MODE_CGDIR && j + 1 < te) {
+        // p of the slice this block owns, written from the stage in slice order:
+        // contiguous 16-byte stores (the same arithmetic as the strip copies above)
+        float4* pn = reinterpret_cast<float4*>(p_new + (size_t)wrap(j + 1) * V);
+        const float4* r4 = reinterpret_cast<const float4*>(Sv0);
+        const float4* o4 = reinterpret_cast<const float4*>(Sv1);
+        for (int e = threadIdx.x; e < (V >> 1); e += blockDim.x) {
+          float4 v = r4[e];
+          if (!first) {
+            const float4 o = o4[e];
+            v = make_float4(fmaf(beta, o.x, v.x), fmaf(beta, o.y, v.y), fmaf(beta, o.z, v.z), fmaf(beta, o.w, v.w));
+          }
+          pn[e] = v;
         }
       }
     }

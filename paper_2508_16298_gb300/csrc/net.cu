@@ -74,42 +74,108 @@ __device__ __forceinline__ void net_neighbour(const Geo& g, const float2* __rest
   }
 }
 
-// One layer, one thread per site.  Weights [7][COUT][CIN] (BF16) are widened to
-// FP32 in shared memory; every thread of a warp reads the same weight, a
-// broadcast.
+// One layer, one thread per site.  Weights [7][COUT][CIN] (BF16) are widened
+// to FP32 in shared memory, transposed to [7][CIN][COUT] so that the COUT
+// weights of one (mu, c') pair are one or more 16-byte broadcast reads.  Site
+// coordinates are computed once per site in 32-bit arithmetic, and a
+// neighbour's CIN channels are read as 16-byte pairs.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) net_layer_kernel(Geo g, const float2* __restrict__ th32,
                                                         const __nv_bfloat16* __restrict__ W,
                                                         const float2* __restrict__ in, float2* __restrict__ out,
                                                         long long n) {
-  __shared__ float w[7 * COUT * CIN];
-  for (int k = threadIdx.x; k < 7 * COUT * CIN; k += blockDim.x) w[k] = __bfloat162float(W[k]);
+  __shared__ __align__(16) float w[7 * COUT * CIN];
+  for (int k = threadIdx.x; k < 7 * COUT * CIN; k += blockDim.x) {
+    const int mu = k / (COUT * CIN), c = (k / CIN) % COUT, cp = k % CIN;
+    w[(mu * CIN + cp) * COUT + c] = __bfloat162float(W[k]);
+  }
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const int V = g.V, L = g.L, N = g.Ntau;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)n; i += gridDim.x * blockDim.x) {
+    const int tau = i / V, s = i - tau * V, y = s / L, x = s - y * L;
+    const int base = tau * V;
     float2 acc[COUT];
 #pragma unroll
     for (int c = 0; c < COUT; ++c) acc[c] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int mu = 0; mu < 7; ++mu) {
-      long long j;
-      float2 ph;
-      net_neighbour(g, th32, i, mu, j, ph);
-      const float2* hin = in + j * CIN;
+      int j = i;
+      float2 ph = make_float2(1.f, 0.f);
+      float sn, cs;
+      if (mu == 1) {
+        j = base + y * L + (x + 1 == L ? 0 : x + 1);
+        __sincosf(__ldg(th32 + i).x, &sn, &cs);
+        ph = make_float2(cs, sn);
+      } else if (mu == 2) {
+        j = base + y * L + (x == 0 ? L - 1 : x - 1);
+        __sincosf(__ldg(th32 + j).x, &sn, &cs);
+        ph = make_float2(cs, -sn);
+      } else if (mu == 3) {
+        j = base + (y + 1 == L ? 0 : y + 1) * L + x;
+        __sincosf(__ldg(th32 + i).y, &sn, &cs);
+        ph = make_float2(cs, sn);
+      } else if (mu == 4) {
+        j = base + (y == 0 ? L - 1 : y - 1) * L + x;
+        __sincosf(__ldg(th32 + j).y, &sn, &cs);
+        ph = make_float2(cs, -sn);
+      } else if (mu == 5) {
+        const int tp = tau + 1 == N ? 0 : tau + 1;
+        j = tp * V + s;
+        ph = make_float2(tp == 0 ? -1.f : 1.f, 0.f);
+      } else if (mu == 6) {
+        const int tm = tau == 0 ? N - 1 : tau - 1;
+        j = tm * V + s;
+        ph = make_float2(tau == 0 ? -1.f : 1.f, 0.f);
+      }
+      const float* wm = w + mu * CIN * COUT;
 #pragma unroll
-      for (int cp = 0; cp < CIN; ++cp) {
-        const float2 v = cmulf(ph, hin[cp]);
-        const float* wc = w + (mu * COUT) * CIN + cp;
+      for (int cp2 = 0; cp2 < (CIN + 1) / 2; ++cp2) {
+        float2 hv[2];
+        if constexpr (CIN % 2 == 0) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(in + (size_t)j * CIN) + cp2);
+          hv[0] = make_float2(q.x, q.y);
+          hv[1] = make_float2(q.z, q.w);
+        } else {
+          hv[0] = __ldg(in + (size_t)j * CIN + 2 * cp2);
+          hv[1] = make_float2(0.f, 0.f);
+        }
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) {
-          const float wv = wc[c * CIN];
-          acc[c].x = fmaf(wv, v.x, acc[c].x);
-          acc[c].y = fmaf(wv, v.y, acc[c].y);
+        for (int h = 0; h < 2; ++h) {
+          const int cp = 2 * cp2 + h;
+          if (cp >= CIN) break;
+          const float2 v = cmulf(ph, hv[h]);
+          const float* wc = wm + cp * COUT;
+          if constexpr (COUT % 4 == 0) {
+#pragma unroll
+            for (int c4 = 0; c4 < COUT / 4; ++c4) {
+              const float4 wv = reinterpret_cast<const float4*>(wc)[c4];
+              acc[4 * c4 + 0].x = fmaf(wv.x, v.x, acc[4 * c4 + 0].x);
+              acc[4 * c4 + 0].y = fmaf(wv.x, v.y, acc[4 * c4 + 0].y);
+              acc[4 * c4 + 1].x = fmaf(wv.y, v.x, acc[4 * c4 + 1].x);
+              acc[4 * c4 + 1].y = fmaf(wv.y, v.y, acc[4 * c4 + 1].y);
+              acc[4 * c4 + 2].x = fmaf(wv.z, v.x, acc[4 * c4 + 2].x);
+              acc[4 * c4 + 2].y = fmaf(wv.z, v.y, acc[4 * c4 + 2].y);
+              acc[4 * c4 + 3].x = fmaf(wv.w, v.x, acc[4 * c4 + 3].x);
+              acc[4 * c4 + 3].y = fmaf(wv.w, v.y, acc[4 * c4 + 3].y);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < COUT; ++c) {
+              acc[c].x = fmaf(wc[c], v.x, acc[c].x);
+              acc[c].y = fmaf(wc[c], v.y, acc[c].y);
+            }
+          }
         }
       }
     }
-    float2* o = out + i * COUT;
+    if constexpr (COUT % 2 == 0) {
+      float4* o = reinterpret_cast<float4*>(out + (size_t)i * COUT);
 #pragma unroll
-    for (int c = 0; c < COUT; ++c) o[c] = acc[c];
+      for (int c2 = 0; c2 < COUT / 2; ++c2) o[c2] = make_float4(acc[2 * c2].x, acc[2 * c2].y, acc[2 * c2 + 1].x, acc[2 * c2 + 1].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) out[(size_t)i * COUT + c] = acc[c];
+    }
   }
 }
 
