@@ -62,11 +62,15 @@ struct hqmc_config {
   LineLaunch ll64{}, ll32{};
   double2* z64 = nullptr;
   float2* z32 = nullptr;
+  double2* r64b = nullptr;  // second residual buffers of the fused preconditioned update
+  float2* r32b = nullptr;
+  int fuse_pc64 = 1, fuse_pc32 = 1;  // preconditioned update fused with the preconditioner (autotuned)
   double* part_rz = nullptr;
   SliceLaunch fused64{}, fused32{};  // shapes used for APPLY / CG direction (nby > 0: register-blocked)
   float tuned_us64 = 0.f, tuned_us32 = 0.f;  // autotuner: time of one FP64 / FP32 apply (0: not tuned)
   SliceLaunch sl1{};   // apply_M and force (one CTA per slice, no cluster)
   int ew_grid = 0;    // CG update grid (= number of <r,r> partials)
+  int n_part_ew = 0;  // slots of part_ew: the update's or the fused preconditioned update's partials
   int act_grid = 0;
   int reliable = kDefaultReliable;
 
@@ -266,7 +270,7 @@ int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, 
   RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
   LK(1, (launch_mdagm<double, MODE_RESID>(cfg->sl, a, s)));
   RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
-  LK(1, launch_resid_finalize(cfg->part_resid, cfg->sl.grid, fin_mode, tol, maxit, cfg->part_ew, cfg->ew_grid,
+  LK(1, launch_resid_finalize(cfg->part_resid, cfg->sl.grid, fin_mode, tol, maxit, cfg->part_ew, cfg->n_part_ew,
                            cfg->st, cfg->report, gate, s));
   return HQMC_OK;
 }
@@ -285,21 +289,27 @@ int precondition(hqmc_config* cfg, const C2<R>* r, C2<R>* z, const CgState* st, 
   return HQMC_OK;
 }
 
+// One CG iteration: the direction step, then the vector update.  Preconditioned:
+// with `rb` set, the update is fused with the preconditioner and moves r from
+// r to rb (odd iterations of a loop body: from rb back to r); without it, the
+// plain update and a separate preconditioner application.
 template <class R>
 int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, const C2<R>* U, void* x,
-                 bool x_double, bool pc, C2<R>* z, cudaStream_t s) {
+                 bool x_double, bool pc, C2<R>* z, C2<R>* rb, int c, cudaStream_t s) {
+  const LineLaunch& ll = sizeof(R) == 8 ? cfg->ll64 : cfg->ll32;
+  const bool fused = pc && rb != nullptr;
   MdagmArgs<R> a = mdagm_args<R, MODE_CGDIR>(cfg);
   a.U = U;
   a.y = q;
   a.r = pc ? z : r;  // preconditioned CG: the direction is built from z = Otilde^{-1} r
   if (pc) {
     a.part_rz = cfg->part_rz;
-    a.n_part_rz = sizeof(R) == 8 ? cfg->ll64.gx * cfg->ll64.gy : cfg->ll32.gx * cfg->ll32.gy;
+    a.n_part_rz = ll.gx * ll.gy;
   }
   a.pbuf[0] = pbuf[0];
   a.pbuf[1] = pbuf[1];
   a.part_in = cfg->part_ew;
-  a.n_part_in = cfg->ew_grid;
+  a.n_part_in = fused ? ll.gx * ll.gy : cfg->ew_grid;
   a.part_out = cfg->part_mdagm;
   a.st = cfg->st;
   int slot;
@@ -308,6 +318,24 @@ int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, con
   LK(1, (launch_fused<R, MODE_CGDIR>(cfg, a, s)));
   RET(timer_end(cfg, tcls, s, slot));
   RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
+  if (fused) {
+    LineUpdArgs<R> u{};
+    u.x = reinterpret_cast<C2<R>*>(x);
+    u.r_in = (c & 1) ? rb : r;
+    u.r_out = (c & 1) ? r : rb;
+    u.p0 = pbuf[0];
+    u.p1 = pbuf[1];
+    u.q = q;
+    u.z = z;
+    u.part_pq = cfg->part_mdagm;
+    u.n_pq = fused_shape<R>(cfg).grid;
+    u.part_rr = cfg->part_ew;
+    u.part_rz = cfg->part_rz;
+    u.st = cfg->st;
+    LK(1, launch_line_update<R>(cfg->g, cfg->lc, ll, u, s));
+    RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
+    return HQMC_OK;
+  }
   LK(1, launch_cg_update<R>(cfg->n, cfg->ew_grid, x, x_double ? 1 : 0, r, pbuf, q, cfg->part_mdagm, fused_shape<R>(cfg).grid,
                          cfg->part_ew, cfg->st, s));
   RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
@@ -387,11 +415,16 @@ int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, c
   const bool mixed = solver_fp32(solver);
   const bool pc = solver_pc(solver);
   const int iters = mixed ? cfg->reliable : kBodyIters64;
+  // the fused preconditioned update alternates two residual buffers, so an even
+  // number of iterations per body leaves r where the body's residual expects it
+  const bool fuse = pc && (iters % 2 == 0) && (mixed ? cfg->fuse_pc32 : cfg->fuse_pc64);
   for (int c = 0; c < iters; ++c) {
     if (mixed)
-      RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, pc, cfg->z32, s));
+      RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, pc, cfg->z32,
+                              fuse ? cfg->r32b : nullptr, c, s));
     else
-      RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, pc, cfg->z64, s));
+      RET(cg_iteration<double>(cfg, cfg->r64, cfg->p64, cfg->q64, cfg->U64, x, true, pc, cfg->z64,
+                               fuse ? cfg->r64b : nullptr, c, s));
   }
   if (mixed) {
     LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, cfg->st, GATE_ACTIVE, s));
@@ -402,7 +435,7 @@ int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, c
     // after a restart z must follow the new r; otherwise this recomputes the same z
     if (pc) RET(precondition<double>(cfg, cfg->r64, cfg->z64, cfg->st, s));
   }
-  *nkernels = (pc ? 3 : 2) * iters + (mixed ? 3 : 2) + (pc ? 1 : 0);
+  *nkernels = (pc && !fuse ? 3 : 2) * iters + (mixed ? 3 : 2) + (pc ? 1 : 0);
   return HQMC_OK;
 }
 
@@ -653,10 +686,12 @@ int line_coefficients(hqmc_config* cfg) {
   cfg->pc_a = a;
   cfg->pc_b = b;
   cfg->lc = LineCoef{rho, std::pow(rho, W + 1), rho / b, W};
-  if (line_smem_bytes(8, W) > kMaxLineSmem)
+  if (line_smem_bytes(8, W) > kMaxLineSmem || line_update_smem_bytes(8, W) > kMaxLineSmem)
     return fail(cfg, HQMC_EUNSUPPORTED, "tau-line preconditioner width W=%d too large", W);
   CK(prepare_line_precond<double>(W));
   CK(prepare_line_precond<float>(W));
+  CK(prepare_line_update<double>(W));
+  CK(prepare_line_update<float>(W));
   CK(cudaDeviceSynchronize());
   return HQMC_OK;
 }
@@ -700,6 +735,65 @@ int time_shape(hqmc_config* cfg, const SliceLaunch& sh, float* us) {
   }
   cfg->launches += reps + 1;
   *us = 1e3f * ms / reps;
+  return HQMC_OK;
+}
+
+// Preconditioned CG: times the vector update fused with the preconditioner
+// against the plain update followed by a preconditioner application, on zero
+// vectors with a CG state set to "running", and keeps the faster form.
+template <class R>
+int tune_pc_update(hqmc_config* cfg) {
+  CgState h{};
+  h.done = CG_RUNNING;
+  h.k = h.k2 = 1;
+  h.maxit = 1 << 30;
+  h.rr[0] = h.rr[1] = 1.0;
+  CK(cudaMemcpy(cfg->st, &h, sizeof(CgState), cudaMemcpyHostToDevice));
+  std::vector<double> ones((size_t)cfg->sl.grid + 8, 1.0);
+  CK(cudaMemcpy(cfg->part_mdagm, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const bool dbl = sizeof(R) == 8;
+  C2<R>* r = dbl ? (C2<R>*)cfg->r64 : (C2<R>*)cfg->r32;
+  C2<R>* rb = dbl ? (C2<R>*)cfg->r64b : (C2<R>*)cfg->r32b;
+  C2<R>* q = dbl ? (C2<R>*)cfg->q64 : (C2<R>*)cfg->q32;
+  C2<R>* z = dbl ? (C2<R>*)cfg->z64 : (C2<R>*)cfg->z32;
+  C2<R>* x = dbl ? (C2<R>*)cfg->vscratch : (C2<R>*)cfg->xh32;
+  C2<R>* pb[2] = {dbl ? (C2<R>*)cfg->p64[0] : (C2<R>*)cfg->p32[0], dbl ? (C2<R>*)cfg->p64[1] : (C2<R>*)cfg->p32[1]};
+  for (C2<R>* v : {r, rb, q, z, x, pb[0], pb[1]}) CK(cudaMemset(v, 0, sizeof(C2<R>) * cfg->n));
+  const LineLaunch& ll = dbl ? cfg->ll64 : cfg->ll32;
+  const int npq = fused_shape<R>(cfg).grid;
+  auto fused = [&]() {
+    LineUpdArgs<R> u{x, r, rb, pb[0], pb[1], q, z, cfg->part_mdagm, npq, cfg->part_ew, cfg->part_rz, cfg->st};
+    return launch_line_update<R>(cfg->g, cfg->lc, ll, u, 0);
+  };
+  auto separate = [&]() {
+    cudaError_t e = launch_cg_update<R>(cfg->n, cfg->ew_grid, x, dbl ? 1 : 0, r, pb, q, cfg->part_mdagm, npq,
+                                        cfg->part_ew, cfg->st, 0);
+    if (e == cudaSuccess) e = launch_line_precond<R>(cfg->g, cfg->lc, ll, r, z, cfg->part_rz, cfg->st, 0);
+    return e;
+  };
+  float us[2] = {0.f, 0.f};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t err = cudaSuccess;
+  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+    // every launch advances st->k by one; the state stays "running"
+    err = v ? separate() : fused();
+    const int reps = 5;
+    if (err == cudaSuccess) err = cudaEventRecord(e0, 0);
+    for (int k = 0; k < reps && err == cudaSuccess; ++k) err = v ? separate() : fused();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    us[v] = 1e3f * ms / reps;
+    cfg->launches += (reps + 1) * (v ? 2 : 1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(err);
+  (dbl ? cfg->fuse_pc64 : cfg->fuse_pc32) = us[0] <= us[1] ? 1 : 0;
+  CK(cudaMemset(cfg->st, 0, sizeof(CgState)));
   return HQMC_OK;
 }
 
@@ -768,6 +862,8 @@ int autotune(hqmc_config* cfg) {
       cfg->tuned_us32 = best;
     }
   }
+  RET(tune_pc_update<double>(cfg));
+  RET(tune_pc_update<float>(cfg));
   CK(cudaDeviceSynchronize());
   return HQMC_OK;
 }
@@ -1002,12 +1098,15 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     // partials of the fused kernel: room for any cluster size (grid <= Ntau + 7)
     if ((rc = dalloc(cfg, &cfg->part_mdagm, 2 * ((size_t)p->Ntau + 8)))) break;
     if ((rc = dalloc(cfg, &cfg->part_resid, 2 * ((size_t)p->Ntau + 8)))) break;
-    if ((rc = dalloc(cfg, &cfg->part_ew, (size_t)cfg->ew_grid))) break;
-    if ((rc = dalloc(cfg, &cfg->part_act, 4 * (size_t)cfg->act_grid))) break;
     cfg->ll64 = line_launch(cfg->g, 8);
     cfg->ll32 = line_launch(cfg->g, 4);
+    cfg->n_part_ew = std::max(cfg->ew_grid, std::max(cfg->ll64.gx * cfg->ll64.gy, cfg->ll32.gx * cfg->ll32.gy));
+    if ((rc = dalloc(cfg, &cfg->part_ew, (size_t)cfg->n_part_ew))) break;
+    if ((rc = dalloc(cfg, &cfg->part_act, 4 * (size_t)cfg->act_grid))) break;
     if ((rc = dalloc(cfg, &cfg->z64, n))) break;
     if ((rc = dalloc(cfg, &cfg->z32, n))) break;
+    if ((rc = dalloc(cfg, &cfg->r64b, n))) break;
+    if ((rc = dalloc(cfg, &cfg->r32b, n))) break;
     if ((rc = dalloc(cfg, &cfg->part_rz,
                      (size_t)std::max(cfg->ll64.gx * cfg->ll64.gy, cfg->ll32.gx * cfg->ll32.gy)))) break;
     if ((rc = dalloc(cfg, &cfg->terms, 8))) break;

@@ -180,6 +180,29 @@ cudaError_t launch_line_precond(const Geo& g, const LineCoef& lc, const LineLaun
                                 double* part_rz, const CgState* st, cudaStream_t s);
 cudaError_t launch_pi_flux(const Geo& g, double* theta, cudaStream_t s);
 
+// Preconditioned CG: the vector update fused with the preconditioner (precond.cu).
+template <class R>
+struct LineUpdArgs {
+  C2<R>* x;               // iterate (FP64) or FP32 correction (mixed)
+  const C2<R>* r_in;      // residual before the step (read with halos)
+  C2<R>* r_out;           // residual after the step (a different buffer)
+  const C2<R>* p0;        // directions: the one used is pbuf[(k2+1)&1]
+  const C2<R>* p1;
+  const C2<R>* q;         // O p
+  C2<R>* z;               // Otilde^{-1} r (output)
+  const double* part_pq;  // partials of <p, O p>
+  int n_pq;
+  double* part_rr;        // per-tile partials of <r, r> and <r, z>
+  double* part_rz;
+  CgState* st;
+};
+size_t line_update_smem_bytes(int real_bytes, int W);
+template <class R>
+cudaError_t prepare_line_update(int W);
+template <class R>
+cudaError_t launch_line_update(const Geo& g, const LineCoef& lc, const LineLaunch& ll, const LineUpdArgs<R>& a,
+                               cudaStream_t s);
+
 // Fused M^dagger M over many chains in one launch (generic kernel, links from
 // memory): CTA b runs cluster tile b / C = (chain, first slice) of `tiles`.
 template <class R, int MODE>

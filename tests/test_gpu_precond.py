@@ -134,3 +134,19 @@ def test_preconditioned_edge_cases(hq):
         with pytest.raises(hq.HQMCError) as e:
             hq.apply_precond(cfg, phi, z=phi)
         assert e.value.status == hq.EINVAL
+
+
+@pytest.mark.parametrize("reliable", [25, 50])
+def test_fused_and_separate_preconditioned_updates_agree(hq, reliable):
+    """An odd reliable-update period keeps the separate update and preconditioner
+    (the fused form alternates two residual buffers and needs an even loop body);
+    both reach the same solution."""
+    L, N = 12, 48
+    lat = oracle.Lattice(L, N)
+    th = inputs.theta_ordered(L, N, 81, tau_walk=0.0)
+    phi = inputs.complex_gaussian(L, N, 82)
+    Xo, _, _ = opc.pcg(lat, th, phi, opc.coefficients(lat), tol=1e-12)
+    with hq.Config(L, N, reliable_interval=reliable) as cfg:
+        X, info = hq.cg_solve(cfg, cuda(th), cuda(phi), tol=1e-9, solver="pmixed")
+    assert info["status"] == 0 and info["true_residual"] <= 1e-9
+    assert rel(X.cpu().numpy(), Xo) < 1e-5
