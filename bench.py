@@ -61,6 +61,8 @@ WORKLOADS = {
 BATCH_LATTICES = [(L, 10 * L) for L in (12, 16, 20, 24) for _ in range(8)]
 WORKLOADS["batched_32chains_L12-24"] = dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=0.0005, tol=1e-8,
                                             solver="cg64", seed=100, start="cold", batched=True)
+# the same batch with the tau-line preconditioner in the batched CG (FP64)
+WORKLOADS["batched_32chains_L12-24_pcg64"] = dict(WORKLOADS["batched_32chains_L12-24"], solver="pcg64")
 # learned + mixed precision at L = 66, Ntau = 660 against plain FP64 on the same chain state: the net is
 # trained (untimed) on (theta, phi, x) triples the sampler produces at this size; dt keeps |dH| ~ V dt^2
 # as at L = 24
@@ -178,7 +180,8 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
 # CG iterations per trajectory used to scale oracle samples when no GPU run is
 # available (the reference arm); measured on the GPU with the same algorithm.
 ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 11000.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 16500.0,
-                     "batched_32chains_L12-24": 11000.0, "hmc_learned_fp32_L66_Nt660": 2640.0,
+                     "batched_32chains_L12-24": 11000.0, "batched_32chains_L12-24_pcg64": 1800.0,
+                     "hmc_learned_fp32_L66_Nt660": 2640.0,
                      "estimate_L66_Nt660_40rv": 250.0}
 # oracle CG iterations per bounded sample (the largest lattices take about a second per iteration on the host)
 ORACLE_SAMPLE_ITERS = {"hmc_learned_fp32_L66_Nt660": 4, "hmc_mixed_L48_Nt480": 6, "estimate_L66_Nt660_40rv": 4}
@@ -520,6 +523,7 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
     thetas = [torch.from_numpy(inputs.theta_ordered(L, N, s, tau_walk=0.0)).cuda() for (L, N), s in zip(lats, seeds)]
     stream = torch.cuda.current_stream()
     with hqmc.Batch(lats) as b:
+        b.set_solver(wl["solver"])
         for k in range(args.warmup):
             b.trajectory(thetas, seeds, k, wl["nsteps"], dts, tol=wl["tol"])
         if world > 1:
@@ -546,7 +550,8 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
         with hqmc.Config(L, N, variant=1) as cfg:
             a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            hqmc.trajectory(cfg, th.clone(), seed=s, traj_counter=10 ** 6, nsteps=wl["nsteps"], dt=dt, tol=wl["tol"])
+            hqmc.trajectory(cfg, th.clone(), seed=s, traj_counter=10 ** 6, nsteps=wl["nsteps"], dt=dt, tol=wl["tol"],
+                            solver=wl["solver"])
             z.record(stream)
             torch.cuda.synchronize()
             seq_ms += a.elapsed_time(z)
@@ -558,7 +563,9 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl_name, "chains": len(lats), "lattices": "L in {12,16,20,24} x 8, Ntau = 10 L",
                        "n_leapfrog": wl["nsteps"], "dt": "0.0005 * sqrt(138240 / sites)", "cg_tol": wl["tol"],
-                       "solver": "cg64 (batched: one fused launch + one update launch per CG iteration)"},
+                       "solver": wl["solver"] + " (batched: one fused launch + one update launch" +
+                                 (" + one preconditioner launch" if wl["solver"] == "pcg64" else "") +
+                                 " per CG iteration for all chains)"},
             "gpu_launches": int(launches),
             "sequential_traj_per_s": len(lats) / (seq_ms / 1e3),
             "batched_over_sequential": value / (len(lats) / (seq_ms / 1e3)),

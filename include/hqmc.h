@@ -310,6 +310,12 @@ typedef struct hqmc_batch hqmc_batch;
 HQMC_API int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out);
 HQMC_API int hqmc_free_batch(hqmc_batch* b);
 HQMC_API const char* hqmc_batch_last_error(const hqmc_batch* b);
+
+/* Solver of the batch's CG loop: HQMC_SOLVER_CG64 (default) or HQMC_SOLVER_PCG64, the
+ * FP64 CG preconditioned with each chain's tau-line preconditioner (hqmc_apply_precond),
+ * applied to all chains in one launch per iteration.  A chain's results are those of
+ * its own config made with variant 1 and the same solver. */
+HQMC_API int hqmc_batch_set_solver(hqmc_batch* b, int solver);
 /* Kernels the batch has enqueued (including its chains' configs). */
 HQMC_API long long hqmc_batch_launch_count(const hqmc_batch* b);
 

@@ -417,7 +417,7 @@ int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, c
   const int iters = mixed ? cfg->reliable : kBodyIters64;
   // the fused preconditioned update alternates two residual buffers, so an even
   // number of iterations per body leaves r where the body's residual expects it
-  const bool fuse = pc && (iters % 2 == 0) && (mixed ? cfg->fuse_pc32 : cfg->fuse_pc64);
+  const bool fuse = pc && (iters % 2 == 0) && (mixed ? cfg->fuse_pc32 : cfg->fuse_pc64) && cfg->p.variant != 1;
   for (int c = 0; c < iters; ++c) {
     if (mixed)
       RET(cg_iteration<float>(cfg, cfg->r32, cfg->p32, cfg->q32, cfg->U32, cfg->xh32, false, pc, cfg->z32,
@@ -1473,6 +1473,11 @@ struct hqmc_batch {
   int2* d_ublocks = nullptr;
   int* d_unblocks = nullptr;
   CgState** d_states = nullptr;
+  int solver = HQMC_SOLVER_CG64;  // CG64 or PCG64 (tau-line preconditioner)
+  LineBatchDesc<double>* d_line = nullptr;  // per-chain preconditioner descriptors
+  int4* d_ltiles = nullptr;                 // (chain, bx, by) tiles of the batched preconditioner
+  int nltiles = 0;
+  int maxW = 0;
   void* h_stage = nullptr;  // pinned staging of the descriptor arrays
   size_t stage_bytes = 0;
   cudaStream_t cap = nullptr;
@@ -1520,6 +1525,8 @@ void batch_release(hqmc_batch* b) {
   cudaFree(b->d_ublocks);
   cudaFree(b->d_unblocks);
   cudaFree(b->d_states);
+  cudaFree(b->d_line);
+  cudaFree(b->d_ltiles);
   if (b->h_stage) cudaFreeHost(b->h_stage);
   for (hqmc_config* c : b->cfgs) hqmc_free_config(c);
   b->cfgs.clear();
@@ -1534,13 +1541,20 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
   auto* rl = rs + nc;
   auto* up = (UpdArgs<double>*)(rl + nc);
   auto* fin = (FinArgs*)(up + nc);
+  auto* ld = (LineBatchDesc<double>*)(fin + nc);
+  const bool pc = b->solver == HQMC_SOLVER_PCG64;
   for (int c = 0; c < nc; ++c) {
     hqmc_config* cfg = b->cfgs[c];
     const int nslots = (cfg->p.Ntau + b->C - 1) / b->C * b->C;
     MdagmArgs<double> a = mdagm_args<double, MODE_CGDIR>(cfg);
     a.U = cfg->U64;
     a.y = cfg->q64;
-    a.r = cfg->r64;
+    a.r = pc ? cfg->z64 : cfg->r64;
+    if (pc) {
+      a.part_rz = cfg->part_rz;
+      a.n_part_rz = cfg->ll64.gx * cfg->ll64.gy;
+    }
+    ld[c] = LineBatchDesc<double>{cfg->g, cfg->lc, cfg->r64, cfg->z64, cfg->part_rz, cfg->st, cfg->ll64.gx};
     a.pbuf[0] = cfg->p64[0];
     a.pbuf[1] = cfg->p64[1];
     a.part_in = cfg->part_ew;
@@ -1571,17 +1585,21 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
   BCK(cudaMemcpyAsync(b->d_resid_loop, rl, nc * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(b->d_upd, up, nc * sizeof(UpdArgs<double>), cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(b->d_fin, fin, nc * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_line, ld, nc * sizeof(LineBatchDesc<double>), cudaMemcpyHostToDevice, s));
   return HQMC_OK;
 }
 
 int batch_body(hqmc_batch* b, cudaStream_t s) {
   const int nc = (int)b->cfgs.size();
+  const bool pc = b->solver == HQMC_SOLVER_PCG64;
   for (int it = 0; it < kBodyIters64; ++it) {
     BCK((launch_mdagm_batch<double, MODE_CGDIR>(b->d_cgdir, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
     BCK(launch_cg_update_batch(b->d_upd, b->d_ublocks, b->d_unblocks, b->total_ublocks, s));
+    if (pc) BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, s));
   }
   BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_loop, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
   BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_RESTART, 0.0, 0, GATE_REC, s));
+  if (pc) BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, s));
   return HQMC_OK;
 }
 
@@ -1620,7 +1638,8 @@ int batch_graph(hqmc_batch* b) {
   }
   cudaGraphDestroy(graph);
   if (rc != HQMC_OK) cudaGetLastError();
-  b->body_kernels = 2 * kBodyIters64 + 3;
+  const bool pc = b->solver == HQMC_SOLVER_PCG64;
+  b->body_kernels = (pc ? 3 : 2) * kBodyIters64 + 3 + (pc ? 1 : 0);
   return rc;
 }
 
@@ -1633,6 +1652,10 @@ int batch_solve(hqmc_batch* b, const double2* const* phi, double2* const* x, dou
   BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_start, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
   BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_START, tol, maxit, GATE_ALWAYS, s));
   b->launches += 2;
+  if (b->solver == HQMC_SOLVER_PCG64) {
+    BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, s));
+    b->launches += 1;
+  }
   if ((rc = batch_graph(b)) != HQMC_OK) return rc;
   BCK(cudaGraphLaunch(b->exec, s));
   int worst = HQMC_OK;
@@ -1659,7 +1682,8 @@ int batch_solve(hqmc_batch* b, const double2* const* phi, double2* const* x, dou
     inf.status = status;
     inf.iterations = st.k;
     inf.true_residual = st.bb > 0 ? std::sqrt(cfg->report_h[0] / st.bb) : 0.0;
-    inf.recursive_residual = st.bb > 0 ? std::sqrt(st.rr[st.k & 1] / st.bb) : 0.0;
+    const double rr_rec = (b->solver == HQMC_SOLVER_PCG64 && st.k > st.seg_start) ? st.rr_rec : st.rr[st.k & 1];
+    inf.recursive_residual = st.bb > 0 ? std::sqrt(rr_rec / st.bb) : 0.0;
     if (status == HQMC_OK && !(inf.true_residual <= tol)) status = inf.status = HQMC_ENOTCONV;
     if (infos) infos[c] = inf;
     worst = merge_status(worst, status);
@@ -1712,6 +1736,20 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
     }
     b->ntiles = (int)tiles.size();
     b->total_ublocks = (int)ublocks.size();
+    // tiles of the batched preconditioner: every chain's own (bx, by) grid
+    std::vector<int4> ltiles;
+    for (int c = 0; c < nchains; ++c) {
+      const LineLaunch& ll = b->cfgs[c]->ll64;
+      b->maxW = std::max(b->maxW, b->cfgs[c]->lc.W);
+      for (int by = 0; by < ll.gy; ++by)
+        for (int bx = 0; bx < ll.gx; ++bx) ltiles.push_back(make_int4(c, bx, by, 0));
+    }
+    b->nltiles = (int)ltiles.size();
+    if (prepare_line_precond_batch(b->maxW) != cudaSuccess) {
+      cudaGetLastError();
+      rc = bfail(b, HQMC_EUNSUPPORTED, "batched preconditioner does not fit");
+      break;
+    }
     std::vector<CgState*> states;
     for (hqmc_config* cfg : b->cfgs) states.push_back(cfg->st);
     auto dal = [&](void** p, size_t bytes) {
@@ -1728,11 +1766,14 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
         !dal((void**)&b->d_fin, nchains * sizeof(FinArgs)) || !dal((void**)&b->d_tiles, tiles.size() * sizeof(int2)) ||
         !dal((void**)&b->d_ublocks, ublocks.size() * sizeof(int2)) ||
         !dal((void**)&b->d_unblocks, unblocks.size() * sizeof(int)) ||
-        !dal((void**)&b->d_states, states.size() * sizeof(CgState*))) {
+        !dal((void**)&b->d_states, states.size() * sizeof(CgState*)) ||
+        !dal((void**)&b->d_line, nchains * sizeof(LineBatchDesc<double>)) ||
+        !dal((void**)&b->d_ltiles, ltiles.size() * sizeof(int4))) {
       rc = bfail(b, HQMC_ENOMEM, "batch tables");
       break;
     }
-    b->stage_bytes = nchains * (3 * sizeof(MdagmArgs<double>) + sizeof(UpdArgs<double>) + sizeof(FinArgs));
+    b->stage_bytes = nchains * (3 * sizeof(MdagmArgs<double>) + sizeof(UpdArgs<double>) + sizeof(FinArgs) +
+                                sizeof(LineBatchDesc<double>));
     if (cudaMallocHost(&b->h_stage, b->stage_bytes) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
@@ -1742,7 +1783,8 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
     if (cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_ublocks, ublocks.data(), ublocks.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_unblocks, unblocks.data(), unblocks.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_states, states.data(), states.size() * sizeof(CgState*), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(b->d_states, states.data(), states.size() * sizeof(CgState*), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_ltiles, ltiles.data(), ltiles.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
       rc = bfail(b, HQMC_ECUDA, "batch table upload");
       break;
     }
@@ -1766,6 +1808,19 @@ int hqmc_free_batch(hqmc_batch* b) {
 }
 
 const char* hqmc_batch_last_error(const hqmc_batch* b) { return b ? b->err : "no batch"; }
+
+int hqmc_batch_set_solver(hqmc_batch* b, int solver) {
+  if (!b) return HQMC_EINVAL;
+  if (solver != HQMC_SOLVER_CG64 && solver != HQMC_SOLVER_PCG64)
+    return bfail(b, HQMC_EINVAL, "batched solver must be HQMC_SOLVER_CG64 or HQMC_SOLVER_PCG64");
+  if (solver != b->solver && b->exec) {  // the loop body changes: capture it again on next use
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->solver = solver;
+  return HQMC_OK;
+}
 
 long long hqmc_batch_launch_count(const hqmc_batch* b) {
   if (!b) return 0;

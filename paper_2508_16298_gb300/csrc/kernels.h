@@ -180,6 +180,21 @@ cudaError_t launch_line_precond(const Geo& g, const LineCoef& lc, const LineLaun
                                 double* part_rz, const CgState* st, cudaStream_t s);
 cudaError_t launch_pi_flux(const Geo& g, double* theta, cudaStream_t s);
 
+// Batched preconditioner: one launch over the tiles (chain, bx, by) of many chains.
+template <class R>
+struct LineBatchDesc {
+  Geo g;
+  LineCoef lc;
+  const C2<R>* u;
+  C2<R>* z;
+  double* part;
+  const CgState* st;
+  int gx;  // the chain's own tile grid width (partial index by * gx + bx)
+};
+cudaError_t launch_line_precond_batch(const LineBatchDesc<double>* descs, const int4* tiles, int ntiles, int W,
+                                     cudaStream_t s);
+cudaError_t prepare_line_precond_batch(int W);
+
 // Preconditioned CG: the vector update fused with the preconditioner (precond.cu).
 template <class R>
 struct LineUpdArgs {

@@ -62,22 +62,21 @@ size_t line_smem_bytes(int real_bytes, int W) {
   return (size_t)((tc + 2 * W + 1) + (tc + W + 1)) * kLineSites * 2 * real_bytes;
 }
 
+// One tile (site block bx, slice block by of a gx-wide grid) of z = Otilde^{-1} u
+// with its partial of <u, z> in part[by * gx + bx].
 template <class R>
-__global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_kernel(Geo g, LineCoef lc,
-                                                                             const C2<R>* __restrict__ u,
-                                                                             C2<R>* __restrict__ z,
-                                                                             double* __restrict__ part,
-                                                                             const CgState* st) {
+__device__ __forceinline__ void line_precond_tile(const Geo& g, const LineCoef& lc, const C2<R>* __restrict__ u,
+                                                  C2<R>* __restrict__ z, double* __restrict__ part, int bx, int by,
+                                                  int gx) {
   using T = C2<R>;
   constexpr int TC = line_tile_slices<R>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
-  if (!line_gate(st)) return;  // uniform over the grid
   const int N = g.Ntau, V = g.V, W = lc.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int s0 = blockIdx.x * kLineSites, s = s0 + lane;
+  const int s0 = bx * kLineSites, s = s0 + lane;
   const bool site_ok = s < V;
-  const int t0 = blockIdx.y * TC, t1 = min(N, t0 + TC), nt = t1 - t0;
+  const int t0 = by * TC, t1 = min(N, t0 + TC), nt = t1 - t0;
   const int nu = nt + 2 * W + 1;  // rows of u: slices t0 - W .. t1 + W
   const int nx = nt + W + 1;      // rows of x: slices t0 .. t1 + W
   T* U = reinterpret_cast<T*>(smem_raw);
@@ -161,8 +160,30 @@ __global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_kernel(Ge
   }
   if (part) {
     const double tot = block_sum((double)dot, red);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    if (threadIdx.x == 0) part[by * gx + bx] = tot;
   }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_kernel(Geo g, LineCoef lc,
+                                                                             const C2<R>* __restrict__ u,
+                                                                             C2<R>* __restrict__ z,
+                                                                             double* __restrict__ part,
+                                                                             const CgState* st) {
+  if (!line_gate(st)) return;  // uniform over the grid
+  line_precond_tile<R>(g, lc, u, z, part, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+// Many chains in one launch: block b runs tile tiles[b] = (chain, bx, by) with
+// that chain's descriptor, so each chain's tiles and partials are those of its
+// own launch.
+template <class R>
+__global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_batch_kernel(
+    const LineBatchDesc<R>* __restrict__ descs, const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  const LineBatchDesc<R> d = descs[t.x];
+  if (!line_gate(d.st)) return;  // uniform over the block
+  line_precond_tile<R>(d.g, d.lc, d.u, d.z, d.part, t.y, t.z, d.gx);
 }
 
 // Preconditioned CG, fused update and preconditioner (one launch per iteration
@@ -398,6 +419,16 @@ cudaError_t launch_line_precond(const Geo& g, const LineCoef& lc, const LineLaun
   const dim3 grid(ll.gx, ll.gy);
   line_precond_kernel<R><<<grid, ll.block, line_smem_bytes(sizeof(R), lc.W), s>>>(g, lc, r, z, part_rz, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_line_precond_batch(const LineBatchDesc<double>* descs, const int4* tiles, int ntiles, int W,
+                                     cudaStream_t s) {
+  line_precond_batch_kernel<double><<<ntiles, kLineSites * kLineWarps, line_smem_bytes(8, W), s>>>(descs, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_line_precond_batch(int W) {
+  return raise_smem_limit(line_precond_batch_kernel<double>, line_smem_bytes(8, W));
 }
 
 template cudaError_t launch_line_precond<double>(const Geo&, const LineCoef&, const LineLaunch&, const double2*,

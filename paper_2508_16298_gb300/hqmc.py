@@ -41,6 +41,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
            "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory",
+           "hqmc_batch_set_solver",
            "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
            "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner")
 
@@ -103,6 +104,7 @@ _sig = {
     "hqmc_free_batch": ([_vp], _i),
     "hqmc_batch_last_error": ([_vp], ctypes.c_char_p),
     "hqmc_batch_launch_count": ([_vp], ctypes.c_longlong),
+    "hqmc_batch_set_solver": ([_vp, _i], _i),
     "hqmc_batch_cg_solve": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
                              ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_batch_trajectory": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), _u64, _i,
@@ -439,6 +441,10 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(_lib.hqmc_batch_launch_count(self._h))
+
+    def set_solver(self, solver):
+        """"cg64" (default) or "pcg64" for every chain (hqmc_batch_set_solver)."""
+        self._check(_lib.hqmc_batch_set_solver(self._h, _solver(solver)))
 
     def _check(self, rc, allow=(OK,)):
         if rc not in allow:

@@ -53,3 +53,43 @@ def test_batched_trajectory_equals_independent_trajectories(hq):
 def test_batch_rejects_bad_lattice(hq):
     with pytest.raises(hq.HQMCError):
         hq.Batch([(8, 16), (9, 16)])
+
+
+def test_batched_preconditioned_cg_equals_independent_solves(hq):
+    """The tau-line preconditioner in the batch: one launch over every chain's tiles,
+    bit for bit the results of single-chain PCG64 solves (variant 1 keeps the same
+    separate update and preconditioner kernels)."""
+    thetas = [torch.from_numpy(inputs.theta_ordered(L, N, 800 + i, tau_walk=0.0)).cuda()
+              for i, (L, N) in enumerate(LATS)]
+    phis = [torch.from_numpy(inputs.complex_gaussian(L, N, 900 + i)).cuda() for i, (L, N) in enumerate(LATS)]
+    with hq.Batch(LATS) as b:
+        xs0, infos0 = b.cg_solve(thetas, phis, tol=1e-10)
+        b.set_solver("pcg64")
+        xs, infos = b.cg_solve(thetas, phis, tol=1e-10)
+    for i, (L, N) in enumerate(LATS):
+        with hq.Config(L, N, variant=1) as cfg:
+            x1, info1 = hq.cg_solve(cfg, thetas[i], phis[i], tol=1e-10, solver="pcg64")
+        assert infos[i]["status"] == 0 and infos[i]["iterations"] == info1["iterations"]
+        assert infos[i]["iterations"] < infos0[i]["iterations"]
+        assert torch.equal(xs[i], x1), i
+        assert infos[i]["true_residual"] == info1["true_residual"]
+
+
+def test_batched_preconditioned_trajectory_equals_independent_trajectories(hq):
+    th0 = [inputs.theta_hot(L, N, 1000 + i) for i, (L, N) in enumerate(LATS)]
+    seeds = [31 + i for i in range(len(LATS))]
+    dts = [0.02, 0.015, 0.01, 0.02]
+    with hq.Batch(LATS) as b:
+        b.set_solver("pcg64")
+        thetas = [torch.from_numpy(t).cuda() for t in th0]
+        infos = b.trajectory(thetas, seeds, traj_counter=5, nsteps=3, dts=dts, tol=1e-10)
+        with pytest.raises(hq.HQMCError):
+            b.set_solver("mixed")
+    for i, (L, N) in enumerate(LATS):
+        with hq.Config(L, N, variant=1) as cfg:
+            t1 = torch.from_numpy(th0[i]).cuda()
+            info1 = hq.trajectory(cfg, t1, seed=seeds[i], traj_counter=5, nsteps=3, dt=dts[i], tol=1e-10,
+                                  solver="pcg64")
+        assert infos[i]["dH"] == info1["dH"] and infos[i]["accepted"] == info1["accepted"], i
+        assert infos[i]["cg_iterations"] == info1["cg_iterations"]
+        assert torch.equal(thetas[i], t1), i
