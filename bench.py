@@ -83,6 +83,12 @@ MDAGM_FLOPS_PER_SITE = 134
 MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pmixed": 40, "plearned": 40}
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu capture summarised in
+# profiles/mdagm_walk_fp32_L66_Nt660.md (cold caches; writes still in L2 at the kernel's end are not
+# counted there).  Valid for the kernel as captured; set to None when the kernel changes.
+NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 79.5456e6 + 10.34624e6}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -453,8 +459,10 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     shape = cfg.launch_shape(hqmc.FP32 if fp32 else hqmc.FP64)
     kname = kernel_name(shape, "float" if fp32 else "double")
     if fp32:  # the FP32 fused kernel is bounded by HBM bandwidth
+        traffic = NCU_TRAFFIC_BYTES.get(wl_name)
         roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved_gbs,
-                    "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm, "traffic": None,
+                    "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm, "traffic": traffic,
+                    "traffic_note": "DRAM read + write bytes per launch, ncu (profiles/)" if traffic else None,
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "bytes_per_site": MDAGM_BYTES_PER_SITE[wl["solver"]], "sites_per_launch": sites,
                     "tflops_algorithmic": achieved_tflops, "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms,

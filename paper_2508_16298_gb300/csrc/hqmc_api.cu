@@ -24,6 +24,7 @@ constexpr int kBodyIters64 = 16;      // FP64 CG iterations per loop body
 constexpr int kDefaultReliable = 50;  // mixed solver residual-update period (iterations per body)
 constexpr int kMaxBreakdowns = 8;     // mixed solver: FP32 breakdown restarts before the FP64 fallback
 constexpr size_t kMaxLineSmem = 227 * 1024;  // tau-line preconditioner tile: opt-in shared memory per block
+constexpr long long kFuseMaxSites = 2000000;  // fused preconditioned update by default up to this size
 constexpr double kLineTruncation = 1e-3;  // entries of the factor's inverse below this are dropped (Methods)
 constexpr size_t kMaxGraphs = 8;      // cached solve graphs per config
 
@@ -64,7 +65,8 @@ struct hqmc_config {
   float2* z32 = nullptr;
   double2* r64b = nullptr;  // second residual buffers of the fused preconditioned update
   float2* r32b = nullptr;
-  int fuse_pc64 = 1, fuse_pc32 = 1;  // preconditioned update fused with the preconditioner (autotuned)
+  int fuse_pc64 = 1, fuse_pc32 = 1;  // preconditioned update fused with the preconditioner (autotuned;
+                                     // default: fused below kFuseMaxSites, where it measured faster)
   double* part_rz = nullptr;
   SliceLaunch fused64{}, fused32{};  // shapes used for APPLY / CG direction (nby > 0: register-blocked)
   float tuned_us64 = 0.f, tuned_us32 = 0.f;  // autotuner: time of one FP64 / FP32 apply (0: not tuned)
@@ -1130,6 +1132,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
       break;
     }
     if ((rc = line_coefficients(cfg)) != HQMC_OK) break;
+    cfg->fuse_pc64 = cfg->fuse_pc32 = n <= kFuseMaxSites ? 1 : 0;
     if (p->autotune && (rc = autotune(cfg)) != HQMC_OK) break;
   } while (0);
   if (rc != HQMC_OK) {
