@@ -375,6 +375,8 @@ struct hqmc_net {
   float* v = nullptr;
   void* wb = nullptr;      // BF16 weights used by the layers
   void* wt = nullptr;      // BF16 adjoint weights (backward stencil)
+  std::vector<float> hw;   // host copy of the BF16 weights as floats (inference launches take them by value)
+  int hw_valid = 0;        // cleared when a training step changes the device weights
   int steps = 0;
   int device = 0;
 };
@@ -394,11 +396,28 @@ int net_workspace(hqmc_config* cfg) {
 }
 
 // z = K(theta) r for complex-double r, z; the float theta table must be current.
-int net_forward(hqmc_config* cfg, hqmc_net* net, const double2* r, double2* z, cudaStream_t s) {
+// Inference layers take the weights by value from the host copy (refreshed
+// from the device after training steps); the training forward pass reads the
+// device weights that its Adam steps update.
+int net_forward(hqmc_config* cfg, hqmc_net* net, const double2* r, double2* z, cudaStream_t s,
+                bool host_weights = true) {
+  if (host_weights && !net->hw_valid) {
+    std::vector<__nv_bfloat16> hb(net->total);
+    CK(cudaMemcpyAsync(hb.data(), net->wb, net->total * sizeof(__nv_bfloat16), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    net->hw.resize(net->total);
+    for (int e = 0; e < net->total; ++e) net->hw[e] = __bfloat162float(hb[e]);
+    net->hw_valid = 1;
+  }
   LK(1, launch_net_convert(r, cfg->net_h[0], 1, 1.0, cfg->n, s));
-  for (int l = 0; l < kNetLayers; ++l)
-    LK(1, launch_net_layer(cfg->g, cfg->th32, (const char*)net->wb + 2 * (size_t)net->off[l], net->cin[l], net->cout[l],
-                           cfg->net_h[l], cfg->net_h[l + 1], s));
+  for (int l = 0; l < kNetLayers; ++l) {
+    if (host_weights)
+      LK(1, launch_net_layer_host_weights(cfg->g, cfg->th32, net->hw.data() + net->off[l], net->cin[l], net->cout[l],
+                                          cfg->net_h[l], cfg->net_h[l + 1], s));
+    else
+      LK(1, launch_net_layer(cfg->g, cfg->th32, (const char*)net->wb + 2 * (size_t)net->off[l], net->cin[l],
+                             net->cout[l], cfg->net_h[l], cfg->net_h[l + 1], s));
+  }
   if (z) LK(1, launch_net_convert(cfg->net_h[kNetLayers], z, 0, 1.0, cfg->n, s));
   return HQMC_OK;
 }
@@ -1966,6 +1985,9 @@ int net_upload(hqmc_net* net, const float* host) {
     cudaGetLastError();
     return HQMC_ECUDA;
   }
+  net->hw.resize(net->total);
+  for (int e = 0; e < net->total; ++e) net->hw[e] = __bfloat162float(hb[e]);
+  net->hw_valid = 1;
   net->steps = 0;
   return HQMC_OK;
 }
@@ -2054,7 +2076,8 @@ int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, co
   cudaStream_t s = (cudaStream_t)stream;
   RET(net_workspace(cfg));
   RET(theta_float(cfg, theta, s));
-  RET(net_forward(cfg, net, (const double2*)phi, nullptr, s));  // activations h0..h4
+  RET(net_forward(cfg, net, (const double2*)phi, nullptr, s, false));  // activations h0..h4
+  net->hw_valid = 0;  // this step's Adam update changes the device weights
   // ||x||^2 on the device, then the loss and its gradient with respect to h4
   LK(2, launch_action_terms(cfg->g, cfg->bp, theta, nullptr, (const double2*)x, (const double2*)x, cfg->act_grid,
                             cfg->part_act, cfg->terms, s));

@@ -332,6 +332,10 @@ cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, c
 // Learned preconditioner (net.cu).  Weights are BF16 [7][cout][cin] per layer.
 cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, int cin, int cout, const float2* in,
                              float2* out, cudaStream_t s);
+// Inference layer with the weights passed by value from host memory ([7][cout][cin] FP32 values of
+// the BF16 weights): the same arithmetic as launch_net_layer.
+cudaError_t launch_net_layer_host_weights(const Geo& g, const float2* th32, const float* w, int cin, int cout,
+                                         const float2* in, float2* out, cudaStream_t s);
 cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
                              double* partials, int nchunks, cudaStream_t s);
 cudaError_t launch_net_loss(const float2* h, const double2* x, const double* xx, float2* d, double* part, int nblocks,

@@ -179,6 +179,106 @@ __global__ void __launch_bounds__(256) net_layer_kernel(Geo g, const float2* __r
   }
 }
 
+// Inference form of the same layer.  The weights arrive as a kernel parameter
+// (constant bank), transposed to [7][CIN][COUT]; with the direction and channel
+// loops fully unrolled every weight index is a compile-time constant, so each
+// FMA reads its weight straight from the constant bank: no shared-memory fill,
+// no weight loads and no waits on them.  The arithmetic and its order are those
+// of net_layer_kernel, so the results are identical.
+template <int CIN, int COUT>
+struct NetLayerW {
+  float w[7][CIN][COUT];
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) net_layer_cw_kernel(Geo g, const float2* __restrict__ th32,
+                                                           const __grid_constant__ NetLayerW<CIN, COUT> W,
+                                                           const float2* __restrict__ in, float2* __restrict__ out,
+                                                           int n) {
+  const int V = g.V, L = g.L, N = g.Ntau;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int tau = i / V, s = i - tau * V, y = s / L, x = s - y * L;
+    const int base = tau * V;
+    float2 acc[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int mu = 0; mu < 7; ++mu) {
+      int j = i;
+      float2 ph = make_float2(1.f, 0.f);
+      float sn, cs;
+      if (mu == 1) {
+        j = base + y * L + (x + 1 == L ? 0 : x + 1);
+        __sincosf(__ldg(th32 + i).x, &sn, &cs);
+        ph = make_float2(cs, sn);
+      } else if (mu == 2) {
+        j = base + y * L + (x == 0 ? L - 1 : x - 1);
+        __sincosf(__ldg(th32 + j).x, &sn, &cs);
+        ph = make_float2(cs, -sn);
+      } else if (mu == 3) {
+        j = base + (y + 1 == L ? 0 : y + 1) * L + x;
+        __sincosf(__ldg(th32 + i).y, &sn, &cs);
+        ph = make_float2(cs, sn);
+      } else if (mu == 4) {
+        j = base + (y == 0 ? L - 1 : y - 1) * L + x;
+        __sincosf(__ldg(th32 + j).y, &sn, &cs);
+        ph = make_float2(cs, -sn);
+      } else if (mu == 5) {
+        const int tp = tau + 1 == N ? 0 : tau + 1;
+        j = tp * V + s;
+        ph = make_float2(tp == 0 ? -1.f : 1.f, 0.f);
+      } else if (mu == 6) {
+        const int tm = tau == 0 ? N - 1 : tau - 1;
+        j = tm * V + s;
+        ph = make_float2(tau == 0 ? -1.f : 1.f, 0.f);
+      }
+#pragma unroll
+      for (int cp2 = 0; cp2 < (CIN + 1) / 2; ++cp2) {
+        float2 hv[2];
+        if constexpr (CIN % 2 == 0) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(in + (size_t)j * CIN) + cp2);
+          hv[0] = make_float2(q.x, q.y);
+          hv[1] = make_float2(q.z, q.w);
+        } else {
+          hv[0] = __ldg(in + (size_t)j * CIN + 2 * cp2);
+          hv[1] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cp = 2 * cp2 + h;
+          if (cp >= CIN) break;
+          const float2 v = cmulf(ph, hv[h]);
+#pragma unroll
+          for (int c = 0; c < COUT; ++c) {
+            const float wv = W.w[mu][cp][c];
+            acc[c].x = fmaf(wv, v.x, acc[c].x);
+            acc[c].y = fmaf(wv, v.y, acc[c].y);
+          }
+        }
+      }
+    }
+    if constexpr (COUT % 2 == 0) {
+      float4* o = reinterpret_cast<float4*>(out + (size_t)i * COUT);
+#pragma unroll
+      for (int c2 = 0; c2 < COUT / 2; ++c2) o[c2] = make_float4(acc[2 * c2].x, acc[2 * c2].y, acc[2 * c2 + 1].x, acc[2 * c2 + 1].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) out[(size_t)i * COUT + c] = acc[c];
+    }
+  }
+}
+
+template <int CIN, int COUT>
+static cudaError_t layer_cw(const Geo& g, const float2* th32, const float* w, const float2* in, float2* out,
+                            int n, int nb, cudaStream_t s) {
+  NetLayerW<CIN, COUT> W;
+  for (int mu = 0; mu < 7; ++mu)
+    for (int c = 0; c < COUT; ++c)
+      for (int cp = 0; cp < CIN; ++cp) W.w[mu][cp][c] = w[(mu * COUT + c) * CIN + cp];
+  net_layer_cw_kernel<CIN, COUT><<<nb, 256, 0, s>>>(g, th32, W, in, out, n);
+  return cudaGetLastError();
+}
+
 // Weight gradient: G[mu][c][c'] = sum_x Re(conj(d(x, c)) (T_mu h)(x, c')), one
 // thread per weight entry over a chunk of sites; partials[chunk][entry].
 template <int CIN, int COUT>
@@ -281,6 +381,16 @@ cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, in
   else if (cin == 16 && cout == 1) net_layer_kernel<16, 1><<<nb, 256, 0, s>>>(g, th32, w, in, out, n);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+cudaError_t launch_net_layer_host_weights(const Geo& g, const float2* th32, const float* w, int cin, int cout,
+                                         const float2* in, float2* out, cudaStream_t s) {
+  const int n = g.V * g.Ntau;
+  const int nb = blocks_for(n, 256);
+  if (cin == 1 && cout == 16) return layer_cw<1, 16>(g, th32, w, in, out, n, nb, s);
+  if (cin == 16 && cout == 16) return layer_cw<16, 16>(g, th32, w, in, out, n, nb, s);
+  if (cin == 16 && cout == 1) return layer_cw<16, 1>(g, th32, w, in, out, n, nb, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
