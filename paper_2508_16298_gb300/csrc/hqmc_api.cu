@@ -60,7 +60,9 @@ struct hqmc_config {
   // tau-line preconditioner: coefficients from the pi-flux field, launch shape, workspace
   double pc_a = 0, pc_b = 0;
   LineCoef lc{};
-  LineLaunch ll64{}, ll32{};
+  LineLaunch ll64{}, ll32{};    // separate tau-line preconditioner (FP32 tile height tuned per config)
+  LineLaunch llu64{}, llu32{};  // fused update and preconditioner
+  size_t smem_per_sm = 0;
   double2* z64 = nullptr;
   float2* z32 = nullptr;
   double2* r64b = nullptr;  // second residual buffers of the fused preconditioned update
@@ -298,15 +300,19 @@ int precondition(hqmc_config* cfg, const C2<R>* r, C2<R>* z, const CgState* st, 
 template <class R>
 int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, const C2<R>* U, void* x,
                  bool x_double, bool pc, C2<R>* z, C2<R>* rb, int c, cudaStream_t s) {
-  const LineLaunch& ll = sizeof(R) == 8 ? cfg->ll64 : cfg->ll32;
   const bool fused = pc && rb != nullptr;
+  const LineLaunch& ll = fused ? (sizeof(R) == 8 ? cfg->llu64 : cfg->llu32) : (sizeof(R) == 8 ? cfg->ll64 : cfg->ll32);
+  const LineLaunch& lls = sizeof(R) == 8 ? cfg->ll64 : cfg->ll32;
   MdagmArgs<R> a = mdagm_args<R, MODE_CGDIR>(cfg);
   a.U = U;
   a.y = q;
   a.r = pc ? z : r;  // preconditioned CG: the direction is built from z = Otilde^{-1} r
   if (pc) {
+    // <r, z> partials: a body's first iteration reads those of the separate
+    // preconditioner that closed the previous body (or started the solve)
+    const LineLaunch& lz = (fused && c > 0) ? ll : lls;
     a.part_rz = cfg->part_rz;
-    a.n_part_rz = ll.gx * ll.gy;
+    a.n_part_rz = lz.gx * lz.gy;
   }
   a.pbuf[0] = pbuf[0];
   a.pbuf[1] = pbuf[1];
@@ -707,10 +713,11 @@ int line_coefficients(hqmc_config* cfg) {
   cfg->pc_a = a;
   cfg->pc_b = b;
   cfg->lc = LineCoef{rho, std::pow(rho, W + 1), rho / b, W};
-  if (line_smem_bytes(8, W) > kMaxLineSmem || line_update_smem_bytes(8, W) > kMaxLineSmem)
+  if (line_smem_bytes(8, W, cfg->ll64.chunk) > kMaxLineSmem || line_update_smem_bytes(8, W) > kMaxLineSmem)
     return fail(cfg, HQMC_EUNSUPPORTED, "tau-line preconditioner width W=%d too large", W);
-  CK(prepare_line_precond<double>(W));
-  CK(prepare_line_precond<float>(W));
+  cfg->ll32 = line_launch(g, line_chunk_candidates(g, 4, W, cfg->num_sms, cfg->smem_per_sm).front());
+  CK(prepare_line_precond<double>(W, cfg->ll64.chunk));
+  CK(prepare_line_precond<float>(W, cfg->ll32.chunk));
   CK(prepare_line_update<double>(W));
   CK(prepare_line_update<float>(W));
   CK(cudaDeviceSynchronize());
@@ -781,10 +788,11 @@ int tune_pc_update(hqmc_config* cfg) {
   C2<R>* pb[2] = {dbl ? (C2<R>*)cfg->p64[0] : (C2<R>*)cfg->p32[0], dbl ? (C2<R>*)cfg->p64[1] : (C2<R>*)cfg->p32[1]};
   for (C2<R>* v : {r, rb, q, z, x, pb[0], pb[1]}) CK(cudaMemset(v, 0, sizeof(C2<R>) * cfg->n));
   const LineLaunch& ll = dbl ? cfg->ll64 : cfg->ll32;
+  const LineLaunch& llu = dbl ? cfg->llu64 : cfg->llu32;
   const int npq = fused_shape<R>(cfg).grid;
   auto fused = [&]() {
     LineUpdArgs<R> u{x, r, rb, pb[0], pb[1], q, z, cfg->part_mdagm, npq, cfg->part_ew, cfg->part_rz, cfg->st};
-    return launch_line_update<R>(cfg->g, cfg->lc, ll, u, 0);
+    return launch_line_update<R>(cfg->g, cfg->lc, llu, u, 0);
   };
   auto separate = [&]() {
     cudaError_t e = launch_cg_update<R>(cfg->n, cfg->ew_grid, x, dbl ? 1 : 0, r, pb, q, cfg->part_mdagm, npq,
@@ -815,6 +823,49 @@ int tune_pc_update(hqmc_config* cfg) {
   CK(err);
   (dbl ? cfg->fuse_pc64 : cfg->fuse_pc32) = us[0] <= us[1] ? 1 : 0;
   CK(cudaMemset(cfg->st, 0, sizeof(CgState)));
+  return HQMC_OK;
+}
+
+// Tile height of the separate FP32 preconditioner: times the candidate heights
+// (line_chunk_candidates: the first few, and the fixed default) on zero operands
+// and keeps the fastest.  The state stays "done = running"; no partials are read.
+int tune_line_chunk(hqmc_config* cfg) {
+  std::vector<int> cand = line_chunk_candidates(cfg->g, 4, cfg->lc.W, cfg->num_sms, cfg->smem_per_sm);
+  if (cand.size() > 4) cand.erase(cand.begin() + 3, cand.end() - 1);
+  CK(cudaMemset(cfg->st, 0, sizeof(CgState)));
+  CK(cudaMemset(cfg->r32, 0, sizeof(float2) * cfg->n));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int chosen = cfg->ll32.chunk;
+  cudaError_t err = cudaSuccess;
+  for (int tc : cand) {
+    const LineLaunch ll = line_launch(cfg->g, tc);
+    err = prepare_line_precond<float>(cfg->lc.W, tc);
+    if (err != cudaSuccess) break;
+    auto go = [&]() {
+      return launch_line_precond<float>(cfg->g, cfg->lc, ll, cfg->r32, cfg->z32, cfg->part_rz, cfg->st, 0);
+    };
+    err = go();
+    const int reps = 5;
+    if (err == cudaSuccess) err = cudaEventRecord(e0, 0);
+    for (int k = 0; k < reps && err == cudaSuccess; ++k) err = go();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err != cudaSuccess) break;
+    cfg->launches += reps + 1;
+    if (ms < best) {
+      best = ms;
+      chosen = tc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(err);
+  cfg->ll32 = line_launch(cfg->g, chosen);
   return HQMC_OK;
 }
 
@@ -884,6 +935,7 @@ int autotune(hqmc_config* cfg) {
     }
   }
   RET(tune_pc_update<double>(cfg));
+  RET(tune_line_chunk(cfg));
   RET(tune_pc_update<float>(cfg));
   CK(cudaDeviceSynchronize());
   return HQMC_OK;
@@ -1038,6 +1090,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     pick_block(8, &cfg->slb64);
     pick_block(4, &cfg->slb32);
     cfg->num_sms = prop.multiProcessorCount;
+    cfg->smem_per_sm = prop.sharedMemPerMultiprocessor;
     // tau-walking FP32 kernel: the smallest strip height whose block fits, one CTA per SM
     cfg->slw32 = cfg->sl32;
     cfg->slw32.walk = 0;
@@ -1119,9 +1172,14 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     // partials of the fused kernel: room for any cluster size (grid <= Ntau + 7)
     if ((rc = dalloc(cfg, &cfg->part_mdagm, 2 * ((size_t)p->Ntau + 8)))) break;
     if ((rc = dalloc(cfg, &cfg->part_resid, 2 * ((size_t)p->Ntau + 8)))) break;
-    cfg->ll64 = line_launch(cfg->g, 8);
-    cfg->ll32 = line_launch(cfg->g, 4);
-    cfg->n_part_ew = std::max(cfg->ew_grid, std::max(cfg->ll64.gx * cfg->ll64.gy, cfg->ll32.gx * cfg->ll32.gy));
+    // preconditioner tiles: the FP32 height is set with the coefficients; partials
+    // have room for the smallest height any config picks (16 slices)
+    cfg->ll64 = line_update_launch(cfg->g, 8);
+    cfg->ll32 = line_update_launch(cfg->g, 4);
+    cfg->llu64 = line_update_launch(cfg->g, 8);
+    cfg->llu32 = line_update_launch(cfg->g, 4);
+    const LineLaunch l16 = line_launch(cfg->g, 16);
+    cfg->n_part_ew = std::max(cfg->ew_grid, std::max(cfg->llu64.gx * cfg->llu64.gy, cfg->llu32.gx * cfg->llu32.gy));
     if ((rc = dalloc(cfg, &cfg->part_ew, (size_t)cfg->n_part_ew))) break;
     if ((rc = dalloc(cfg, &cfg->part_act, 4 * (size_t)cfg->act_grid))) break;
     if ((rc = dalloc(cfg, &cfg->z64, n))) break;
@@ -1129,7 +1187,7 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     if ((rc = dalloc(cfg, &cfg->r64b, n))) break;
     if ((rc = dalloc(cfg, &cfg->r32b, n))) break;
     if ((rc = dalloc(cfg, &cfg->part_rz,
-                     (size_t)std::max(cfg->ll64.gx * cfg->ll64.gy, cfg->ll32.gx * cfg->ll32.gy)))) break;
+                     (size_t)std::max(l16.gx * l16.gy, cfg->llu32.gx * cfg->llu32.gy)))) break;
     if ((rc = dalloc(cfg, &cfg->terms, 8))) break;
     if ((rc = dalloc(cfg, &cfg->report, 2))) break;
     if ((rc = dalloc(cfg, &cfg->st, 1))) break;
@@ -1500,6 +1558,7 @@ struct hqmc_batch {
   int4* d_ltiles = nullptr;                 // (chain, bx, by) tiles of the batched preconditioner
   int nltiles = 0;
   int maxW = 0;
+  int maxtc = 0;  // tallest preconditioner tile of the chains (shared memory of the batched launch)
   void* h_stage = nullptr;  // pinned staging of the descriptor arrays
   size_t stage_bytes = 0;
   cudaStream_t cap = nullptr;
@@ -1576,7 +1635,8 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
       a.part_rz = cfg->part_rz;
       a.n_part_rz = cfg->ll64.gx * cfg->ll64.gy;
     }
-    ld[c] = LineBatchDesc<double>{cfg->g, cfg->lc, cfg->r64, cfg->z64, cfg->part_rz, cfg->st, cfg->ll64.gx};
+    ld[c] = LineBatchDesc<double>{cfg->g,        cfg->lc,  cfg->r64,         cfg->z64,
+                                  cfg->part_rz, cfg->st, cfg->ll64.gx, cfg->ll64.chunk};
     a.pbuf[0] = cfg->p64[0];
     a.pbuf[1] = cfg->p64[1];
     a.part_in = cfg->part_ew;
@@ -1617,11 +1677,11 @@ int batch_body(hqmc_batch* b, cudaStream_t s) {
   for (int it = 0; it < kBodyIters64; ++it) {
     BCK((launch_mdagm_batch<double, MODE_CGDIR>(b->d_cgdir, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
     BCK(launch_cg_update_batch(b->d_upd, b->d_ublocks, b->d_unblocks, b->total_ublocks, s));
-    if (pc) BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, s));
+    if (pc) BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, b->maxtc, s));
   }
   BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_loop, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
   BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_RESTART, 0.0, 0, GATE_REC, s));
-  if (pc) BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, s));
+  if (pc) BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, b->maxtc, s));
   return HQMC_OK;
 }
 
@@ -1675,7 +1735,7 @@ int batch_solve(hqmc_batch* b, const double2* const* phi, double2* const* x, dou
   BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_START, tol, maxit, GATE_ALWAYS, s));
   b->launches += 2;
   if (b->solver == HQMC_SOLVER_PCG64) {
-    BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, s));
+    BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, b->maxtc, s));
     b->launches += 1;
   }
   if ((rc = batch_graph(b)) != HQMC_OK) return rc;
@@ -1763,11 +1823,12 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
     for (int c = 0; c < nchains; ++c) {
       const LineLaunch& ll = b->cfgs[c]->ll64;
       b->maxW = std::max(b->maxW, b->cfgs[c]->lc.W);
+      b->maxtc = std::max(b->maxtc, ll.chunk);
       for (int by = 0; by < ll.gy; ++by)
         for (int bx = 0; bx < ll.gx; ++bx) ltiles.push_back(make_int4(c, bx, by, 0));
     }
     b->nltiles = (int)ltiles.size();
-    if (prepare_line_precond_batch(b->maxW) != cudaSuccess) {
+    if (prepare_line_precond_batch(b->maxW, b->maxtc) != cudaSuccess) {
       cudaGetLastError();
       rc = bfail(b, HQMC_EUNSUPPORTED, "batched preconditioner does not fit");
       break;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "common.cuh"
 
@@ -170,10 +171,14 @@ struct LineLaunch {
   int block;  // threads per block
   int gx, gy; // grid: site tiles x slice tiles (gx * gy partials of <r, z>)
 };
-LineLaunch line_launch(const Geo& g, int real_bytes);
-size_t line_smem_bytes(int real_bytes, int W);
+// Separate preconditioner kernel: tiles of `chunk` slices.
+LineLaunch line_launch(const Geo& g, int chunk);
+// Fused update-and-preconditioner kernel: its fixed tile height.
+LineLaunch line_update_launch(const Geo& g, int real_bytes);
+size_t line_smem_bytes(int real_bytes, int W, int tc);
+std::vector<int> line_chunk_candidates(const Geo& g, int real_bytes, int W, int num_sms, size_t smem_per_sm);
 template <class R>
-cudaError_t prepare_line_precond(int W);
+cudaError_t prepare_line_precond(int W, int tc);
 // z = Otilde^{-1} r and partials of <r, z>; gated on st->done == CG_RUNNING unless st is NULL.
 template <class R>
 cudaError_t launch_line_precond(const Geo& g, const LineCoef& lc, const LineLaunch& ll, const C2<R>* r, C2<R>* z,
@@ -190,10 +195,11 @@ struct LineBatchDesc {
   double* part;
   const CgState* st;
   int gx;  // the chain's own tile grid width (partial index by * gx + bx)
+  int tc;  // slices per tile, as in the chain's own launch
 };
 cudaError_t launch_line_precond_batch(const LineBatchDesc<double>* descs, const int4* tiles, int ntiles, int W,
-                                     cudaStream_t s);
-cudaError_t prepare_line_precond_batch(int W);
+                                     int tc, cudaStream_t s);
+cudaError_t prepare_line_precond_batch(int W, int tc);
 
 // Preconditioned CG: the vector update fused with the preconditioner (precond.cu).
 template <class R>

@@ -10,20 +10,29 @@
 // applied to every site's tau line independently.
 //
 // One kernel does both passes on a tile of 32 sites (one warp width, so a
-// slice row of the tile is 256 B contiguous in FP32) by TC consecutive slices:
-//   1. the block loads u on slices [t0 - W, t1 + W] of its sites into shared
-//      memory, every load independent (coalesced rows);
-//   2. forward:  x_tau = sum_m rho^m u~_{tau-m} for tau in [t0, t1 + W], each
+// slice row of the tile is 256 B contiguous in FP32) by tc consecutive slices
+// (tc chosen per config so that, where possible, all tiles are resident at once):
+//   1. forward:  x_tau = sum_m rho^m u~_{tau-m} for tau in [t0, t1 + W], each
 //      warp a contiguous sub-range, as a sliding-window recursion
 //      x_tau = rho x_{tau-1} + u~_tau - rho^{W+1} u~_{tau-W-1} started W slices
-//      before its sub-range, into a second shared buffer;
-//   3. backward: y_tau = sum_m rho^m x~_{tau+m} for tau in [t0, t1), the same
-//      recursion in descending tau; z = (rho/b) y is written once, with the
-//      partial sums of Re <r, z> for pCG (r = u is still in shared memory).
+//      before its sub-range.  u is read straight from global memory, one
+//      coalesced row per warp load: a stream for the entering row and one for
+//      the leaving row W+1 slices behind (an L1 hit), each keeping its slice
+//      index and the sign of its wraps.  x goes to shared memory, the tile's
+//      only buffer, so several tiles share an SM;
+//   2. backward: y_tau = sum_m rho^m x~_{tau+m} for tau in [t0, t1), the same
+//      recursion in descending tau; z = (rho/b) y is written once.
+// pCG also needs Re <r, z>.  With z = (rho/b) F^dagger F r it equals
+// (rho/b) ||F r||^2 = (rho/b) sum_tau |x_tau|^2, and the tiles' own slices
+// [t0, t1) partition the line, so the forward pass sums |x_tau|^2 over them: no
+// second read of r, and the sum is positive by construction.
 // u~ and x~ are the antiperiodic extensions (a sign flip per wrap); the halo
 // rows are read again by the neighbouring tile, mostly from L2, so HBM sees
 // one read of r and one write of z.
 #include "kernels.h"
+
+#include <algorithm>
+#include <vector>
 
 namespace hqmc {
 
@@ -54,92 +63,146 @@ __device__ __forceinline__ bool line_gate(const CgState* st) {
 constexpr int kLineSites = 32;  // sites per tile (one warp width)
 constexpr int kLineWarps = 8;   // warps per block: independent recursion chains hide the FMA latency
 
-// Slices per tile: FP32 128, FP64 64 (shared memory: both buffers of the tile).
+// Slices per tile of the fused update-and-preconditioner kernel, and the
+// separate kernel's default where no height fits all tiles at once: FP32 128, FP64 64.
 template <class R> constexpr int line_tile_slices() { return sizeof(R) == 4 ? 128 : 64; }
 
-size_t line_smem_bytes(int real_bytes, int W) {
-  const int tc = real_bytes == 4 ? line_tile_slices<float>() : line_tile_slices<double>();
-  return (size_t)((tc + 2 * W + 1) + (tc + W + 1)) * kLineSites * 2 * real_bytes;
+// Shared memory of a tile of tc slices: x on slices t0 .. t1 + W.
+size_t line_smem_bytes(int real_bytes, int W, int tc) { return (size_t)(tc + W + 1) * kLineSites * 2 * real_bytes; }
+
+// Candidate heights of the separate kernel's tiles (FP32): tc = ceil(N / k),
+// 16 <= tc <= 256, with at least four tiles resident per SM and all tiles
+// resident at once (one round), ordered by the recursion work per SM (each
+// warp restarts both recursions W slices early: a fixed cost per tile).  The
+// first is the default; the autotuner times them.  FP64 keeps 64 slices.
+std::vector<int> line_chunk_candidates(const Geo& g, int real_bytes, int W, int num_sms, size_t smem_per_sm) {
+  std::vector<std::pair<double, int>> c;
+  if (real_bytes == 4) {
+    const long gx = (g.V + kLineSites - 1) / kLineSites;
+    int last = 0;
+    for (int k = 1; k <= g.Ntau; ++k) {
+      const int tc = (g.Ntau + k - 1) / k;
+      if (tc == last) continue;
+      last = tc;
+      if (tc > 256) continue;
+      if (tc < 16) break;
+      const long per_sm = std::min<long>(2048 / (kLineSites * kLineWarps),
+                                         (long)(smem_per_sm / (line_smem_bytes(real_bytes, W, tc) + 1024)));
+      const long tiles = gx * ((g.Ntau + tc - 1) / tc);
+      if (per_sm < 4 || tiles > per_sm * num_sms) continue;
+      const double work = (double)((tiles + num_sms - 1) / num_sms) * (2.0 * tc + W + 1 + 2.0 * kLineWarps * W);
+      c.push_back({work, tc});
+    }
+  }
+  std::sort(c.begin(), c.end());
+  std::vector<int> out;
+  for (const auto& e : c) out.push_back(e.second);
+  const int dflt = real_bytes == 4 ? line_tile_slices<float>() : line_tile_slices<double>();
+  if (std::find(out.begin(), out.end(), dflt) == out.end()) out.push_back(dflt);
+  return out;
 }
+
+namespace {
+
+// Rows of u for consecutive slices j, j+1, ... of one site: the element, and
+// the sign of the antiperiodic extension, (-1)^(wraps of j).  WRAP = false: the
+// caller guarantees every slice it reads lies in [0, N) (no index or sign work).
+template <class R, bool WRAP>
+struct LineStream {
+  const C2<R>* p;
+  int m;
+  R sgn;
+  __device__ __forceinline__ void start(const C2<R>* u, int j, int N, int V, int s) {
+    if constexpr (WRAP) {
+      const LinePos q = line_pos(j, N);
+      m = q.m;
+      sgn = (R)q.sgn;
+      p = u + (size_t)m * V + s;
+    } else {
+      p = u + (size_t)j * V + s;
+    }
+  }
+  __device__ __forceinline__ C2<R> get() const {
+    const C2<R> v = __ldg(p);
+    if constexpr (WRAP) return mk(sgn * v.x, sgn * v.y);
+    return v;
+  }
+  __device__ __forceinline__ void next(int N, int V) {
+    p += V;
+    if constexpr (WRAP) {
+      if (++m == N) {
+        m = 0;
+        p -= (size_t)N * V;
+        sgn = -sgn;
+      }
+    }
+  }
+};
+
+// Forward pass of one warp: x rows [a, b) (row i is slice t0 + i) into X, and
+// the sum of |x|^2 over the rows below nt (the tile's own slices).
+template <class R, bool WRAP>
+__device__ __forceinline__ void line_forward(const C2<R>* __restrict__ u, C2<R>* __restrict__ X, int a, int b,
+                                             int t0, int nt, int N, int V, int W, int site, int lane, R rho, R rw,
+                                             R& xx) {
+  using T = C2<R>;
+  LineStream<R, WRAP> in, out;
+  in.start(u, t0 + a - W, N, V, site);  // slices t0+a-W .. t0+a for the first window
+  out = in;
+  T acc = mk(R(0), R(0));
+#pragma unroll 4
+  for (int m = 0; m <= W; ++m) {
+    acc = caxpy(in.get(), rho, acc);
+    in.next(N, V);
+  }
+  X[a * kLineSites + lane] = acc;
+  if (a < nt) xx += cdot_re_own(acc, acc);
+#pragma unroll 4
+  for (int i = a + 1; i < b; ++i) {
+    acc = caxpy(caxpy(in.get(), rho, acc), -rw, out.get());  // enters slice t0+i, leaves t0+i-W-1
+    in.next(N, V);
+    out.next(N, V);
+    X[i * kLineSites + lane] = acc;
+    if (i < nt) xx += cdot_re_own(acc, acc);
+  }
+}
+
+}  // namespace
 
 // One tile (site block bx, slice block by of a gx-wide grid) of z = Otilde^{-1} u
 // with its partial of <u, z> in part[by * gx + bx].
 template <class R>
-__device__ __forceinline__ void line_precond_tile(const Geo& g, const LineCoef& lc, const C2<R>* __restrict__ u,
-                                                  C2<R>* __restrict__ z, double* __restrict__ part, int bx, int by,
-                                                  int gx) {
+__device__ __forceinline__ void line_precond_tile(const Geo& g, const LineCoef& lc, int tc,
+                                                  const C2<R>* __restrict__ u, C2<R>* __restrict__ z,
+                                                  double* __restrict__ part, int bx, int by, int gx) {
   using T = C2<R>;
-  constexpr int TC = line_tile_slices<R>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const int N = g.Ntau, V = g.V, W = lc.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s0 = bx * kLineSites, s = s0 + lane;
   const bool site_ok = s < V;
-  const int t0 = by * TC, t1 = min(N, t0 + TC), nt = t1 - t0;
-  const int nu = nt + 2 * W + 1;  // rows of u: slices t0 - W .. t1 + W
-  const int nx = nt + W + 1;      // rows of x: slices t0 .. t1 + W
-  T* U = reinterpret_cast<T*>(smem_raw);
-  T* X = U + (size_t)(TC + 2 * W + 1) * kLineSites;
-
-  // 1. u rows into shared memory by asynchronous copies (all in flight at once),
-  //    then the sign of the antiperiodic extension on the rows that wrapped
-  LinePos p = line_pos(t0 - W + warp, N);  // stepped by kLineWarps rows below
-  for (int row = warp; row < nu; row += kLineWarps) {
-    T* dst = U + row * kLineSites + lane;
-    if (site_ok) {
-      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-      const T* src = u + (size_t)p.m * V + s;
-      if constexpr (sizeof(T) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
-      else
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
-    } else {
-      *dst = mk(R(0), R(0));
-    }
-    p.m += kLineWarps;
-    while (p.m >= N) {
-      p.m -= N;
-      p.sgn = -p.sgn;
-    }
-  }
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-  {  // rows before slice 0 or past slice N-1 carry the sign of their wraps
-    LinePos q = line_pos(t0 - W + warp, N);
-    for (int row = warp; row < nu; row += kLineWarps) {
-      if (q.sgn < 0.f) {
-        T* e = U + row * kLineSites + lane;
-        *e = mk(-e->x, -e->y);
-      }
-      q.m += kLineWarps;
-      while (q.m >= N) {
-        q.m -= N;
-        q.sgn = -q.sgn;
-      }
-    }
-  }
-  __syncthreads();
+  const int sr = site_ok ? s : V - 1;  // lanes past the last site read a valid one and store nothing
+  const int t0 = by * tc, t1 = min(N, t0 + tc), nt = t1 - t0;
+  const int nx = nt + W + 1;  // rows of x: slices t0 .. t1 + W
+  T* X = reinterpret_cast<T*>(smem_raw);
   const R rho = (R)lc.rho, rw = (R)lc.rhoW1, sc = (R)lc.scale;
-  // 2. forward: rows of x split over the warps; U row of slice tau is tau - t0 + W
+  R xx = 0;  // sum of |x_tau|^2 over this thread's own slices (FP32: in float, cdot_re_own)
+
+  // 1. forward: rows of x split over the warps; x row i is slice t0 + i
   {
     const int per = (nx + kLineWarps - 1) / kLineWarps;
-    const int a = warp * per, b = min(nx, a + per);  // x rows [a, b): slices t0 + a ..
+    const int a = warp * per, b = min(nx, a + per);  // x rows [a, b)
     if (a < b) {
-      T acc = mk(R(0), R(0));
-#pragma unroll 4
-      for (int m = 0; m <= W; ++m) acc = caxpy(U[(a + m) * kLineSites + lane], rho, acc);  // slices t0+a-W .. t0+a
-      X[a * kLineSites + lane] = acc;
-#pragma unroll 4
-      for (int i = a + 1; i < b; ++i) {
-        acc = caxpy(caxpy(U[(i + W) * kLineSites + lane], rho, acc), -rw, U[(i - 1) * kLineSites + lane]);
-        X[i * kLineSites + lane] = acc;
-      }
+      // slices read: t0 + a - W .. t0 + b - 1
+      if (t0 + a - W >= 0 && t0 + b - 1 < N)
+        line_forward<R, false>(u, X, a, b, t0, nt, N, V, W, sr, lane, rho, rw, xx);
+      else
+        line_forward<R, true>(u, X, a, b, t0, nt, N, V, W, sr, lane, rho, rw, xx);
     }
   }
   __syncthreads();
-  // 3. backward over the tile's own slices, split over the warps
-  R dot = 0;  // FP32: the thread's terms in float (cdot_re_own)
+  // 2. backward over the tile's own slices, split over the warps
   {
     const int per = (nt + kLineWarps - 1) / kLineWarps;
     const int a = warp * per, b = min(nt, a + per);  // output rows [a, b)
@@ -148,30 +211,26 @@ __device__ __forceinline__ void line_precond_tile(const Geo& g, const LineCoef& 
 #pragma unroll 4
       for (int m = W; m >= 0; --m) acc = caxpy(X[(b - 1 + m) * kLineSites + lane], rho, acc);
       for (int i = b - 1;; --i) {
-        const T zv = cscale(sc, acc);
-        if (site_ok) {
-          z[(t0 + i) * V + s] = zv;
-          dot += cdot_re_own(U[(i + W) * kLineSites + lane], zv);
-        }
+        if (site_ok) z[(size_t)(t0 + i) * V + s] = cscale(sc, acc);
         if (i == a) break;
         acc = caxpy(caxpy(X[(i - 1) * kLineSites + lane], rho, acc), -rw, X[(i + W) * kLineSites + lane]);
       }
     }
   }
   if (part) {
-    const double tot = block_sum((double)dot, red);
+    const double tot = block_sum(site_ok ? (double)sc * (double)xx : 0.0, red);
     if (threadIdx.x == 0) part[by * gx + bx] = tot;
   }
 }
 
 template <class R>
-__global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_kernel(Geo g, LineCoef lc,
+__global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_kernel(Geo g, LineCoef lc, int tc,
                                                                              const C2<R>* __restrict__ u,
                                                                              C2<R>* __restrict__ z,
                                                                              double* __restrict__ part,
                                                                              const CgState* st) {
   if (!line_gate(st)) return;  // uniform over the grid
-  line_precond_tile<R>(g, lc, u, z, part, blockIdx.x, blockIdx.y, gridDim.x);
+  line_precond_tile<R>(g, lc, tc, u, z, part, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // Many chains in one launch: block b runs tile tiles[b] = (chain, bx, by) with
@@ -183,7 +242,7 @@ __global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_batch_ker
   const int4 t = tiles[blockIdx.x];
   const LineBatchDesc<R> d = descs[t.x];
   if (!line_gate(d.st)) return;  // uniform over the block
-  line_precond_tile<R>(d.g, d.lc, d.u, d.z, d.part, t.y, t.z, d.gx);
+  line_precond_tile<R>(d.g, d.lc, d.tc, d.u, d.z, d.part, t.y, t.z, d.gx);
 }
 
 // Preconditioned CG, fused update and preconditioner (one launch per iteration
@@ -397,38 +456,43 @@ template cudaError_t launch_line_update<double>(const Geo&, const LineCoef&, con
 template cudaError_t launch_line_update<float>(const Geo&, const LineCoef&, const LineLaunch&,
                                                const LineUpdArgs<float>&, cudaStream_t);
 
-LineLaunch line_launch(const Geo& g, int real_bytes) {
+LineLaunch line_launch(const Geo& g, int chunk) {
   LineLaunch ll;
-  ll.chunk = real_bytes == 4 ? line_tile_slices<float>() : line_tile_slices<double>();
+  ll.chunk = chunk;
   ll.block = kLineSites * kLineWarps;
   ll.gx = (g.V + kLineSites - 1) / kLineSites;
   ll.gy = (g.Ntau + ll.chunk - 1) / ll.chunk;
   return ll;
 }
 
-template <class R>
-cudaError_t prepare_line_precond(int W) {
-  return raise_smem_limit(line_precond_kernel<R>, line_smem_bytes(sizeof(R), W));
+LineLaunch line_update_launch(const Geo& g, int real_bytes) {
+  return line_launch(g, real_bytes == 4 ? line_tile_slices<float>() : line_tile_slices<double>());
 }
-template cudaError_t prepare_line_precond<double>(int);
-template cudaError_t prepare_line_precond<float>(int);
+
+template <class R>
+cudaError_t prepare_line_precond(int W, int tc) {
+  return raise_smem_limit(line_precond_kernel<R>, line_smem_bytes(sizeof(R), W, tc));
+}
+template cudaError_t prepare_line_precond<double>(int, int);
+template cudaError_t prepare_line_precond<float>(int, int);
 
 template <class R>
 cudaError_t launch_line_precond(const Geo& g, const LineCoef& lc, const LineLaunch& ll, const C2<R>* r, C2<R>* z,
                                 double* part_rz, const CgState* st, cudaStream_t s) {
   const dim3 grid(ll.gx, ll.gy);
-  line_precond_kernel<R><<<grid, ll.block, line_smem_bytes(sizeof(R), lc.W), s>>>(g, lc, r, z, part_rz, st);
+  line_precond_kernel<R><<<grid, ll.block, line_smem_bytes(sizeof(R), lc.W, ll.chunk), s>>>(g, lc, ll.chunk, r, z,
+                                                                                            part_rz, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_line_precond_batch(const LineBatchDesc<double>* descs, const int4* tiles, int ntiles, int W,
-                                     cudaStream_t s) {
-  line_precond_batch_kernel<double><<<ntiles, kLineSites * kLineWarps, line_smem_bytes(8, W), s>>>(descs, tiles);
+                                     int tc, cudaStream_t s) {
+  line_precond_batch_kernel<double><<<ntiles, kLineSites * kLineWarps, line_smem_bytes(8, W, tc), s>>>(descs, tiles);
   return cudaGetLastError();
 }
 
-cudaError_t prepare_line_precond_batch(int W) {
-  return raise_smem_limit(line_precond_batch_kernel<double>, line_smem_bytes(8, W));
+cudaError_t prepare_line_precond_batch(int W, int tc) {
+  return raise_smem_limit(line_precond_batch_kernel<double>, line_smem_bytes(8, W, tc));
 }
 
 template cudaError_t launch_line_precond<double>(const Geo&, const LineCoef&, const LineLaunch&, const double2*,
