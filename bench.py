@@ -467,7 +467,8 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
                     "bytes_per_site": MDAGM_BYTES_PER_SITE[wl["solver"]], "sites_per_launch": sites,
                     "tflops_algorithmic": achieved_tflops, "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms,
                     "cg_update_avg_us": 1e3 * up_ms / max(n_up, 1),
-                    "precond_avg_us": 1e3 * pc_ms / n_pc if n_pc else None}
+                    "precond_avg_us": 1e3 * pc_ms / n_pc if n_pc else None,
+                    "precond_shape": hqmc.get_precond_shape(cfg, hqmc.FP32)}
     else:
         roofline = {"kernel": kname, "bound": "alu", "achieved": achieved_tflops,
                     "peak": fp64_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_tflops,
@@ -681,6 +682,7 @@ def run_profile_case(wl):
         hqmc.trajectory(cfg, theta, seed=wl["seed"], traj_counter=0, nsteps=2, dt=wl["dt"], tol=wl["tol"],
                         solver=wl["solver"])
         torch.cuda.synchronize()
+        print("preconditioner shape (FP32):", hqmc.get_precond_shape(cfg, hqmc.FP32), file=sys.stderr)
         if net is not None:
             hqmc.set_preconditioner(cfg, None)
             net.close()

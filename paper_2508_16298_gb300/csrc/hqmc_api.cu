@@ -1303,6 +1303,14 @@ int hqmc_get_precond(const hqmc_config* cfg, double* a, double* b, double* rho, 
   return HQMC_OK;
 }
 
+int hqmc_get_precond_shape(const hqmc_config* cfg, int precision, int* tile_slices, int* fused) {
+  if (!cfg || (precision != HQMC_FP64 && precision != HQMC_FP32)) return HQMC_EINVAL;
+  const bool dbl = precision == HQMC_FP64;
+  if (tile_slices) *tile_slices = dbl ? cfg->ll64.chunk : cfg->ll32.chunk;
+  if (fused) *fused = (dbl ? cfg->fuse_pc64 : cfg->fuse_pc32) && cfg->p.variant != 1 ? 1 : 0;
+  return HQMC_OK;
+}
+
 int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* x, double tol, int maxit, int solver,
                   hqmc_solve_info* info, void* stream) {
   if (!cfg) return HQMC_EINVAL;

@@ -140,7 +140,10 @@ struct LineStream {
 };
 
 // Forward pass of one warp: x rows [a, b) (row i is slice t0 + i) into X, and
-// the sum of |x|^2 over the rows below nt (the tile's own slices).
+// the sum of |x|^2 over the rows below nt (the tile's own slices).  Loads are
+// issued in batches of kLineBatch rows per stream ahead of the dependent FMAs.
+constexpr int kLineBatch = 8;
+
 template <class R, bool WRAP>
 __device__ __forceinline__ void line_forward(const C2<R>* __restrict__ u, C2<R>* __restrict__ X, int a, int b,
                                              int t0, int nt, int N, int V, int W, int site, int lane, R rho, R rw,
@@ -150,16 +153,42 @@ __device__ __forceinline__ void line_forward(const C2<R>* __restrict__ u, C2<R>*
   in.start(u, t0 + a - W, N, V, site);  // slices t0+a-W .. t0+a for the first window
   out = in;
   T acc = mk(R(0), R(0));
-#pragma unroll 4
-  for (int m = 0; m <= W; ++m) {
+  int m = 0;
+  for (; m + kLineBatch <= W + 1; m += kLineBatch) {
+    T v[kLineBatch];
+#pragma unroll
+    for (int k = 0; k < kLineBatch; ++k) {
+      v[k] = in.get();
+      in.next(N, V);
+    }
+#pragma unroll
+    for (int k = 0; k < kLineBatch; ++k) acc = caxpy(v[k], rho, acc);
+  }
+  for (; m <= W; ++m) {
     acc = caxpy(in.get(), rho, acc);
     in.next(N, V);
   }
   X[a * kLineSites + lane] = acc;
   if (a < nt) xx += cdot_re_own(acc, acc);
-#pragma unroll 4
-  for (int i = a + 1; i < b; ++i) {
-    acc = caxpy(caxpy(in.get(), rho, acc), -rw, out.get());  // enters slice t0+i, leaves t0+i-W-1
+  int i = a + 1;
+  for (; i + kLineBatch <= b; i += kLineBatch) {
+    T vi[kLineBatch], vo[kLineBatch];
+#pragma unroll
+    for (int k = 0; k < kLineBatch; ++k) {
+      vi[k] = in.get();
+      vo[k] = out.get();
+      in.next(N, V);
+      out.next(N, V);
+    }
+#pragma unroll
+    for (int k = 0; k < kLineBatch; ++k) {
+      acc = caxpy(caxpy(vi[k], rho, acc), -rw, vo[k]);  // enters slice t0+i+k, leaves t0+i+k-W-1
+      X[(i + k) * kLineSites + lane] = acc;
+      if (i + k < nt) xx += cdot_re_own(acc, acc);
+    }
+  }
+  for (; i < b; ++i) {
+    acc = caxpy(caxpy(in.get(), rho, acc), -rw, out.get());
     in.next(N, V);
     out.next(N, V);
     X[i * kLineSites + lane] = acc;
@@ -188,6 +217,21 @@ __device__ __forceinline__ void line_precond_tile(const Geo& g, const LineCoef& 
   T* X = reinterpret_cast<T*>(smem_raw);
   const R rho = (R)lc.rho, rw = (R)lc.rhoW1, sc = (R)lc.scale;
   R xx = 0;  // sum of |x_tau|^2 over this thread's own slices (FP32: in float, cdot_re_own)
+
+  // The tile reads slices t0 - W .. t1 + W of its sites: request all of them
+  // into L2 at once (128-byte lines), so that the recursions' dependent loads
+  // meet L2 latency rather than DRAM latency.
+  {
+    const int lines_per_row = (min(kLineSites, V - s0) * (int)sizeof(T) + 127) / 128;
+    const int nrow = nt + 2 * W + 1;
+    for (int k = threadIdx.x; k < nrow * lines_per_row; k += blockDim.x) {
+      const int row = k / lines_per_row, l = k - row * lines_per_row;
+      const int j = t0 - W + row;
+      const int m = ((unsigned)j < (unsigned)N) ? j : line_pos(j, N).m;
+      const char* pl = reinterpret_cast<const char*>(u + (size_t)m * V + s0) + 128 * l;
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pl));
+    }
+  }
 
   // 1. forward: rows of x split over the warps; x row i is slice t0 + i
   {

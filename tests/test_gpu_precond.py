@@ -50,6 +50,24 @@ def test_coefficients_and_apply(hq, L, N):
     assert z32.dtype == np.complex64 and rel(z32, opc.apply(c, r.astype(np.complex64).astype(np.complex128))) < 1e-5
 
 
+@pytest.mark.parametrize("L,N", [(24, 240), (66, 660)])
+def test_tile_height_and_autotuned_parity(hq, L, N):
+    """The separate kernel's FP32 tile height is chosen per config (all tiles
+    resident at once where a height allows it; timed by the autotuner when it
+    runs); the result does not depend on it.  FP64 tiles keep 64 slices."""
+    lat = oracle.Lattice(L, N)
+    c = opc.coefficients(lat)
+    r = inputs.complex_gaussian(L, N, 700 + L).astype(np.complex64)
+    want = opc.apply(c, r.astype(np.complex128))
+    for autotune in (False, True):
+        with hq.Config(L, N, autotune=autotune) as cfg:
+            sh = hq.get_precond_shape(cfg, hq.FP32)
+            assert 16 <= sh["tile_slices"] <= 256 and sh["fused"] in (False, True)
+            assert hq.get_precond_shape(cfg, hq.FP64)["tile_slices"] == 64
+            z = hq.apply_precond(cfg, cuda(r)).cpu().numpy()
+        assert rel(z, want) < 1e-5
+
+
 @pytest.mark.parametrize("L,N,start", [(4, 6, "hot"), (8, 40, "hot"), (8, 40, "cold"), (12, 24, "warm")])
 def test_pcg64_matches_oracle_pcg(hq, L, N, start):
     lat = oracle.Lattice(L, N)
