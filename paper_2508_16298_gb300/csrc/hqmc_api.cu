@@ -713,9 +713,10 @@ int line_coefficients(hqmc_config* cfg) {
   cfg->pc_a = a;
   cfg->pc_b = b;
   cfg->lc = LineCoef{rho, std::pow(rho, W + 1), rho / b, W};
+  cfg->ll64 = line_launch(g, line_chunk_candidates(g, 8, W, cfg->num_sms, cfg->smem_per_sm).front());
+  cfg->ll32 = line_launch(g, line_chunk_candidates(g, 4, W, cfg->num_sms, cfg->smem_per_sm).front());
   if (line_smem_bytes(8, W, cfg->ll64.chunk) > kMaxLineSmem || line_update_smem_bytes(8, W) > kMaxLineSmem)
     return fail(cfg, HQMC_EUNSUPPORTED, "tau-line preconditioner width W=%d too large", W);
-  cfg->ll32 = line_launch(g, line_chunk_candidates(g, 4, W, cfg->num_sms, cfg->smem_per_sm).front());
   CK(prepare_line_precond<double>(W, cfg->ll64.chunk));
   CK(prepare_line_precond<float>(W, cfg->ll32.chunk));
   CK(prepare_line_update<double>(W));

@@ -70,15 +70,27 @@ template <class R> constexpr int line_tile_slices() { return sizeof(R) == 4 ? 12
 // Shared memory of a tile of tc slices: x on slices t0 .. t1 + W.
 size_t line_smem_bytes(int real_bytes, int W, int tc) { return (size_t)(tc + W + 1) * kLineSites * 2 * real_bytes; }
 
-// Candidate heights of the separate kernel's tiles (FP32): tc = ceil(N / k),
+// Candidate heights of the separate kernel's tiles.  FP32: tc = ceil(N / k),
 // 16 <= tc <= 256, with at least four tiles resident per SM and all tiles
 // resident at once (one round), ordered by the recursion work per SM (each
-// warp restarts both recursions W slices early: a fixed cost per tile).  The
-// first is the default; the autotuner times them.  FP64 keeps 64 slices.
+// warp restarts both recursions W slices early: a fixed cost per tile); the
+// first is the default, the autotuner times them.  FP64 is bound by the FP64
+// FMA rate, so the work per slice decides: the tallest tc = ceil(N / k) <= 256
+// that still gives every SM two tiles, else 64.
 std::vector<int> line_chunk_candidates(const Geo& g, int real_bytes, int W, int num_sms, size_t smem_per_sm) {
   std::vector<std::pair<double, int>> c;
-  if (real_bytes == 4) {
-    const long gx = (g.V + kLineSites - 1) / kLineSites;
+  const long gx = (g.V + kLineSites - 1) / kLineSites;
+  if (real_bytes == 8) {
+    for (int k = 1; k <= g.Ntau; ++k) {
+      const int tc = (g.Ntau + k - 1) / k;
+      if (tc > 256) continue;
+      if (tc < 64) break;
+      if (line_smem_bytes(real_bytes, W, tc) + 1024 > smem_per_sm) continue;
+      if (gx * ((g.Ntau + tc - 1) / tc) >= 2L * num_sms) return {tc};
+    }
+    return {line_tile_slices<double>()};
+  }
+  {
     int last = 0;
     for (int k = 1; k <= g.Ntau; ++k) {
       const int tc = (g.Ntau + k - 1) / k;

@@ -54,7 +54,8 @@ def test_coefficients_and_apply(hq, L, N):
 def test_tile_height_and_autotuned_parity(hq, L, N):
     """The separate kernel's FP32 tile height is chosen per config (all tiles
     resident at once where a height allows it; timed by the autotuner when it
-    runs); the result does not depend on it.  FP64 tiles keep 64 slices."""
+    runs); the result does not depend on it.  FP64 tiles are the tallest that
+    leave two per SM on large lattices, else 64 slices."""
     lat = oracle.Lattice(L, N)
     c = opc.coefficients(lat)
     r = inputs.complex_gaussian(L, N, 700 + L).astype(np.complex64)
@@ -63,9 +64,11 @@ def test_tile_height_and_autotuned_parity(hq, L, N):
         with hq.Config(L, N, autotune=autotune) as cfg:
             sh = hq.get_precond_shape(cfg, hq.FP32)
             assert 16 <= sh["tile_slices"] <= 256 and sh["fused"] in (False, True)
-            assert hq.get_precond_shape(cfg, hq.FP64)["tile_slices"] == 64
+            assert hq.get_precond_shape(cfg, hq.FP64)["tile_slices"] == (220 if L == 66 else 64)
             z = hq.apply_precond(cfg, cuda(r)).cpu().numpy()
+            z64 = hq.apply_precond(cfg, cuda(r.astype(np.complex128))).cpu().numpy()
         assert rel(z, want) < 1e-5
+        assert rel(z64, want) < 1e-12
 
 
 @pytest.mark.parametrize("L,N,start", [(4, 6, "hot"), (8, 40, "hot"), (8, 40, "cold"), (12, 24, "warm")])
