@@ -226,6 +226,28 @@ __device__ __forceinline__ double warp_sum_partials(const double* p, int n) {
   return __shfl_sync(0xffffffffu, s, 0);
 }
 
+// The same sum with four running sums per lane (elements lane + 32 j, j mod 4):
+// the dependent FP64 additions (slow on this part) form chains a quarter as
+// long, for a few more registers.  Used where hundreds of partials are summed
+// at the start of a kernel whose other registers dominate.
+__device__ __forceinline__ double warp_sum_partials4(const double* p, int n) {
+  const int lane = threadIdx.x & 31;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = lane;
+  for (; k + 96 < n; k += 128) {
+    s0 += p[k];
+    s1 += p[k + 32];
+    s2 += p[k + 64];
+    s3 += p[k + 96];
+  }
+  if (k < n) s0 += p[k];
+  if (k + 32 < n) s1 += p[k + 32];
+  if (k + 64 < n) s2 += p[k + 64];
+  double s = (s0 + s1) + (s2 + s3);
+  s = warp_sum(s);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
 // ---------------------------------------------------------------------------
 // Device-resident CG state.  Every field is written by exactly one kernel
 // launch and read by later launches, or written by block 0 into a slot that

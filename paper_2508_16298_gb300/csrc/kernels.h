@@ -87,7 +87,7 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
     } else if (k == seg) {
       flags = 2;
       if (a.part_rz) {
-        const double rz = warp_sum_partials(a.part_rz, a.n_part_rz);
+        const double rz = warp_sum_partials4(a.part_rz, a.n_part_rz);
         if (!isfinite(rz) || !(rz > 0.0)) {
           flags = 1;
           new_done = isfinite(rz) ? CG_BREAKDOWN : CG_NONFINITE;
@@ -96,8 +96,8 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
         }
       }
     } else {
-      const double rr = warp_sum_partials(a.part_in, a.n_part_in);
-      const double rz = a.part_rz ? warp_sum_partials(a.part_rz, a.n_part_rz) : rr;
+      const double rr = warp_sum_partials4(a.part_in, a.n_part_in);
+      const double rz = a.part_rz ? warp_sum_partials4(a.part_rz, a.n_part_rz) : rr;
       if (!isfinite(rr) || !isfinite(rz)) {
         flags = 1;
         new_done = CG_NONFINITE;

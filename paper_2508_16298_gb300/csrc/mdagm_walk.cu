@@ -16,6 +16,8 @@
 // (its links and x_{j+1}), then one thread refills the stage for step j + 1
 // while the block runs the two sweeps of step j, so HBM streams under the
 // compute.  The vector read for the halo row tb - 1 is the only direct load.
+// The first stage and the halo row are requested before the CG-direction head
+// sums the previous kernels' partials, so that latency overlaps the copy.
 //
 // CG-direction mode forms p = r + beta p_old on the fly, writes p and q = O p,
 // and accumulates <p, q> = Re sum_tau [<x_tau, t_tau> + cB <z_tau, w_tau>]
@@ -63,17 +65,15 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
   __shared__ float s_beta;
   __shared__ int s_k;
 
-  if (MODE == MODE_CGDIR) {
-    cgdir_head<float>(a, blockIdx.x == 0, s_flags, s_beta, s_k);
-    if (s_flags & 1) return;  // uniform over the grid
-  }
-  const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);
-  const float beta = (MODE == MODE_CGDIR) ? s_beta : 0.f;
+  // The direction buffers follow the iteration count k, which no kernel changes
+  // while this one runs (the update kernel advances it): iteration k reads
+  // pbuf[k & 1] and writes pbuf[(k + 1) & 1].  Read here, before the head.
+  const int k0 = MODE == MODE_CGDIR ? *(volatile const int*)&a.st->k : 0;
   const T* p_old = nullptr;
   T* p_new = nullptr;
   if (MODE == MODE_CGDIR) {
-    p_old = (s_k & 1) ? a.pbuf[1] : a.pbuf[0];
-    p_new = (s_k & 1) ? a.pbuf[0] : a.pbuf[1];
+    p_old = (k0 & 1) ? a.pbuf[1] : a.pbuf[0];
+    p_new = (k0 & 1) ? a.pbuf[0] : a.pbuf[1];
   }
   const T* vsrc = MODE == MODE_CGDIR ? a.r : a.x;
 
@@ -82,15 +82,17 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
   const int te = (int)((long long)(blockIdx.x + 1) * N / G);
   auto wrap = [N](int j) { return j < 0 ? j + N : (j >= N ? j - N : j); };
 
+  // The stage always carries p_old in CG-direction mode (ignored on the first
+  // iteration of a segment), so its size does not wait for the head.
   const uint32_t slice_bytes = (uint32_t)V * (uint32_t)sizeof(T);
-  const uint32_t stage_bytes = slice_bytes * (1 + ((MODE == MODE_CGDIR && !first) ? 2 : 1));
+  const uint32_t stage_bytes = slice_bytes * (MODE == MODE_CGDIR ? 3 : 2);
   auto issue = [&](int j) {  // stage of step j: theta_j and the vectors of slice j + 1
     const size_t sj = (size_t)wrap(j) * V, sn = (size_t)wrap(j + 1) * V;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(&bar, stage_bytes);
     bulk_load(Sth, a.th32 + sj, slice_bytes, &bar);
     bulk_load(Sv0, vsrc + sn, slice_bytes, &bar);
-    if (MODE == MODE_CGDIR && !first) bulk_load(Sv1, p_old + sn, slice_bytes, &bar);
+    if (MODE == MODE_CGDIR) bulk_load(Sv1, p_old + sn, slice_bytes, &bar);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar);
@@ -98,14 +100,8 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
   }
 
   const StripGeo sg = strip_geo<NBY>(L);
-  const float cB = a.cB;
-  const float t1 = (float)a.t1, t2 = (float)a.t2;
-  int eb = 0;
   T v[H][2], t[H][2];
-  StripLinks<T, NBY> lk;
-  double acc = 0.0;
-
-  {  // x_{tb-1}, the halo row (p is formed exactly as its owner forms it)
+  {  // x_{tb-1}, the halo row: r (or x) and p_old requested before the head
     const size_t base = (size_t)wrap(tb - 1) * V;
 #pragma unroll
     for (int r = 0; r < H; ++r) {
@@ -113,12 +109,31 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const size_t gi = base + y * L + (c ? sg.x1 : sg.x0);
-        T xv = vsrc[gi];
-        if (MODE == MODE_CGDIR && !first) xv = caxpy(xv, beta, p_old[gi]);
-        v[r][c] = xv;
+        v[r][c] = vsrc[gi];
+        if (MODE == MODE_CGDIR) t[r][c] = p_old[gi];
       }
     }
   }
+  if (MODE == MODE_CGDIR) {
+    cgdir_head<float>(a, blockIdx.x == 0, s_flags, s_beta, s_k);
+    if (s_flags & 1) {  // uniform over the grid; the stage in flight lands before the block exits
+      if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0);
+      return;
+    }
+  }
+  const bool first = (MODE == MODE_CGDIR) && (s_flags & 2);
+  const float beta = (MODE == MODE_CGDIR) ? s_beta : 0.f;
+  if (MODE == MODE_CGDIR && !first) {  // p of the halo row, formed exactly as its owner forms it
+#pragma unroll
+    for (int r = 0; r < H; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) v[r][c] = caxpy(v[r][c], beta, t[r][c]);
+  }
+  const float cB = a.cB;
+  const float t1 = (float)a.t1, t2 = (float)a.t2;
+  int eb = 0;
+  StripLinks<T, NBY> lk;
+  double acc = 0.0;
   __syncthreads();  // the mbarrier is initialised before anyone waits on it
 
   uint32_t parity = 0;
