@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(256) net_layer_kernel(Geo g, const float2* __r
 // loops fully unrolled every weight index is a compile-time constant, so each
 // FMA reads its weight straight from the constant bank: no shared-memory fill,
 // no weight loads and no waits on them.  The arithmetic and its order are those
-// of net_layer_kernel, so the results are identical.
+// of net_layer_kernel.  Activations with several channels are channel-planar
+// here (channel c of site i at c * n + i), so every warp load and store is one
+// contiguous row of 32 sites; the site-major layout of the training kernels
+// would spread a warp's 16-byte loads over 32 lines.  The inference path's
+// intermediate buffers are its own; one channel is the same in both layouts.
 template <int CIN, int COUT>
 struct NetLayerW {
   float w[7][CIN][COUT];
@@ -233,38 +237,18 @@ __global__ void __launch_bounds__(256) net_layer_cw_kernel(Geo g, const float2* 
         ph = make_float2(tau == 0 ? -1.f : 1.f, 0.f);
       }
 #pragma unroll
-      for (int cp2 = 0; cp2 < (CIN + 1) / 2; ++cp2) {
-        float2 hv[2];
-        if constexpr (CIN % 2 == 0) {
-          const float4 q = __ldg(reinterpret_cast<const float4*>(in + (size_t)j * CIN) + cp2);
-          hv[0] = make_float2(q.x, q.y);
-          hv[1] = make_float2(q.z, q.w);
-        } else {
-          hv[0] = __ldg(in + (size_t)j * CIN + 2 * cp2);
-          hv[1] = make_float2(0.f, 0.f);
-        }
+      for (int cp = 0; cp < CIN; ++cp) {
+        const float2 v = cmulf(ph, __ldg(in + (size_t)cp * n + j));
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int cp = 2 * cp2 + h;
-          if (cp >= CIN) break;
-          const float2 v = cmulf(ph, hv[h]);
-#pragma unroll
-          for (int c = 0; c < COUT; ++c) {
-            const float wv = W.w[mu][cp][c];
-            acc[c].x = fmaf(wv, v.x, acc[c].x);
-            acc[c].y = fmaf(wv, v.y, acc[c].y);
-          }
+        for (int c = 0; c < COUT; ++c) {
+          const float wv = W.w[mu][cp][c];
+          acc[c].x = fmaf(wv, v.x, acc[c].x);
+          acc[c].y = fmaf(wv, v.y, acc[c].y);
         }
       }
     }
-    if constexpr (COUT % 2 == 0) {
-      float4* o = reinterpret_cast<float4*>(out + (size_t)i * COUT);
 #pragma unroll
-      for (int c2 = 0; c2 < COUT / 2; ++c2) o[c2] = make_float4(acc[2 * c2].x, acc[2 * c2].y, acc[2 * c2 + 1].x, acc[2 * c2 + 1].y);
-    } else {
-#pragma unroll
-      for (int c = 0; c < COUT; ++c) out[(size_t)i * COUT + c] = acc[c];
-    }
+    for (int c = 0; c < COUT; ++c) out[(size_t)c * n + i] = acc[c];
   }
 }
 
