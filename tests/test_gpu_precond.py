@@ -33,7 +33,7 @@ def rel(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b))))
 
 
-@pytest.mark.parametrize("L,N", [(4, 6), (6, 33), (8, 40), (10, 9), (24, 240), (66, 660)])
+@pytest.mark.parametrize("L,N", [(4, 6), (6, 2), (6, 33), (8, 40), (10, 9), (24, 240), (66, 660)])
 def test_coefficients_and_apply(hq, L, N):
     """Ntau < W + 1 makes the window wrap the tau line several times (sign per wrap)."""
     lat = oracle.Lattice(L, N)
