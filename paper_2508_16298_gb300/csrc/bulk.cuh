@@ -1,5 +1,5 @@
 // Bulk asynchronous copies global -> shared (cp.async.bulk) completing on an
-// mbarrier, with waits bounded by %globaltimer (mdagm_walk.cu, precond.cu).
+// mbarrier, with waits bounded by %globaltimer (used by mdagm_walk.cu).
 #pragma once
 
 #include <cuda_runtime.h>
