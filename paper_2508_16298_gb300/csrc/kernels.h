@@ -67,6 +67,15 @@ struct MdagmArgs {
 // st->rr, in the step length.
 // s_flags: bit 0 = skip the launch (uniform over the grid), bit 1 = first
 // iteration of a recurrence segment (p = r, or p = z).
+// Partial sums of the head: four running sums per lane for the FP32 kernels (their
+// other registers dominate, and the dependent FP64 additions are slow); the compact
+// sum for the FP64 kernels, whose occupancy the extra registers would lower.
+template <class R>
+__device__ __forceinline__ double head_sum(const double* p, int n) {
+  if constexpr (sizeof(R) == 4) return warp_sum_partials4(p, n);
+  return warp_sum_partials(p, n);
+}
+
 template <class R>
 __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, int& s_flags, R& s_beta,
                                            int& s_k) {
@@ -87,7 +96,7 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
     } else if (k == seg) {
       flags = 2;
       if (a.part_rz) {
-        const double rz = warp_sum_partials4(a.part_rz, a.n_part_rz);
+        const double rz = head_sum<R>(a.part_rz, a.n_part_rz);
         if (!isfinite(rz) || !(rz > 0.0)) {
           flags = 1;
           new_done = isfinite(rz) ? CG_BREAKDOWN : CG_NONFINITE;
@@ -96,8 +105,8 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
         }
       }
     } else {
-      const double rr = warp_sum_partials4(a.part_in, a.n_part_in);
-      const double rz = a.part_rz ? warp_sum_partials4(a.part_rz, a.n_part_rz) : rr;
+      const double rr = head_sum<R>(a.part_in, a.n_part_in);
+      const double rz = a.part_rz ? head_sum<R>(a.part_rz, a.n_part_rz) : rr;
       if (!isfinite(rr) || !isfinite(rz)) {
         flags = 1;
         new_done = CG_NONFINITE;
