@@ -83,6 +83,29 @@ __device__ __forceinline__ T link_from_theta(float th, float t) {
   return mk(t * cs, t * sn);
 }
 
+// t e^{i theta} for theta in [-pi, pi] on the FMA pipe, from the Taylor series of
+// sin and cos at the half angle h = theta/2 (|h| <= pi/2; the omitted terms are
+// below (pi/2)^13/13! = 6e-8 and (pi/2)^14/14! = 7e-9), then
+// cos theta = (cos h - sin h)(cos h + sin h), sin theta = 2 sin h cos h.
+// Links formed this way share the work of a step with __sincosf, whose MUFU
+// pipe otherwise bounds the link phase.
+__device__ __forceinline__ float2 link_from_theta_poly(float th, float t) {
+  const float h = 0.5f * th, h2 = h * h;
+  float sp = fmaf(h2, -1.f / 39916800.f, 1.f / 362880.f);
+  sp = fmaf(h2, sp, -1.f / 5040.f);
+  sp = fmaf(h2, sp, 1.f / 120.f);
+  sp = fmaf(h2, sp, -1.f / 6.f);
+  sp = fmaf(h2, sp, 1.f);
+  const float sh = h * sp;
+  float cp = fmaf(h2, 1.f / 479001600.f, -1.f / 3628800.f);
+  cp = fmaf(h2, cp, 1.f / 40320.f);
+  cp = fmaf(h2, cp, -1.f / 720.f);
+  cp = fmaf(h2, cp, 1.f / 24.f);
+  cp = fmaf(h2, cp, -0.5f);
+  const float ch = fmaf(h2, cp, 1.f);
+  return make_float2(t * ((ch - sh) * (ch + sh)), (2.f * t) * (sh * ch));
+}
+
 template <bool SMEM>
 __device__ __forceinline__ float2 th_at(const float2* th, int i) {
   if constexpr (SMEM) return th[i];
@@ -104,8 +127,8 @@ __device__ __forceinline__ void load_strip_links_smem(const StripGeo& s, const f
     const float4 a = th4[(y * L + s.xl) >> 1];  // theta(2i), theta(x0)
     const float4 b = th4[(y * L + s.x1) >> 1];  // theta(x1), theta(x1 + 1)
     k.u2[r] = link_from_theta<float2>(a.z, t2);
-    k.u1l[r] = link_from_theta<float2>(a.x, t1);
-    k.u1r[r] = link_from_theta<float2>(b.x, t1);
+    k.u1l[r] = link_from_theta_poly(a.x, t1);  // family 1 on the FMA pipe, the rest on MUFU
+    k.u1r[r] = link_from_theta_poly(b.x, t1);
     if (r & 1) {  // D row base + r = drow(r - 1): family 4, tails on odd y
       k.u4[r >> 1][0] = link_from_theta<float2>(a.w, t2);
       k.u4[r >> 1][1] = link_from_theta<float2>(b.y, t2);
