@@ -86,7 +86,7 @@ MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pm
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu capture summarised in
 # profiles/mdagm_walk_fp32_L66_Nt660.md (cold caches; writes still in L2 at the kernel's end are not
 # counted there).  Valid for the kernel as captured; set to None when the kernel changes.
-NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 78.401792e6 + 9.412352e6}
+NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 77.954048e6 + 9.346304e6}
 
 
 def _peaks():
