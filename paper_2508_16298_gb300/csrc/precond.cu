@@ -308,9 +308,12 @@ __global__ void __launch_bounds__(kLineSites* kLineWarps) line_precond_batch_ker
 //   r <- r - alpha q and x <- x + alpha p on the tile's own slices;
 //   z = Otilde^{-1} r on the updated r, with the partials of <r, r> (convergence)
 //   and <r, z> (next step length).
-// The tile loads r and q on its slices and halo, forms r - alpha q there (the
-// halo rows with the same arithmetic as the tiles that own them), then runs the
-// two recursions as line_precond_kernel does.  The updated r goes to a second
+// The tile stages r and q on its slices and halo in shared memory by cp.async
+// (fixed tiles of line_tile_slices rows), forms r - alpha q there (the halo rows
+// with the same arithmetic as the tiles that own them), then runs the same two
+// recursions as line_precond_kernel over the staged rows; <r, z> is summed
+// directly.  (A streaming form like line_precond_kernel's was slower here: it
+// re-reads r and q for the leaving row.)  The updated r goes to a second
 // buffer (r_out): a tile's halo rows are other tiles' own rows, so writing r in
 // place would race with their loads; the caller alternates the two buffers.
 // One HBM pass over r and q, x, p instead of the update's pass plus the
