@@ -64,8 +64,9 @@ enum {
     HQMC_SOLVER_MIXED = 1,   /* CG with M^dagger M in FP32 (complex float) and FP64 reliable
                                 residual updates every params.reliable_interval iterations */
     HQMC_SOLVER_LEARNED = 2, /* the attached net (hqmc_set_preconditioner) corrects the initial
-                                guess, x <- x + K(theta)(phi - O x), kept only if it lowers the
-                                FP64 residual; then the mixed solver, whose FP64 true residual
+                                guess, x <- x + K(theta)(phi - O x) with phi - O x from the FP32
+                                apply (the net's input precision), kept only if its FP64 residual
+                                is below that one; then the mixed solver, whose FP64 true residual
                                 judges convergence */
     /* The same three with the tau-line preconditioner Otilde^{-1} of hqmc_apply_precond in the
      * preconditioned CG of Methods Eq. (pCG): directions from z = Otilde^{-1} r, step lengths

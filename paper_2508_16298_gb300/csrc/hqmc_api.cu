@@ -559,11 +559,22 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   bool started = false;  // the FP64 residual that starts the recurrence is already in place
   if (solver_base(solver) == HQMC_SOLVER_LEARNED) {
     // candidate x1 = x + K r0 with r0 = phi - O x; the CG workspace is free here.
-    // The FP64 residual of x1 is computed as the start of the mixed recurrence, so a
-    // kept candidate costs no extra residual; a rejected one restores x and starts again.
+    // r0 comes from the FP32 fused apply: the net reads it in FP32, and ||r0|| only
+    // decides whether the candidate is kept.  The FP64 residual of x1 is computed as
+    // the start of the mixed recurrence, so a kept candidate costs no FP64 residual
+    // beyond the one any solve starts with; a rejected one restores x and starts again.
     solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
     RET(net_workspace(cfg));
-    RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
+    LK(1, launch_net_convert(x, cfg->xh32, 1, 1.0, cfg->n, s));  // x as float (xh32 is free until the loop)
+    {
+      MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
+      a.U = cfg->U32;
+      a.x = cfg->xh32;
+      a.y = cfg->q32;
+      LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
+    }
+    LK(1, launch_resid_from_fp32(cfg->n, phi, cfg->q32, cfg->vscratch, s));
+    LK(2, launch_cdot(cfg->n, cfg->vscratch, cfg->vscratch, cfg->act_grid, cfg->part_act, cfg->report, s));
     RET(read_state(cfg, s));
     const double rr0 = cfg->report_h[0];
     RET(net_forward(cfg, cfg->net, cfg->vscratch, cfg->p64[1], s));                       // z = K r0

@@ -339,6 +339,8 @@ void philox_uniform_host(uint64_t seed, uint64_t counter, double* u);
 cudaError_t launch_draw_vector(long long n_sites, uint64_t seed, uint32_t stream, uint64_t counter, double2* v,
                                cudaStream_t s);
 // out[0] + i out[1] = <a, b> = sum conj(a_i) b_i; part holds 2 * grid doubles.
+// r = phi - y, y from an FP32 apply (the learned guess's input residual).
+cudaError_t launch_resid_from_fp32(long long n, const double2* phi, const float2* y, double2* r, cudaStream_t s);
 cudaError_t launch_cdot(long long n, const double2* a, const double2* b, int grid, double* part, double* out,
                         cudaStream_t s);
 // FP64 FMA throughput probe (16 flops per thread per iteration).

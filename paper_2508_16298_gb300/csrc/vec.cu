@@ -558,6 +558,22 @@ cudaError_t launch_draw_vector(long long n_sites, uint64_t seed, uint32_t stream
   return cudaGetLastError();
 }
 
+// r = phi - y with y from an FP32 apply (FP64 result).
+__global__ void resid_from_fp32_kernel(long long n, const double2* __restrict__ phi, const float2* __restrict__ y,
+                                       double2* __restrict__ r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 p = phi[i];
+    const float2 v = y[i];
+    r[i] = make_double2(p.x - (double)v.x, p.y - (double)v.y);
+  }
+}
+
+cudaError_t launch_resid_from_fp32(long long n, const double2* phi, const float2* y, double2* r, cudaStream_t s) {
+  resid_from_fp32_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, phi, y, r);
+  return cudaGetLastError();
+}
+
 // <a, b> = sum conj(a_i) b_i (complex), as per-block partials in a fixed order
 // and one warp that sums them: out[0] = Re, out[1] = Im.
 __global__ void cdot_partials_kernel(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
