@@ -241,8 +241,8 @@ SOLVER_TEXT = {
     "pcg64": "pcg64: FP64 CG preconditioned with the tau-line preconditioner",
     "mixed": "mixed: FP32 M^dagger M in CG, FP64 reliable updates every 50 iterations",
     "pmixed": "pmixed: the mixed solver preconditioned with the tau-line preconditioner (FP32)",
-    "learned": "learned: net-corrected initial guess (kept if it lowers the FP64 residual), then the mixed solver",
-    "plearned": "plearned: net-corrected initial guess (kept if it lowers the FP64 residual), then the mixed "
+    "learned": "learned: net-corrected initial guess (kept if its FP64 residual is below the FP32 residual of the guess it corrects), then the mixed solver",
+    "plearned": "plearned: net-corrected initial guess (kept if its FP64 residual is below the FP32 residual of the guess it corrects), then the mixed "
                 "solver preconditioned with the tau-line preconditioner (FP32)",
 }
 
