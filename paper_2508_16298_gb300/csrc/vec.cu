@@ -349,38 +349,52 @@ __device__ __forceinline__ double curl_at(const double* th, int L, int x, int y)
 
 __device__ __forceinline__ double fprime(double d, int noncompact) { return noncompact ? 2.0 * d : sin(d); }
 
+// One thread per (site, chunk of kFinishChunk slices), walking its chunk in tau:
+// the term f'(theta_{tau+1} - theta_tau) of slice tau is the f'(theta_tau' -
+// theta_{tau'-1}) of slice tau' = tau + 1, so it is evaluated once and carried
+// (the same operands in the same order: results identical to evaluating it twice).
+constexpr int kFinishChunk = 32;
+
 __global__ void force_finish_kernel(Geo g, BosonParams bp, const double* __restrict__ theta,
-                                    const double* __restrict__ dSf, double* __restrict__ F, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int tau = (int)(i / g.V);
-    const int s = (int)(i - (long long)tau * g.V);
+                                    const double* __restrict__ dSf, double* __restrict__ F, int nchunk) {
+  const long long nt = (long long)g.V * nchunk;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nt;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(k / g.V);
+    const int s = (int)(k - (long long)ch * g.V);
     const int x = s % g.L, y = s / g.L;
-    const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
-    const int tm = (tau == 0) ? g.Ntau - 1 : tau - 1;
-    const double* th = theta + (size_t)tau * g.V * 2;
-    const double* thp = theta + (size_t)tp * g.V * 2;
-    const double* thm = theta + (size_t)tm * g.V * 2;
-    double dB[2];
-    for (int c = 0; c < 2; ++c) {
-      const double t0 = th[2 * s + c];
-      dB[c] = bp.cK * (fprime(t0 - thm[2 * s + c], bp.noncompact) - fprime(thp[2 * s + c] - t0, bp.noncompact));
+    const int t0 = ch * kFinishChunk, t1 = min(g.Ntau, t0 + kFinishChunk);
+    const int tm0 = (t0 == 0) ? g.Ntau - 1 : t0 - 1;
+    const double2 thm = reinterpret_cast<const double2*>(theta + (size_t)tm0 * g.V * 2)[s];
+    double2 th = reinterpret_cast<const double2*>(theta + (size_t)t0 * g.V * 2)[s];
+    double dprev[2] = {fprime(th.x - thm.x, bp.noncompact), fprime(th.y - thm.y, bp.noncompact)};
+    for (int tau = t0; tau < t1; ++tau) {
+      const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
+      const double2 thp = reinterpret_cast<const double2*>(theta + (size_t)tp * g.V * 2)[s];
+      const double dnext[2] = {fprime(thp.x - th.x, bp.noncompact), fprime(thp.y - th.y, bp.noncompact)};
+      double dB[2] = {bp.cK * (dprev[0] - dnext[0]), bp.cK * (dprev[1] - dnext[1])};
+      if (bp.Kdtau != 0.0) {
+        const double* ths = theta + (size_t)tau * g.V * 2;
+        const int xm = (x == 0) ? g.L - 1 : x - 1, ym = (y == 0) ? g.L - 1 : y - 1;
+        const double s00 = sin(curl_at(ths, g.L, x, y));
+        dB[0] += -bp.Kdtau * s00 + bp.Kdtau * sin(curl_at(ths, g.L, x, ym));
+        dB[1] += bp.Kdtau * s00 - bp.Kdtau * sin(curl_at(ths, g.L, xm, y));
+      }
+      const size_t i = (size_t)tau * g.V + s;
+      const double2 f = reinterpret_cast<const double2*>(dSf)[i];
+      reinterpret_cast<double2*>(F)[i] = make_double2(-f.x - dB[0], -f.y - dB[1]);
+      dprev[0] = dnext[0];
+      dprev[1] = dnext[1];
+      th = thp;
     }
-    if (bp.Kdtau != 0.0) {
-      const int xm = (x == 0) ? g.L - 1 : x - 1, ym = (y == 0) ? g.L - 1 : y - 1;
-      const double s00 = sin(curl_at(th, g.L, x, y));
-      dB[0] += -bp.Kdtau * s00 + bp.Kdtau * sin(curl_at(th, g.L, x, ym));
-      dB[1] += bp.Kdtau * s00 - bp.Kdtau * sin(curl_at(th, g.L, xm, y));
-    }
-    const double2 f = reinterpret_cast<const double2*>(dSf)[i];
-    reinterpret_cast<double2*>(F)[i] = make_double2(-f.x - dB[0], -f.y - dB[1]);
   }
 }
 
 cudaError_t launch_force_finish(const Geo& g, const BosonParams& bp, const double* theta,
                                 const double* dSf, double* F, cudaStream_t s) {
-  const long long n = (long long)g.V * g.Ntau;
-  force_finish_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(g, bp, theta, dSf, F, n);
+  const int nchunk = (g.Ntau + kFinishChunk - 1) / kFinishChunk;
+  const long long n = (long long)g.V * nchunk;
+  force_finish_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(g, bp, theta, dSf, F, nchunk);
   return cudaGetLastError();
 }
 
