@@ -56,6 +56,7 @@ struct hqmc_config {
   SliceLaunch slb64{}; // register-blocked fused M^dagger M, FP64 (nby = 0: not available)
   SliceLaunch slb32{}; // register-blocked fused M^dagger M, FP32 (nby = 0: not available)
   SliceLaunch slw32{}; // tau-walking fused M^dagger M, FP32 (walk = 0: not available)
+  SliceLaunch slw32h[3]{};  // every strip height whose walk block fits (walk = 0: unused), for the autotuner
   int num_sms = 0;
   // tau-line preconditioner: coefficients from the pi-flux field, launch shape, workspace
   double pc_a = 0, pc_b = 0;
@@ -908,13 +909,17 @@ int autotune(hqmc_config* cfg) {
       }
     }
     if (!dbl && cfg->slw32.walk) {
-      // tau-walking kernel: one to a few CTAs per SM, never more CTAs than slices
-      const int bps = mdagm_walk_blocks_per_sm(cfg->slw32);
-      for (int m = 1; m <= bps && m <= 4; ++m) {
-        SliceLaunch w = cfg->slw32;
-        w.grid = std::min(N, m * cfg->num_sms);
-        cand.push_back(w);
-        if (w.grid == N) break;
+      // tau-walking kernel, every strip height that fits: one to a few CTAs per
+      // SM, never more CTAs than slices
+      for (const SliceLaunch& h : cfg->slw32h) {
+        if (!h.walk) continue;
+        const int bps = mdagm_walk_blocks_per_sm(h);
+        for (int m = 1; m <= bps && m <= 4; ++m) {
+          SliceLaunch w = h;
+          w.grid = std::min(N, m * cfg->num_sms);
+          cand.push_back(w);
+          if (w.grid == N) break;
+        }
       }
     }
     if (!dbl && cfg->p.variant == 3) {  // the tau-walking kernel only
@@ -1103,12 +1108,14 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     pick_block(4, &cfg->slb32);
     cfg->num_sms = prop.multiProcessorCount;
     cfg->smem_per_sm = prop.sharedMemPerMultiprocessor;
-    // tau-walking FP32 kernel: the smallest strip height whose block fits, one CTA per SM
+    // tau-walking FP32 kernel: by default the smallest strip height whose block
+    // fits; every height that fits is kept for the autotuner (a taller strip has
+    // fewer threads per CTA, and on some lattices two CTAs then share an SM)
     cfg->slw32 = cfg->sl32;
     cfg->slw32.walk = 0;
     {
       const int Lh = L / 2;
-      for (int nby = 1; nby <= 3 && !cfg->slw32.walk; ++nby) {
+      for (int nby = 1; nby <= 3; ++nby) {
         if (Lh % nby) continue;
         const int th = Lh * Lh / nby;
         if (th > walk_thread_cap(nby) || walk_smem_bytes(cfg->g, MODE_CGDIR) > prop.sharedMemPerBlockOptin) continue;
@@ -1123,7 +1130,8 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
           cudaGetLastError();
           continue;
         }
-        cfg->slw32 = c;
+        cfg->slw32h[nby - 1] = c;
+        if (!cfg->slw32.walk) cfg->slw32 = c;
       }
     }
     // variant 1 keeps the generic kernel, 2 demands the register-blocked one

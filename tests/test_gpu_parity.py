@@ -320,7 +320,7 @@ def test_invalid_arguments(hq):
             hq.apply_MdagM(cfg, th, torch.zeros((4, 4, 5), dtype=torch.complex128, device="cuda"))
 
 
-@pytest.mark.parametrize("L,N", [(8, 13), (24, 240), (66, 660)])
+@pytest.mark.parametrize("L,N", [(8, 13), (24, 240), (48, 480), (66, 660)])
 def test_autotuned_shapes_keep_parity(hq, L, N):
     """The autotuner picks kernel variant and cluster size; results must not change."""
     lat = oracle.Lattice(L, N)
