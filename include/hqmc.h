@@ -196,11 +196,13 @@ HQMC_API int hqmc_apply_precond(hqmc_config* cfg, const void* r, void* z, int pr
  * output may be NULL. */
 HQMC_API int hqmc_get_precond(const hqmc_config* cfg, double* a, double* b, double* rho, int* W);
 
-/* Launch shape of the preconditioner for one precision (host query): slices
- * per tile of the separate kernel (*tile_slices; FP32 chosen per config, timed
- * by the autotuner when it runs) and whether preconditioned CG fuses the vector
- * update with the preconditioner (*fused, 0 or 1; the autotuner's choice).  Any
- * output may be NULL. */
+/* Launch shape of the tau-line preconditioner (Methods, "CG method and
+ * preconditioner") for one precision, a host query with no device work: slices
+ * per tile of the separate kernel (*tile_slices; chosen per config, for FP32
+ * timed by the autotuner when it runs) and whether preconditioned CG fuses the
+ * vector update with the preconditioner (*fused, 0 or 1; the autotuner's
+ * choice, 0 under variant 1).  Any output may be NULL.  Returns HQMC_EINVAL for
+ * a NULL cfg or a precision other than HQMC_FP64 / HQMC_FP32. */
 HQMC_API int hqmc_get_precond_shape(const hqmc_config* cfg, int precision, int* tile_slices, int* fused);
 
 /* y = (M^dagger M) x in FP64 without a config and without allocating device
