@@ -129,3 +129,31 @@ def test_pcg_cuts_iterations_on_a_tau_smooth_field():
     X2, its2, _, _ = oracle.cg(lat, th, phi, tol=1e-8)
     assert res <= 1e-8 and its * 4 < its2
     assert np.linalg.norm(X - X2) < 1e-6 * np.linalg.norm(X2)
+
+
+def test_F_and_its_adjoint_against_the_dense_shift():
+    """F_W and F_W^dagger as dense polynomials in the antiperiodic shift matrix: apply_F
+    is sum rho^m S^m and apply_F_adj its transpose, on lines short enough to wrap
+    several times (N < W)."""
+    for N in (5, 12, 40):
+        lat = oracle.Lattice(4, N)
+        c = pc.coefficients(lat)
+        S = antiperiodic_shift(N)
+        F = sum(c.rho ** m * np.linalg.matrix_power(S, m) for m in range(c.W + 1))
+        u = inputs.complex_gaussian(4, N, 500 + N)
+        Fu = np.einsum("ts,s...->t...", F, u)
+        Ftu = np.einsum("st,s...->t...", F, u)
+        assert np.max(np.abs(pc.apply_F(c, u) - Fu)) < 1e-12 * np.max(np.abs(Fu))
+        assert np.max(np.abs(pc.apply_F_adj(c, u) - Ftu)) < 1e-12 * np.max(np.abs(Ftu))
+
+
+def test_rz_is_the_scaled_norm_of_F_r():
+    """<r, Otilde^{-1} r> = (rho/b) ||F_W r||^2, the form in which the GPU sums the
+    pCG step length (each tile adds |x_tau|^2 of its own slices in the forward pass)."""
+    lat = oracle.Lattice(4, 40)
+    c = pc.coefficients(lat)
+    r = inputs.complex_gaussian(4, 40, 611)
+    rz = np.vdot(r.reshape(-1), pc.apply(c, r).reshape(-1))
+    x = pc.apply_F(c, r)
+    assert abs(rz.imag) < 1e-12 * abs(rz.real)
+    assert abs(rz.real - c.scale * np.vdot(x.reshape(-1), x.reshape(-1)).real) < 1e-12 * rz.real
