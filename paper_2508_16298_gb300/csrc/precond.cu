@@ -85,7 +85,8 @@ std::vector<int> line_chunk_candidates(const Geo& g, int real_bytes, int W, int 
       const int tc = (g.Ntau + k - 1) / k;
       if (tc > 256) continue;
       if (tc < 64) break;
-      if (line_smem_bytes(real_bytes, W, tc) + 1024 > smem_per_sm) continue;
+      // one tile must fit a block's opt-in shared memory (227 KB) and the SM
+      if (line_smem_bytes(real_bytes, W, tc) > std::min(smem_per_sm - 1024, (size_t)227 * 1024)) continue;
       if (gx * ((g.Ntau + tc - 1) / tc) >= 2L * num_sms) return {tc};
     }
     return {line_tile_slices<double>()};
