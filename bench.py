@@ -89,6 +89,26 @@ MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pm
 NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 77.954048e6 + 9.346304e6}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks: a job's time is that of its slowest replica."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every replica's units over the slowest replica's time."""
+    return world * units_per_rank / seconds
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Each replica runs its own chain, with seeds 1000 apart."""
+    return seed + 1000 * rank
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -331,7 +351,7 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     L, N = wl["L"], wl["Ntau"]
     sites = L * L * N
     cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True)
-    seed = wl["seed"] + 1000 * rank
+    seed = rank_seed(wl["seed"], rank)
     theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver=wl["solver"])
@@ -384,11 +404,8 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     n_up, up_ms = hqmc.get_timing(cfg, hqmc.TIMER_CG_UPDATE)
     n_pc, pc_ms = hqmc.get_timing(cfg, hqmc.TIMER_PRECOND)
     hqmc.set_timing(cfg, False)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = job_rate(args.steps, world, total_ms / 1e3)
 
     # ---- end to end through the public API with host buffers ----------------
     theta_h = theta.cpu().pin_memory()
@@ -402,11 +419,8 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
         theta_h.copy_(th_dev, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e_value = job_rate(e2e_steps, world, e2e_s)
 
     # ---- plain FP64 on the same chain state (same draws, dt, N_lf, tolerance) -----
     compare = None
@@ -526,7 +540,7 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     lats = BATCH_LATTICES
-    seeds = [wl["seed"] + i + 1000 * rank for i in range(len(lats))]
+    seeds = [rank_seed(wl["seed"] + i, rank) for i in range(len(lats))]
     # dt scaled with the volume as in the single-chain workload (|dH| ~ V dt^2)
     dts = [wl["dt"] * ((24 * 24 * 240) / (L * L * N)) ** 0.5 for L, N in lats]
     thetas = [torch.from_numpy(inputs.theta_ordered(L, N, s, tau_walk=0.0)).cuda() for (L, N), s in zip(lats, seeds)]
@@ -548,11 +562,8 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         launches = b.launch_count() - l0
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * len(lats) / (ms / 1e3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = job_rate(args.steps * len(lats), world, ms / 1e3)
     # the same chains, one trajectory each, run one after another
     seq_ms = 0.0
     for (L, N), s, dt, th in zip(lats, seeds, dts, thetas):
@@ -597,7 +608,7 @@ def run_estimate(args, wl_name, wl, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     L, N, nrv = wl["L"], wl["Ntau"], wl["nrv"]
     cfg = hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"], autotune=True)
-    seed = wl["seed"] + 1000 * rank
+    seed = rank_seed(wl["seed"], rank)
     theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for k in range(args.warmup):
@@ -625,11 +636,8 @@ def run_estimate(args, wl_name, wl, rank, world, local_rank):
     launches = cfg.launch_count() - l0
     clk = clocks.stop()
     total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * nrv / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = job_rate(args.steps * nrv, world, total_ms / 1e3)
     if rank != 0:
         return
     cb = oracle_sample(dict(wl, nsteps=-1), statistics.mean(its) / nrv, start_theta(wl, wl["seed"]),
