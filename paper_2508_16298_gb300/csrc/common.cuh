@@ -100,15 +100,15 @@ __device__ __forceinline__ void factor_pass(const Geo& g, int fam, T* v, const T
 
 // v <- (1 + U T_fam)^{-1} v = (1 - U T_fam) v / (1 - |U|^2); used by the force
 // sweep to step back through the factors without storing every partial product.
-template <class T>
-__device__ __forceinline__ void factor_pass_inverse(const Geo& g, int fam, T* v, const T* __restrict__ U) {
+// |U| is the family's tanh factor t_f, so inv = 1/(1 - t_f^2) is one constant per
+// family (the caller's), not a division per bond.
+template <class T, class R>
+__device__ __forceinline__ void factor_pass_inverse(const Geo& g, int fam, T* v, const T* __restrict__ U, R inv) {
   const int nb = g.V >> 1;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     int i, j, c;
     bond_of(g, fam, b, i, j, c);
     T u = __ldg(U + 2 * i + c);
-    auto nrm = u.x * u.x + u.y * u.y;
-    auto inv = 1 / (1 - nrm);
     T mu = mk(-u.x, -u.y);
     T vi = v[i], vj = v[j];
     T ni = cfma(vi, mu, vj);

@@ -23,8 +23,8 @@ namespace hqmc {
 __constant__ static const int kFam[7] = {4, 3, 2, 1, 2, 3, 4};  // P(1) ... P(7)
 
 __global__ void __launch_bounds__(1024, 1)
-force_kernel(Geo g, double cB, const double2* __restrict__ U, const double2* __restrict__ X,
-             double* __restrict__ dSf) {
+force_kernel(Geo g, double cB, double inv1, double inv2, const double2* __restrict__ U,
+             const double2* __restrict__ X, double* __restrict__ dSf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int V = g.V, N = g.Ntau;
   double2* u = reinterpret_cast<double2*>(smem_raw);
@@ -45,7 +45,9 @@ force_kernel(Geo g, double cB, const double2* __restrict__ U, const double2* __r
   apply_P(g, u, Ut);  // u = P X_tau
   for (int s = threadIdx.x; s < V; s += blockDim.x) w[s] = caxpy(X[bp + s], -sigp * cB, u[s]);  // Y_{tau+1}
   __syncthreads();
-  factor_pass_inverse(g, kFam[0], u, Ut);  // u_1 = P(1)^{-1} P X_tau
+  // 1/(1 - |U|^2): family 1 carries tanh(a), the others tanh(a/2)
+  auto inv_of = [&](int fam) { return fam == 1 ? inv1 : inv2; };
+  factor_pass_inverse(g, kFam[0], u, Ut, inv_of(kFam[0]));  // u_1 = P(1)^{-1} P X_tau
   __syncthreads();
 
   const double coef = -2.0 * cB * sgn;
@@ -69,7 +71,7 @@ force_kernel(Geo g, double cB, const double2* __restrict__ U, const double2* __r
     if (k == 6) break;
     __syncthreads();
     factor_pass(g, fam, w, Ut);                    // w_{k+1} = P(k) w_k
-    factor_pass_inverse(g, kFam[k + 1], u, Ut);    // u_{k+1} = P(k+1)^{-1} u_k
+    factor_pass_inverse(g, kFam[k + 1], u, Ut, inv_of(kFam[k + 1]));  // u_{k+1} = P(k+1)^{-1} u_k
     __syncthreads();
   }
 }
@@ -78,9 +80,10 @@ cudaError_t prepare_force(const SliceLaunch& sl) {
   return raise_smem_limit(force_kernel, 2 * sl.g.V * sizeof(double2));
 }
 
-cudaError_t launch_force(const SliceLaunch& sl, double cB, const double2* U, const double2* X,
+cudaError_t launch_force(const SliceLaunch& sl, double cB, double t1, double t2, const double2* U, const double2* X,
                          double* dSf, cudaStream_t s) {
-  force_kernel<<<sl.g.Ntau, sl.threads, 2 * sl.g.V * sizeof(double2), s>>>(sl.g, cB, U, X, dSf);
+  force_kernel<<<sl.g.Ntau, sl.threads, 2 * sl.g.V * sizeof(double2), s>>>(sl.g, cB, 1.0 / (1.0 - t1 * t1),
+                                                                          1.0 / (1.0 - t2 * t2), U, X, dSf);
   return cudaGetLastError();
 }
 

@@ -651,7 +651,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
 int force(hqmc_config* cfg, const double* theta, const double2* X, double* F, double* dSf, cudaStream_t s) {
   int slot;
   RET(timer_begin(cfg, HQMC_TIMER_FORCE, s, &slot));
-  LK(1, launch_force(cfg->sl1, cfg->cB, cfg->U64, X, dSf, s));
+  LK(1, launch_force(cfg->sl1, cfg->cB, cfg->t1, cfg->t2, cfg->U64, X, dSf, s));
   RET(timer_end(cfg, HQMC_TIMER_FORCE, s, slot));
   LK(1, launch_force_finish(cfg->g, cfg->bp, theta, dSf, F, s));
   return HQMC_OK;

@@ -310,7 +310,7 @@ cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, co
 cudaError_t launch_loop_condition(CgState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 
 // Fermion force dS_f/dtheta given X (FP64).
-cudaError_t launch_force(const SliceLaunch& sl, double cB, const double2* U, const double2* X,
+cudaError_t launch_force(const SliceLaunch& sl, double cB, double t1, double t2, const double2* U, const double2* X,
                          double* dSf, cudaStream_t s);
 cudaError_t prepare_force(const SliceLaunch& sl);
 
