@@ -1,6 +1,11 @@
 import os
 import sys
 
+# The CPU oracle's OpenMP threads sleep instead of spinning between calls, so
+# that they do not compete with numpy's BLAS threads in tests that alternate the
+# two (set before any library that links libgomp is loaded).
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
