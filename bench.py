@@ -83,9 +83,9 @@ MDAGM_FLOPS_PER_SITE = 134
 MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pmixed": 40, "plearned": 40}
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu capture summarised in
-# profiles/mdagm_walk_fp32_L66_Nt660.md (cold caches; writes still in L2 at the kernel's end are not
-# counted there).  Valid for the kernel as captured; set to None when the kernel changes.
+# DRAM bytes (read + write) of one launch of the dominant kernel from an ncu capture of the τ-walking
+# FP32 kernel at L = 66 (cold caches; writes still in L2 at the kernel's end are not counted there).
+# Valid for the kernel as captured; set to None when the kernel changes.
 NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 77.954048e6 + 9.346304e6}
 
 
@@ -309,6 +309,7 @@ def train_net(hqmc, inputs, cfg, wl, theta, seed, dev):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     net = hqmc.Net(seed=seed)
+    hqmc.set_preconditioner(cfg, net)  # allocates the config's net workspace
     first = last = None
     for ep in range(wl["epochs"]):
         losses = [net.train_step(cfg, th, ph, x, lr=wl["lr"]) for th, ph, x in trips]
@@ -316,7 +317,6 @@ def train_net(hqmc, inputs, cfg, wl, theta, seed, dev):
         last = statistics.mean(losses)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    hqmc.set_preconditioner(cfg, net)
     return net, {"triples": len(trips), "epochs": wl["epochs"], "sampler_s": round(t1 - t0, 2),
                  "train_s": round(t2 - t1, 2), "loss_first_epoch": round(first, 4), "loss_last_epoch": round(last, 4),
                  "loss": "||K(theta) phi - x||^2 / ||x||^2"}

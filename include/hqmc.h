@@ -49,9 +49,13 @@ typedef enum {
     HQMC_ENOTCONV = 2,     /* CG used up maxit; x holds the last iterate, info the true residual */
     HQMC_EBREAKDOWN = 3,   /* CG met <d, O d> <= 0 */
     HQMC_ENONFINITE = 4,   /* a NaN or Inf reached a CG reduction or the Hamiltonian */
-    HQMC_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    HQMC_ETIMEOUT = 5,     /* a bounded device-side wait (about 1 s) gave up: the kernel wrote NaN
+                              into its outputs and set the config's error word; the next solve
+                              (hqmc_cg_solve, hqmc_leapfrog, hqmc_trajectory, hqmc_estimate)
+                              returns this code and clears the word */
     HQMC_ECUDA = 6,        /* a CUDA runtime call failed (text in hqmc_last_error) */
-    HQMC_ENOMEM = 7,       /* workspace allocation failed in hqmc_make_config */
+    HQMC_ENOMEM = 7,       /* workspace allocation failed (hqmc_make_config, hqmc_make_batch,
+                              hqmc_net_create, hqmc_set_preconditioner) */
     HQMC_EUNSUPPORTED = 8  /* option not available for these sizes or this device */
 } hqmc_status;
 
@@ -126,10 +130,12 @@ typedef struct hqmc_traj_info {
 /* ---- configuration ----------------------------------------------------- */
 
 /* Validates *p, chooses launch shapes for the current device and allocates
- * the workspace (this is the only call that allocates device memory).
+ * the workspace.  On a config, device memory is allocated only here and, for
+ * the learned net's activation fields, in hqmc_set_preconditioner; no apply,
+ * solve, force, leapfrog, trajectory or net call allocates.
  * *out receives the config; free it with hqmc_free_config.
  * Errors: HQMC_EINVAL (parameters), HQMC_EUNSUPPORTED (device is not
- * compute capability 10.x or 11.x-class with clusters), HQMC_ENOMEM, HQMC_ECUDA. */
+ * compute capability 10.x, the sm_103a build's family), HQMC_ENOMEM, HQMC_ECUDA. */
 HQMC_API int hqmc_make_config(const hqmc_params* p, hqmc_config** out);
 
 /* Releases the workspace.  NULL is accepted.  Waits for the device. */
@@ -205,8 +211,16 @@ HQMC_API int hqmc_get_precond(const hqmc_config* cfg, double* a, double* b, doub
  * a NULL cfg or a precision other than HQMC_FP64 / HQMC_FP32. */
 HQMC_API int hqmc_get_precond_shape(const hqmc_config* cfg, int precision, int* tile_slices, int* fused);
 
+/* Overrides the autotuner's choice between the fused and the separate vector
+ * update of preconditioned CG for one precision (fused: 1 or 0), e.g. to check
+ * both forms on one lattice.  Host-only; takes effect at the next solve.
+ * Returns HQMC_EINVAL for a NULL cfg, a bad precision or fused not 0/1, and
+ * HQMC_EUNSUPPORTED for fused = 1 on a variant-1 config (generic kernels only). */
+HQMC_API int hqmc_set_precond_fused(hqmc_config* cfg, int precision, int fused);
+
 /* y = (M^dagger M) x in FP64 without a config and without allocating device
- * memory.  The paper has no counterpart: this entry point exists for callers
+ * memory (HQMC_EUNSUPPORTED on a device that is not compute capability 10.x;
+ * HQMC_EINVAL for a non-finite or non-positive dtau * t).  The paper has no counterpart: this entry point exists for callers
  * that cannot allocate, such as code running while another component owns the
  * device allocator (a memory pool that must not be bypassed, or a budget that is
  * already handed out), plug-ins that are only given device pointers, or code
@@ -360,16 +374,22 @@ HQMC_API int hqmc_net_num_weights(const hqmc_net* net);
 /* FP32 master weights to / from host memory (n == hqmc_net_num_weights). */
 HQMC_API int hqmc_net_get_weights(const hqmc_net* net, float* host, int n);
 HQMC_API int hqmc_net_set_weights(hqmc_net* net, const float* host, int n);
-/* z = K(theta) r (complex double in and out; computed in FP32).  The first net
- * call on a config allocates its activation workspace (5 + 32 channel fields). */
+/* z = K(theta) r (complex double in and out; computed in FP32).  Needs the net
+ * workspace of the config: attach a net with hqmc_set_preconditioner first
+ * (HQMC_EINVAL otherwise).  Allocates nothing. */
 HQMC_API int hqmc_net_apply(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* r, void* z,
                             void* stream);
 /* One Adam step (lr; betas 0.9, 0.999) on loss = ||K(theta) phi - x||^2 / ||x||^2
  * for one (theta, phi, x) triple with x = (M^dagger M)^{-1} phi; *loss_host
- * (nullable) receives the loss before the step (then the call synchronises). */
+ * (nullable) receives the loss before the step (then the call synchronises).
+ * Like hqmc_net_apply it needs the config's net workspace and allocates nothing. */
 HQMC_API int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* phi,
                                  const void* x, double lr, double* loss_host, void* stream);
-/* Attaches (or with NULL detaches) the net used by HQMC_SOLVER_LEARNED. */
+/* Attaches (or with NULL detaches) the net used by HQMC_SOLVER_LEARNED.  The
+ * first attach on a config allocates the net workspace (activation and gradient
+ * fields, 5 + 32 complex-float channels per site, about 300 B per site), which the
+ * config keeps until hqmc_free_config; make this call before any stream capture.
+ * The net must belong to the config's device.  Errors: HQMC_EINVAL, HQMC_ENOMEM. */
 HQMC_API int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net);
 
 /* ---- instrumentation ---------------------------------------------------- */

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "status.h"
+
 namespace hqmc {
 
 template <class R> struct CT;
@@ -270,14 +272,7 @@ struct CgState {
   double rr_rec;     // preconditioned CG: last recursive <r,r> (rr[] holds <r, Otilde^{-1} r> there)
 };
 
-// CG_REC_CONVERGED: the recursive residual met tol; the true residual still has
-// to be checked.  CG_CONVERGED: the true FP64 residual met tol.
-// CG_STAGNATED (mixed solver): eight reliable updates cut the true residual by
-// less than 2x, i.e. FP32 rounding stalls the recurrence on this field.  (Plain
-// CG on these ill-conditioned fields may gain less than 10x in 200 iterations,
-// so a tighter test would abandon FP32 on healthy solves.)
-enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONFINITE = 4, CG_REC_CONVERGED = 5,
-       CG_STAGNATED = 6 };
+// CG_* outcome codes: status.h.
 
 // Gates of the kernels that close a loop body: run always, only after the
 // recursive residual converged, or whenever the solve is still active.

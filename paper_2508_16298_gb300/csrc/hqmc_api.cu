@@ -90,12 +90,15 @@ struct hqmc_config {
   double *part_mdagm = nullptr, *part_ew = nullptr, *part_resid = nullptr, *part_act = nullptr;
   double *terms = nullptr, *report = nullptr;
   CgState* st = nullptr;
+  int* dev_err = nullptr;    // device error word: 1 after a bounded device-side wait gave up
+  int* dev_err_h = nullptr;  // its pinned host mirror (read with the CG state)
   // pinned host mirrors
   CgState* st_h = nullptr;
   double* terms_h = nullptr;
   double* report_h = nullptr;
 
-  // learned preconditioner: attached net and its lazily allocated workspace
+  // learned preconditioner: attached net and its workspace (allocated when a net
+  // is first attached with hqmc_set_preconditioner, kept until the config is freed)
   struct hqmc_net* net = nullptr;
   float2* net_h[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // activations (1, 16, 16, 16, 1 channels)
   float2* net_d[2] = {nullptr, nullptr};                               // back-propagated gradients (16 channels)
@@ -175,6 +178,7 @@ void release(hqmc_config* cfg) {
   if (cfg->st_h) cudaFreeHost(cfg->st_h);
   if (cfg->terms_h) cudaFreeHost(cfg->terms_h);
   if (cfg->report_h) cudaFreeHost(cfg->report_h);
+  if (cfg->dev_err_h) cudaFreeHost(cfg->dev_err_h);
   for (auto& tc : cfg->timers)
     for (auto& pr : tc.pairs) {
       cudaEventDestroy(pr.first);
@@ -256,6 +260,7 @@ MdagmArgs<R> mdagm_args(hqmc_config* cfg) {
   a.th32 = cfg->th32;
   a.t1 = cfg->t1;
   a.t2 = cfg->t2;
+  a.err = cfg->dev_err;
   return a;
 }
 
@@ -359,6 +364,7 @@ int cg_iteration(hqmc_config* cfg, C2<R>* r, C2<R>* const pbuf[2], C2<R>* q, con
 int read_state(hqmc_config* cfg, cudaStream_t s) {
   CK(cudaMemcpyAsync(cfg->st_h, cfg->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(cfg->report_h, cfg->report, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cfg->dev_err_h, cfg->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return HQMC_OK;
 }
@@ -390,8 +396,13 @@ struct hqmc_net {
 
 namespace {
 
+// Allocates the net's activation and gradient fields on the config (once).  Called
+// only from hqmc_set_preconditioner, so that no solve, apply or training step
+// allocates device memory.
+bool net_ready(const hqmc_config* cfg) { return cfg->net_scal != nullptr; }  // the last field allocated
+
 int net_workspace(hqmc_config* cfg) {
-  if (cfg->net_h[0]) return HQMC_OK;
+  if (net_ready(cfg)) return HQMC_OK;
   const size_t n = cfg->n;
   const int ch[5] = {1, kNetCh, kNetCh, kNetCh, 1};
   for (int l = 0; l < 5; ++l) RET(dalloc(cfg, &cfg->net_h[l], n * ch[l]));
@@ -565,7 +576,6 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
     // the start of the mixed recurrence, so a kept candidate costs no FP64 residual
     // beyond the one any solve starts with; a rejected one restores x and starts again.
     solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
-    RET(net_workspace(cfg));
     LK(1, launch_net_convert(x, cfg->xh32, 1, 1.0, cfg->n, s));  // x as float (xh32 is free until the loop)
     {
       MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
@@ -628,7 +638,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
       continue;
     }
     // MAXIT, NONFINITE, or a breakdown of the FP64 recurrence: report the true residual of x
-    status = st.done == CG_MAXIT ? HQMC_ENOTCONV : st.done == CG_BREAKDOWN ? HQMC_EBREAKDOWN : HQMC_ENONFINITE;
+    status = solve_status(st.done, *cfg->dev_err_h != 0);
     if (solver_fp32(cur)) LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
     RET(residual(cfg, phi, x, cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s));
     RET(read_state(cfg, s));
@@ -643,6 +653,11 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   const double rr_rec = (pc && st.k > st.seg_start) ? st.rr_rec : st.rr[st.k & 1];
   inf.recursive_residual = st.bb > 0 ? std::sqrt(rr_rec / st.bb) : 0.0;
   if (status == HQMC_OK && !(inf.true_residual <= tol)) status = inf.status = HQMC_ENOTCONV;
+  if (*cfg->dev_err_h) {  // a bounded wait gave up during this solve (or an apply before it)
+    status = inf.status = solve_status(st.done, true);
+    *cfg->dev_err_h = 0;
+    CK(cudaMemsetAsync(cfg->dev_err, 0, sizeof(int), s));
+  }
   if (info) *info = inf;
   return status;
 }
@@ -1211,7 +1226,9 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     if ((rc = dalloc(cfg, &cfg->terms, 8))) break;
     if ((rc = dalloc(cfg, &cfg->report, 2))) break;
     if ((rc = dalloc(cfg, &cfg->st, 1))) break;
+    if ((rc = dalloc(cfg, &cfg->dev_err, 1))) break;
     if (cudaMallocHost(&cfg->st_h, sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&cfg->dev_err_h, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&cfg->terms_h, 8 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&cfg->report_h, 2 * sizeof(double)) != cudaSuccess) {
       rc = fail(cfg, HQMC_ENOMEM, "pinned host allocation failed");
@@ -1223,6 +1240,8 @@ int hqmc_make_config(const hqmc_params* p, hqmc_config** out) {
     }
     cudaMemset(cfg->st, 0, sizeof(CgState));
     cudaMemset(cfg->report, 0, 2 * sizeof(double));
+    cudaMemset(cfg->dev_err, 0, sizeof(int));
+    *cfg->dev_err_h = 0;
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       rc = fail(cfg, HQMC_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
@@ -1328,6 +1347,16 @@ int hqmc_get_precond_shape(const hqmc_config* cfg, int precision, int* tile_slic
   const bool dbl = precision == HQMC_FP64;
   if (tile_slices) *tile_slices = dbl ? cfg->ll64.chunk : cfg->ll32.chunk;
   if (fused) *fused = (dbl ? cfg->fuse_pc64 : cfg->fuse_pc32) && cfg->p.variant != 1 ? 1 : 0;
+  return HQMC_OK;
+}
+
+int hqmc_set_precond_fused(hqmc_config* cfg, int precision, int fused) {
+  if (!cfg || (precision != HQMC_FP64 && precision != HQMC_FP32) || (fused != 0 && fused != 1)) return HQMC_EINVAL;
+  if (fused && cfg->p.variant == 1) return fail(cfg, HQMC_EUNSUPPORTED, "variant 1 keeps the separate update");
+  (precision == HQMC_FP64 ? cfg->fuse_pc64 : cfg->fuse_pc32) = fused;
+  CK(cudaDeviceSynchronize());  // no cached loop graph may still be running
+  for (auto& g : cfg->graphs) cudaGraphExecDestroy(g.exec);  // loop bodies change shape
+  cfg->graphs.clear();
   return HQMC_OK;
 }
 
@@ -1784,7 +1813,7 @@ int batch_solve(hqmc_batch* b, const double2* const* phi, double2* const* x, dou
       BCK(cudaMemsetAsync(x[c], 0, sizeof(double2) * cfg->n, s));
       cfg->report_h[0] = 0.0;
     } else if (st.done != CG_CONVERGED) {
-      status = st.done == CG_MAXIT ? HQMC_ENOTCONV : st.done == CG_BREAKDOWN ? HQMC_EBREAKDOWN : HQMC_ENONFINITE;
+      status = solve_status(st.done, false);  // the batched kernels have no device-side waits
       BRET(residual(cfg, phi[c], x[c], cfg->vscratch, false, FIN_REPORT, tol, maxit, GATE_ALWAYS, s), cfg);
       BRET(read_state(cfg, s), cfg);
     }
@@ -2151,8 +2180,9 @@ int hqmc_net_apply(hqmc_config* cfg, hqmc_net* net, const double* theta, const v
   if (!cfg || !net) return HQMC_EINVAL;
   if (!aligned16(theta) || !aligned16(r) || !aligned16(z)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
   RET(check_device(cfg));
+  if (!net_ready(cfg))
+    return fail(cfg, HQMC_EINVAL, "no net workspace on this config: attach a net with hqmc_set_preconditioner first");
   cudaStream_t s = (cudaStream_t)stream;
-  RET(net_workspace(cfg));
   RET(theta_float(cfg, theta, s));
   return net_forward(cfg, net, (const double2*)r, (double2*)z, s);
 }
@@ -2162,8 +2192,9 @@ int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, co
   if (!cfg || !net || !(lr >= 0)) return HQMC_EINVAL;
   if (!aligned16(theta) || !aligned16(phi) || !aligned16(x)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
   RET(check_device(cfg));
+  if (!net_ready(cfg))
+    return fail(cfg, HQMC_EINVAL, "no net workspace on this config: attach a net with hqmc_set_preconditioner first");
   cudaStream_t s = (cudaStream_t)stream;
-  RET(net_workspace(cfg));
   RET(theta_float(cfg, theta, s));
   RET(net_forward(cfg, net, (const double2*)phi, nullptr, s, false));  // activations h0..h4
   net->hw_valid = 0;  // this step's Adam update changes the device weights
@@ -2206,6 +2237,12 @@ int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, co
 
 int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net) {
   if (!cfg) return HQMC_EINVAL;
+  if (net) {
+    RET(check_device(cfg));
+    if (net->device != cfg->device)
+      return fail(cfg, HQMC_EINVAL, "net belongs to device %d, config to device %d", net->device, cfg->device);
+    RET(net_workspace(cfg));
+  }
   cfg->net = net;
   return HQMC_OK;
 }

@@ -40,6 +40,7 @@ static __device__ __align__(256) double2 g_static_links[2 * kStaticMaxSites];
 std::mutex g_static_mutex;
 double2* g_static_links_dev[kStaticMaxDevices] = {};  // device address per device, once looked up
 size_t g_static_smem_set[kStaticMaxDevices] = {};     // largest dynamic shared memory opted into
+int g_static_major[kStaticMaxDevices] = {};           // compute capability major, once queried (0: not yet)
 
 }  // namespace
 
@@ -48,6 +49,9 @@ extern "C" int hqmc_apply_MdagM_static(const hqmc_params* p, const double* theta
   if (!p || !theta || !x || !y) return HQMC_EINVAL;
   if (((uintptr_t)theta | (uintptr_t)x | (uintptr_t)y) & 15u) return HQMC_EINVAL;
   if (p->L < 4 || (p->L & 1) || p->L > 68 || p->Ntau < 2 || !(p->dtau > 0)) return HQMC_EINVAL;
+  // the link factors are tanh and cosh of dtau * t: a non-finite or non-positive
+  // product would give NaN or a non-physical operator without any other error
+  if (!std::isfinite(p->dtau) || !std::isfinite(p->t) || !(p->dtau * p->t > 0.0)) return HQMC_EINVAL;
   const long long n = (long long)p->L * p->L * p->Ntau;
   if (n > kStaticMaxSites) return HQMC_EUNSUPPORTED;  // beyond the fixed scratch array
   const char* xb = (const char*)x;
@@ -70,6 +74,15 @@ extern "C" int hqmc_apply_MdagM_static(const hqmc_params* p, const double* theta
   double2* links = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_major[dev]) {
+      int major = 0;
+      if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HQMC_ECUDA;
+      }
+      g_static_major[dev] = major;
+    }
+    if (g_static_major[dev] != 10) return HQMC_EUNSUPPORTED;  // the kernels are built for sm_103a only
     if (!g_static_links_dev[dev]) {
       void* addr = nullptr;
       if (cudaGetSymbolAddress(&addr, g_static_links) != cudaSuccess || !addr) {

@@ -57,6 +57,7 @@ struct MdagmArgs {
                            // a batch sets each chain's own block size so sums group sites as in its own launch
   const double* part_rz;   // CGDIR, preconditioned CG: partials of <r, z> (z = Otilde^{-1} r; x/r read z)
   int n_part_rz;
+  int* err;                // set to 1 by a kernel whose bounded device-side wait gave up (NULL: not recorded)
 };
 
 // First step of a CG-direction launch (one warp): read the CG state, decide

@@ -24,8 +24,8 @@
 // (P is Hermitian, so <x, P w> = <P x, w>), one partial per CTA.
 //
 // Waits on the mbarrier are bounded (about one second of %globaltimer); on a
-// timeout the block writes NaN into its outputs, so the solve reports a
-// non-finite residual instead of hanging.
+// timeout the block writes NaN into its outputs and sets the config's device
+// error word, so the solve returns HQMC_ETIMEOUT instead of hanging.
 #include "bulk.cuh"
 #include "strip.cuh"
 
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
     for (int j = tb; j < te; ++j)
       for (int s = threadIdx.x; s < V; s += blockDim.x) a.y[(size_t)j * V + s] = nan2;
     acc = __longlong_as_double(0x7ff8000000000000ll);
+    if (a.err && threadIdx.x == 0) atomicExch(a.err, 1);  // the host reports HQMC_ETIMEOUT
     mbar_wait_bounded(&bar, parity ^ 1);
   }
   if (MODE == MODE_CGDIR) {

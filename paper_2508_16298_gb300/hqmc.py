@@ -35,7 +35,8 @@ TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE, TIMER_MDAGM32, TIMER_PRECOND = 0, 1, 
 # Every function declared in include/hqmc.h.
 EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_error", "hqmc_num_sites",
            "hqmc_launch_count", "hqmc_get_launch_shape",
-           "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_apply_precond", "hqmc_get_precond", "hqmc_get_precond_shape", "hqmc_cg_solve",
+           "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_apply_precond", "hqmc_get_precond", "hqmc_get_precond_shape",
+           "hqmc_set_precond_fused", "hqmc_cg_solve",
            "hqmc_estimate",
            "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
@@ -87,6 +88,7 @@ _sig = {
     "hqmc_apply_precond": ([_vp, _vp, _vp, _i, _vp], _i),
     "hqmc_get_precond_shape": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                                ctypes.c_int),
+    "hqmc_set_precond_fused": ([_vp, _i, _i], _i),
     "hqmc_get_precond": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     "hqmc_cg_solve": ([_vp, _vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
@@ -274,6 +276,11 @@ def get_precond_shape(cfg: Config, precision: int = FP32) -> dict:
     tc, fused = _i(), _i()
     cfg.check(_lib.hqmc_get_precond_shape(cfg.handle, precision, ctypes.byref(tc), ctypes.byref(fused)))
     return {"tile_slices": tc.value, "fused": bool(fused.value)}
+
+
+def set_precond_fused(cfg: Config, fused: bool, precision: int = FP32):
+    """Force the fused (True) or separate (False) preconditioned CG update for one precision."""
+    cfg.check(_lib.hqmc_set_precond_fused(cfg.handle, precision, int(fused)))
 
 
 def _solver(s) -> int:

@@ -48,6 +48,7 @@ def test_net_forward_matches_reference(hq, L, N):
     with hq.Config(L, N) as cfg:
         k = hq.Net(seed=0)
         k.set_weights(w)
+        hq.set_preconditioner(cfg, k)  # allocates the config's net workspace
         z = k.apply(cfg, cuda(th), cuda(r)).cpu().numpy()
         k.close()
     assert rel(z, ref) < 1e-5
@@ -65,6 +66,7 @@ def test_net_is_gauge_covariant(hq):
     with hq.Config(L, N) as cfg:
         k = hq.Net(seed=0)
         k.set_weights(random_flat(7))
+        hq.set_preconditioner(cfg, k)
         a = k.apply(cfg, cuda(thg), cuda(D * r)).cpu().numpy()
         b = D * k.apply(cfg, cuda(th), cuda(r)).cpu().numpy()
         k.close()
@@ -83,6 +85,7 @@ def test_first_adam_step_follows_the_reference_gradient(hq):
     with hq.Config(L, N) as cfg:
         k = hq.Net(seed=0)
         k.set_weights(w)
+        hq.set_preconditioner(cfg, k)
         loss = k.train_step(cfg, cuda(th), cuda(phi), cuda(x), lr=1e-3)
         w1 = k.get_weights()
         k.close()
@@ -101,6 +104,7 @@ def test_training_lowers_the_loss_and_helps_the_solver(hq):
     lat = oracle.Lattice(L, N)
     with hq.Config(L, N) as cfg:
         k = hq.Net(seed=1)
+        hq.set_preconditioner(cfg, k)
         triples = []
         for s in range(6):
             th = cuda(inputs.theta_ordered(L, N, 20 + s, tau_walk=0.0))
@@ -112,7 +116,6 @@ def test_training_lowers_the_loss_and_helps_the_solver(hq):
             for th, phi, X in triples:
                 losses.append(k.train_step(cfg, th, phi, X, lr=3e-3))
         assert np.mean(losses[-6:]) < 0.5 * np.mean(losses[:6])
-        hq.set_preconditioner(cfg, k)
         th = cuda(inputs.theta_ordered(L, N, 99, tau_walk=0.0))
         phi = hq.apply_M(cfg, th, cuda(inputs.complex_gaussian(L, N, 98)), dagger=True)
         Xl, il = hq.cg_solve(cfg, th, phi, tol=1e-8, solver="learned")
@@ -124,3 +127,32 @@ def test_training_lowers_the_loss_and_helps_the_solver(hq):
     r = phi.cpu().numpy() - oracle.apply_MdagM(lat, th.cpu().numpy(), Xl.cpu().numpy())
     assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(phi.cpu().numpy())
     print("learned iterations", il["iterations"], "mixed iterations", ip["iterations"])
+
+
+def test_net_workspace_comes_from_the_attach_call(hq):
+    """hqmc_set_preconditioner allocates the net workspace; without it the net calls
+    refuse (HQMC_EINVAL), and with it neither a net apply, a training step nor a
+    learned solve allocates device memory."""
+    L, N = 8, 16
+    th = cuda(inputs.theta_hot(L, N, 12))
+    r = cuda(inputs.complex_gaussian(L, N, 13))
+    with hq.Config(L, N) as cfg:
+        k = hq.Net(seed=0)
+        with pytest.raises(hq.HQMCError) as e:
+            k.apply(cfg, th, r)
+        assert e.value.status == hq.EINVAL
+        hq.set_preconditioner(cfg, k)
+        phi = hq.apply_M(cfg, th, r, dagger=True)
+        X, _ = hq.cg_solve(cfg, th, phi, tol=1e-10)
+        k.apply(cfg, th, r)  # warm-up: graphs, events
+        hq.cg_solve(cfg, th, phi, tol=1e-8, solver="learned")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            k.apply(cfg, th, r)
+            k.train_step(cfg, th, phi, X, lr=1e-4)
+            hq.cg_solve(cfg, th, phi, tol=1e-8, solver="learned")
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        hq.set_preconditioner(cfg, None)
+        k.close()
