@@ -6,12 +6,18 @@ seeded synthetic gauge field; the chain continues from step to step.
 
 Default workload (learned + mixed precision against plain FP64): L = 66,
 Ntau = 660 (2,874,960 sites), dtau = 0.1, t = 1, J = 1, compact action, CG to a
-true FP64 residual of 1e-8, 20 leapfrog steps of dt = 0.0005 * sqrt(138240 /
-sites).  Before timing, the chain runs 16 mixed-precision trajectories and after
-each forms one (theta, phi, x) triple; the net is trained on them (Adam, 12
-epochs).  The timed steps use the learned solver; the same chain state is then
-advanced with plain FP64 CG (same draws, dt, N_lf, tolerance) for the
-comparison, and the fused M^dagger M apply is timed alone with L2 flushed.
+true FP64 residual of 1e-8, 20 leapfrog steps.  Untimed set-up: from the cold
+start (pi flux + N(0, 0.3^2) per bond, tau-independent, random gauge
+transformation) the chain is thermalised with the preconditioned mixed solver
+for up to 400 trajectories (200 s) while dt follows the acceptance (grown x1.25 after 4
+accepted trajectories in a row, shrunk x0.8 when 2 or fewer of 4 were accepted);
+dt is then frozen where <dH> (~ dt^4) of the last 40 trajectories
+predicts <dH> = 0.1, i.e. an acceptance near 0.8.  Then 8 more trajectories give
+32 (theta, phi, x) triples (4 sources each) and the net takes 8 Adam epochs over
+them.  The timed steps use the learned solver; the same chain state is then
+advanced with plain FP64 CG and with the factor arms (pcg64, mixed, pmixed) on
+the same draws, dt, N_lf and tolerance, and the fused M^dagger M apply is timed
+alone with L2 flushed.
 
 Workload hmc_fp64_L24_Nt240 (plain FP64 GPU HMC): L = 24, Ntau = 240 (138,240
 sites), CG to 1e-8, 20 leapfrog steps of dt = 0.0005.  Start (inputs.theta_ordered with tau_walk=0):
@@ -63,13 +69,16 @@ WORKLOADS["batched_32chains_L12-24"] = dict(L=24, Ntau=240, dtau=0.1, t=1.0, J=1
                                             solver="cg64", seed=100, start="cold", batched=True)
 # the same batch with the tau-line preconditioner in the batched CG (FP64)
 WORKLOADS["batched_32chains_L12-24_pcg64"] = dict(WORKLOADS["batched_32chains_L12-24"], solver="pcg64")
-# learned + mixed precision at L = 66, Ntau = 660 against plain FP64 on the same chain state: the net is
-# trained (untimed) on (theta, phi, x) triples the sampler produces at this size; dt keeps |dH| ~ V dt^2
-# as at L = 24
-WORKLOADS["hmc_learned_fp32_L66_Nt660"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, J=1.0, nsteps=20,
-                                               dt=round(0.0005 * (138240 / 2874960) ** 0.5, 7), tol=1e-8,
-                                               solver="plearned", seed=1, start="cold", compare="cg64",
-                                               triples=16, epochs=12, lr=1e-3)
+# learned + mixed precision at L = 66, Ntau = 660 against plain FP64 on the same chain state.  Untimed
+# set-up: from the cold start the chain is thermalised with the preconditioned mixed solver while dt is
+# adapted to the acceptance (the Methods tune dt adaptively); dt is then frozen.  The net is trained on
+# (theta, phi, x) triples the sampler produces at this size.  The timed steps use that dt.
+WORKLOADS["hmc_learned_fp32_L66_Nt660"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, J=1.0, nsteps=20, dt=2e-4,
+                                               tol=1e-8, solver="plearned", seed=1, start="cold",
+                                               therm=400, therm_s=200.0,
+                                               compare="cg64", compare_steps=5, factors=("pcg64", "mixed", "pmixed", "flearned"),
+                                               factor_steps=3, triple_trajs=8, rhs_per_traj=4, epochs=8,
+                                               lr=1e-3)
 # stochastic estimation (Methods): 40 CN(0,1) vectors on one field, M^{-1} xi by preconditioned mixed CG
 WORKLOADS["estimate_L66_Nt660_40rv"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, J=1.0, nsteps=0, dt=0.0, tol=1e-8,
                                             solver="pmixed", seed=1, start="cold", estimate=True, nrv=40)
@@ -264,6 +273,8 @@ SOLVER_TEXT = {
     "learned": "learned: net-corrected initial guess (kept if its FP64 residual is below the FP32 residual of the guess it corrects), then the mixed solver",
     "plearned": "plearned: net-corrected initial guess (kept if its FP64 residual is below the FP32 residual of the guess it corrects), then the mixed "
                 "solver preconditioned with the tau-line preconditioner (FP32)",
+    "flearned": "flearned: net-corrected initial guess, then flexible CG (Polak-Ribiere beta) with the net as preconditioner "
+                "every iteration, FP32 recurrence with FP64 reliable updates, tau-line pmixed as the fallback",
 }
 
 
@@ -276,7 +287,10 @@ def config_of(wl_name, wl):
                                  "J*dtau/2) + random gauge transformation",
                       "cold": "pi-flux + N(0, 0.3^2) per bond, tau-independent, + random gauge transformation"}
                      [wl["start"]],
-            "n_leapfrog": wl["nsteps"], "dt": wl["dt"], "cg_tol": wl["tol"],
+            "n_leapfrog": wl["nsteps"],
+            "dt": (f"adapted to the acceptance during {wl['therm']} untimed thermalisation trajectories from "
+                   f"{wl['dt']}, then frozen (value in the line's dt)") if wl.get("therm") else wl["dt"],
+            "cg_tol": wl["tol"],
             "solver": SOLVER_TEXT[wl["solver"]],
             "l2": "flushed between timed steps (512 MiB write; step times exclude the flush)"}
 
@@ -290,36 +304,117 @@ def kernel_name(shape, prec):
     return f"mdagm_kernel<{prec}, CG direction, mb={-v}> (cluster {shape['cluster']})"
 
 
-def train_net(hqmc, inputs, cfg, wl, theta, seed, dev):
-    """Untimed set-up of the learned solver: the chain runs `triples` mixed-precision
-    trajectories; after each, phi = M^dagger R with a fresh R and x = (M^dagger M)^{-1} phi
-    (FP64 residual 1e-8) form one training triple; the net then takes `epochs` Adam
-    passes over them.  Returns the net and a short report."""
+THERM_COUNTER = 10 ** 5   # Philox trajectory counters of the thermalisation
+TRIPLE_COUNTER = 10 ** 6  # ... of the trajectories that produce training triples
+
+
+def thermalize(hqmc, cfg, theta, wl, seed):
+    """Untimed set-up: from the start field, trajectories with the preconditioned mixed
+    solver while dt follows the acceptance (the Methods tune dt adaptively): after every
+    4 trajectories dt grows by 1.25 if all 4 were accepted and shrinks by 0.8 if 2 or
+    fewer were, which holds the acceptance near 0.75-0.9.  Stops after `therm`
+    trajectories or `therm_s` seconds; the last dt is the production dt.  Returns
+    (dt, report) with the bosonic action S_B and the CG iterations over the run, so
+    that their levelling off can be read."""
+    dt = wl["dt"]
+    rows, window = [], []
+    t0 = time.perf_counter()
+    k = 0
+    while k < wl["therm"] and time.perf_counter() - t0 < wl["therm_s"]:
+        sb = hqmc.action_terms(cfg, theta)[0]
+        inf = hqmc.trajectory(cfg, theta, seed=seed, traj_counter=THERM_COUNTER + k, nsteps=wl["nsteps"], dt=dt,
+                              tol=wl["tol"], solver="pmixed")
+        rows.append((dt, inf["accepted"], inf["cg_iterations"], sb, inf["dH"]))
+        window.append(inf["accepted"])
+        k += 1
+        if len(window) == 4:
+            acc = sum(window)
+            dt = dt * 1.25 if acc == 4 else dt * 0.8 if acc <= 2 else dt
+            window = []
+    n = len(rows)
+    tenth = max(1, n // 10)
+    last = rows[-min(n, 40):]
+    # production dt: at fixed N_lf the leapfrog's <dH> grows like dt^4; the last 40
+    # trajectories, each rescaled to the controller's final dt, estimate <dH> there,
+    # and dt is set where <dH> = 0.1 (acceptance erfc(sqrt(<dH>)/2) = 0.82), within
+    # [0.7, 1.15] x the final dt
+    m = statistics.mean(r[4] * (dt / r[0]) ** 4 for r in last)
+    dt_prod = dt * min(1.15, max(0.7, (0.1 / max(m, 1e-3)) ** 0.25))
+    report = {"trajectories": n, "seconds": round(time.perf_counter() - t0, 1), "solver": "pmixed",
+              "dt_first": rows[0][0], "dt_controller_final": dt, "mean_dH_last_40_at_that_dt": m,
+              "dt_production": dt_prod,
+              "rule": "every 4 trajectories: dt x1.25 if 4 accepted, x0.8 if <= 2 accepted; production dt from "
+                      "<dH> ~ dt^4 over the last 40, aiming at <dH> = 0.1",
+              "S_B_per_bond": {"first": rows[0][3] / (2 * cfg.n_sites),
+                               "mean_prev_tenth": statistics.mean(r[3] for r in rows[-2 * tenth:-tenth]) / (2 * cfg.n_sites)
+                               if n >= 2 * tenth + 1 else None,
+                               "mean_last_tenth": statistics.mean(r[3] for r in rows[-tenth:]) / (2 * cfg.n_sites)},
+              "cg_iterations_per_traj": {"first_tenth": statistics.mean(r[2] for r in rows[:tenth]),
+                                         "prev_tenth": statistics.mean(r[2] for r in rows[-2 * tenth:-tenth])
+                                         if n >= 2 * tenth + 1 else None,
+                                         "last_tenth": statistics.mean(r[2] for r in rows[-tenth:])},
+              "acceptance_last_40": statistics.mean(r[1] for r in last)}
+    return dt_prod, report
+
+
+def train_net(hqmc, inputs, cfg, wl, theta, dt, seed, dev):
+    """Untimed set-up of the learned solver: `triple_trajs` trajectories of the chain at the
+    production dt; after each, `rhs_per_traj` sources phi = M^dagger R with fresh Gaussian R
+    and x = (M^dagger M)^{-1} phi (preconditioned mixed CG, FP64 residual 1e-8) form
+    training triples (theta, phi, x).  The net then takes `epochs` Adam passes over them.
+    Returns the net and a report with the loss per epoch."""
     import torch
     L, N = wl["L"], wl["Ntau"]
-    kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver="pmixed")
+    kw = dict(nsteps=wl["nsteps"], dt=dt, tol=wl["tol"], solver="pmixed")
     trips = []
     t0 = time.perf_counter()
-    for k in range(wl["triples"]):
-        hqmc.trajectory(cfg, theta, seed=seed, traj_counter=10 ** 6 + k, **kw)
-        R = torch.from_numpy(inputs.complex_gaussian(L, N, seed * 7919 + k)).to(dev)
-        phi = hqmc.apply_M(cfg, theta, R, dagger=True)
-        x, _ = hqmc.cg_solve(cfg, theta, phi, tol=wl["tol"], solver="pmixed")
-        trips.append((theta.clone(), phi, x))
+    for k in range(wl["triple_trajs"]):
+        hqmc.trajectory(cfg, theta, seed=seed, traj_counter=TRIPLE_COUNTER + k, **kw)
+        th = theta.clone()
+        for m in range(wl["rhs_per_traj"]):
+            R = torch.from_numpy(inputs.complex_gaussian(L, N, seed * 7919 + 97 * k + m)).to(dev)
+            phi = hqmc.apply_M(cfg, th, R, dagger=True)
+            x, _ = hqmc.cg_solve(cfg, th, phi, tol=wl["tol"], solver="pmixed")
+            trips.append((th, phi, x))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     net = hqmc.Net(seed=seed)
     hqmc.set_preconditioner(cfg, net)  # allocates the config's net workspace
-    first = last = None
+    curve = []
     for ep in range(wl["epochs"]):
         losses = [net.train_step(cfg, th, ph, x, lr=wl["lr"]) for th, ph, x in trips]
-        first = statistics.mean(losses) if first is None else first
-        last = statistics.mean(losses)
+        curve.append(round(statistics.mean(losses), 4))
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    return net, {"triples": len(trips), "epochs": wl["epochs"], "sampler_s": round(t1 - t0, 2),
-                 "train_s": round(t2 - t1, 2), "loss_first_epoch": round(first, 4), "loss_last_epoch": round(last, 4),
-                 "loss": "||K(theta) phi - x||^2 / ||x||^2"}
+    return net, {"triples": len(trips), "trajectories": wl["triple_trajs"], "sources_per_trajectory": wl["rhs_per_traj"],
+                 "epochs": wl["epochs"], "sampler_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2),
+                 "loss_per_epoch": curve, "loss": "||K(theta) phi - x||^2 / ||x||^2"}
+
+
+def same_draws_arm(hqmc, cfg, theta_start, seed, first_counter, n, solver, wl, dt, flush, stream):
+    """The chain advanced from theta_start with `solver` on the draws of the first n timed
+    steps (counters first_counter ...), dt, N_lf and tolerance unchanged; one untimed
+    single-solve trajectory first builds the solver's CUDA graph.  Returns per-step data."""
+    import torch
+    th = theta_start.clone()
+    kw = dict(nsteps=wl["nsteps"], dt=dt, tol=wl["tol"], solver=solver)
+    hqmc.trajectory(cfg, th.clone(), seed=seed, traj_counter=first_counter, **dict(kw, nsteps=0))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    infos = []
+    for k in range(n):
+        flush.zero_()
+        ev[k][0].record(stream)
+        infos.append(hqmc.trajectory(cfg, th, seed=seed, traj_counter=first_counter + k, **kw))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"solver": solver, "traj_per_s": n / (sum(ms) / 1e3), "steps": n,
+            "acceptance": statistics.mean(i["accepted"] for i in infos),
+            "accepted": [i["accepted"] for i in infos],
+            "cg_iterations_per_traj": statistics.mean(i["cg_iterations"] for i in infos),
+            "dH": [round(i["dH"], 6) for i in infos],
+            "max_true_residual": max(i["max_true_residual"] for i in infos),
+            "step_ms": [round(m, 3) for m in ms]}
 
 
 def time_apply(hqmc, cfg, theta, x, flush, timer, reps=20):
@@ -354,11 +449,15 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     seed = rank_seed(wl["seed"], rank)
     theta = torch.from_numpy(start_theta(wl, seed)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    kw = dict(nsteps=wl["nsteps"], dt=wl["dt"], tol=wl["tol"], solver=wl["solver"])
+    therm = None
+    dt = wl["dt"]
+    if wl.get("therm"):
+        dt, therm = thermalize(hqmc, cfg, theta, wl, seed)
+    kw = dict(nsteps=wl["nsteps"], dt=dt, tol=wl["tol"], solver=wl["solver"])
     learned = None
     net = None
     if wl["solver"] in ("learned", "plearned"):
-        net, learned = train_net(hqmc, inputs, cfg, wl, theta, seed, dev)
+        net, learned = train_net(hqmc, inputs, cfg, wl, theta, dt, seed, dev)
 
     for k in range(args.warmup):
         hqmc.trajectory(cfg, theta, seed=seed, traj_counter=k, **kw)
@@ -422,30 +521,32 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     e2e_s = max_over_ranks(e2e_s, world, dev)
     e2e_value = job_rate(e2e_steps, world, e2e_s)
 
-    # ---- plain FP64 on the same chain state (same draws, dt, N_lf, tolerance) -----
-    compare = None
+    # ---- other solvers on the same chain state and draws (dt, N_lf, tolerance unchanged) -----
+    compare, factors = None, None
     if wl.get("compare"):
-        kw64 = dict(kw, solver=wl["compare"])
-        th64 = theta_start.clone()
-        hqmc.trajectory(cfg, th64.clone(), seed=seed, traj_counter=10 ** 7, **kw64)  # warm-up
-        n64 = min(2, args.steps)
-        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
-        inf64 = []
-        for k in range(n64):
-            flush.zero_()
-            ev64[k][0].record(stream)
-            inf64.append(hqmc.trajectory(cfg, th64, seed=seed, traj_counter=args.warmup + k, **kw64))
-            ev64[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms64 = [a.elapsed_time(b) for a, b in ev64]
-        v64 = n64 / (sum(ms64) / 1e3)
-        compare = {"solver": wl["compare"], "traj_per_s": v64, "speedup": (value / world) / v64,
-                   "steps": n64, "same_draws_as_steps": list(range(n64)),
-                   "acceptance": statistics.mean(i["accepted"] for i in inf64),
-                   "cg_iterations_per_traj": statistics.mean(i["cg_iterations"] for i in inf64),
-                   "dH": [round(i["dH"], 6) for i in inf64],
-                   "max_true_residual": max(i["max_true_residual"] for i in inf64),
-                   "step_ms": [round(m, 3) for m in ms64]}
+        n64 = min(wl.get("compare_steps", 5), args.steps)
+        compare = same_draws_arm(hqmc, cfg, theta_start, seed, args.warmup, n64, wl["compare"], wl, dt, flush, stream)
+        ours = sum(step_ms[:n64]) / 1e3
+        compare["speedup_same_draws"] = (sum(compare["step_ms"]) / 1e3) / ours
+        compare["speedup"] = (value / world) / compare["traj_per_s"]
+        compare["same_draws_as_steps"] = list(range(n64))
+        compare["dH_difference_max"] = max(abs(a - b["dH"]) for a, b in zip(compare["dH"], infos[:n64]))
+        compare["same_accept_decisions"] = all(a == b["accepted"] for a, b in zip(compare["accepted"], infos[:n64]))
+    if wl.get("factors"):
+        nf = min(wl.get("factor_steps", 3), args.steps)
+        arms = {sv: same_draws_arm(hqmc, cfg, theta_start, seed, args.warmup, nf, sv, wl, dt, flush, stream)
+                for sv in wl["factors"]}
+        t = {sv: sum(a["step_ms"]) for sv, a in arms.items()}
+        t[wl["solver"]] = sum(step_ms[:nf])
+        factors = {"steps": nf, "ms_same_draws": {k: round(v, 1) for k, v in t.items()},
+                   "its_per_traj": {sv: a["cg_iterations_per_traj"] for sv, a in arms.items()},
+                   "fp32_over_fp64": t["pcg64"] / t["pmixed"] if "pcg64" in t and "pmixed" in t else None,
+                   "precond_gain": t["mixed"] / t["pmixed"] if "mixed" in t and "pmixed" in t else None,
+                   "net_gain": t["pmixed"] / t[wl["solver"]] if "pmixed" in t else None,
+                   "fcg_net_gain": t["pmixed"] / t["flearned"] if "flearned" in t and "pmixed" in t else None,
+                   "definition": "fp32_over_fp64 = t(pcg64)/t(pmixed); precond_gain = t(mixed)/t(pmixed); "
+                                 "net_gain = t(pmixed)/t(" + wl["solver"] + "); fcg_net_gain = t(pmixed)/t(flearned) "
+                                 "(flexible CG, net every iteration); same draws and start state"}
 
     # ---- the fused M^dagger M apply alone, L2 flushed: FP32 against HBM, FP64 against the FP64 rate
     x32 = torch.from_numpy(inputs.complex_gaussian(L, N, 77).astype(np.complex64)).to(dev)
@@ -513,6 +614,9 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
                          "sample": cb["sample"]},
         "clocks": clk,
         "acceptance": statistics.mean(i["accepted"] for i in infos),
+        "acceptance_stderr": (statistics.mean(i["accepted"] for i in infos) *
+                              (1 - statistics.mean(i["accepted"] for i in infos)) / len(infos)) ** 0.5,
+        "dt": dt,
         "cg_iterations_per_traj": its_per_traj,
         "dH": [round(i["dH"], 6) for i in infos],
         "max_true_residual": max(i["max_true_residual"] for i in infos),
@@ -521,6 +625,10 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     }
     if compare:
         line["vs_plain_fp64"] = compare
+    if factors:
+        line["factors"] = factors
+    if therm:
+        line["thermalization"] = therm
     if learned:
         line["learned"] = learned
     print(json.dumps(line), flush=True)
@@ -700,7 +808,7 @@ def run_profile_case(wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)

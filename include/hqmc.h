@@ -77,7 +77,19 @@ enum {
      * from <r, z>; convergence is still judged on ||r|| and the FP64 true residual. */
     HQMC_SOLVER_PCG64 = 3,
     HQMC_SOLVER_PMIXED = 4,
-    HQMC_SOLVER_PLEARNED = 5
+    HQMC_SOLVER_PLEARNED = 5,
+    /* Flexible CG (Notay 2000) with one kept direction, i.e. the Polak-Ribiere
+     * beta_k = Re<z_k, r_k - r_{k-1}> / Re<z_{k-1}, r_{k-1}>, which stays valid
+     * when the preconditioner changes from one iteration to the next: z = K(theta) r
+     * from the attached net on iterations c with c % net_interval == 0 of every
+     * reliable_interval-long segment (hqmc_set_net_interval; default 1, every
+     * iteration) and z = Otilde^{-1} r (tau-line) on the others.  FP32 recurrence
+     * with FP64 reliable updates, after the learned initial guess of
+     * HQMC_SOLVER_LEARNED.  If the net makes Re<r, z> or <p, O p> non-positive or
+     * stalls the recurrence, the solve continues as HQMC_SOLVER_PMIXED from the
+     * current x (info.fcg_fallback = 1).  The FP64 true residual judges
+     * convergence.  Not a method of the paper (spec extension). */
+    HQMC_SOLVER_FLEARNED = 6
 };
 
 /* Model and lattice (Results "Model"; Methods "Model and partition function"). */
@@ -115,6 +127,7 @@ typedef struct hqmc_solve_info {
                                   rest of the solve to the FP64 recurrence */
     int net_guess_used;        /* learned solver: 1 if the net's correction of the initial
                                   guess lowered the residual and was kept */
+    int fcg_fallback;          /* flexible CG: 1 if it handed the solve to HQMC_SOLVER_PMIXED */
 } hqmc_solve_info;
 
 typedef struct hqmc_traj_info {
@@ -385,6 +398,11 @@ HQMC_API int hqmc_net_apply(hqmc_config* cfg, hqmc_net* net, const double* theta
  * Like hqmc_net_apply it needs the config's net workspace and allocates nothing. */
 HQMC_API int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, const void* phi,
                                  const void* x, double lr, double* loss_host, void* stream);
+/* Flexible CG (HQMC_SOLVER_FLEARNED): the net preconditions iterations c with
+ * c % k == 0 of each reliable-update segment, the tau-line preconditioner the
+ * others (k >= 1; 1 = every iteration).  Host-only; HQMC_EINVAL for k < 1. */
+HQMC_API int hqmc_set_net_interval(hqmc_config* cfg, int k);
+
 /* Attaches (or with NULL detaches) the net used by HQMC_SOLVER_LEARNED.  The
  * first attach on a config allocates the net workspace (activation and gradient
  * fields, 5 + 32 complex-float channels per site, about 300 B per site), which the

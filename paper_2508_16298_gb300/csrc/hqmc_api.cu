@@ -38,6 +38,7 @@ struct SolveGraph {
   const void* phi;
   void* x;
   int solver;
+  long long net_version;  // flexible CG: the net weights captured by value in the body
   int body_kernels;  // kernels per body, including the loop-condition kernel
   cudaGraphExec_t exec;
 };
@@ -103,6 +104,9 @@ struct hqmc_config {
   float2* net_h[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // activations (1, 16, 16, 16, 1 channels)
   float2* net_d[2] = {nullptr, nullptr};                               // back-propagated gradients (16 channels)
   double* net_part = nullptr;                                          // weight-gradient and loss partials
+  float2* r_old32 = nullptr;                                           // flexible CG: residual before the update
+  double *part_fz = nullptr, *part_fx = nullptr;                       // flexible CG: <r, z>, <r_old, z> partials
+  int net_interval = 1;                                                // flexible CG: net on iterations c % k == 0
   double* net_scal = nullptr;                                          // device scalars (norms)
 
   int timing = 0;
@@ -287,8 +291,14 @@ int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, 
 
 // Solver ids: CG64 / MIXED / LEARNED, and the same three with the tau-line
 // preconditioner (PCG64 / PMIXED / PLEARNED).
+// HQMC_SOLVER_FLEARNED: flexible CG with the net (every net_interval-th iteration)
+// and the tau-line preconditioner (the others), after the learned initial guess.
+bool solver_fcg(int solver) { return solver == HQMC_SOLVER_FLEARNED; }
 bool solver_pc(int solver) { return solver >= HQMC_SOLVER_PCG64; }
-int solver_base(int solver) { return solver_pc(solver) ? solver - HQMC_SOLVER_PCG64 : solver; }
+int solver_base(int solver) {
+  if (solver_fcg(solver)) return HQMC_SOLVER_LEARNED;
+  return solver_pc(solver) ? solver - HQMC_SOLVER_PCG64 : solver;
+}
 bool solver_fp32(int solver) { return solver_base(solver) != HQMC_SOLVER_CG64; }
 
 // z = Otilde^{-1} r and the partials of <r, z>, gated on a running solve
@@ -374,7 +384,7 @@ int read_state(hqmc_config* cfg, cudaStream_t s) {
 
 constexpr int kNetLayers = 4;
 constexpr int kNetCh = 16;
-constexpr int kNetChunks = 64;  // site chunks of the weight-gradient reduction
+constexpr int kNetChunks = 304;  // site chunks of the weight-gradient reduction (one block each; 2 per SM)
 
 }  // namespace
 
@@ -390,6 +400,7 @@ struct hqmc_net {
   void* wt = nullptr;      // BF16 adjoint weights (backward stencil)
   std::vector<float> hw;   // host copy of the BF16 weights as floats (inference launches take them by value)
   int hw_valid = 0;        // cleared when a training step changes the device weights
+  long long version = 0;   // bumped whenever the weights change (captured solve loops hold them by value)
   int steps = 0;
   int device = 0;
 };
@@ -409,6 +420,9 @@ int net_workspace(hqmc_config* cfg) {
   RET(dalloc(cfg, &cfg->net_d[0], n * kNetCh));
   RET(dalloc(cfg, &cfg->net_d[1], n * kNetCh));
   RET(dalloc(cfg, &cfg->net_part, (size_t)kNetChunks * 7 * kNetCh * kNetCh + 4096));
+  RET(dalloc(cfg, &cfg->r_old32, n));
+  RET(dalloc(cfg, &cfg->part_fz, (size_t)cfg->act_grid));
+  RET(dalloc(cfg, &cfg->part_fx, (size_t)cfg->act_grid));
   RET(dalloc(cfg, &cfg->net_scal, 8));
   return HQMC_OK;
 }
@@ -417,27 +431,90 @@ int net_workspace(hqmc_config* cfg) {
 // Inference layers take the weights by value from the host copy (refreshed
 // from the device after training steps); the training forward pass reads the
 // device weights that its Adam steps update.
+// Host copy of the BF16 weights as floats, refreshed from the device after
+// training steps (a synchronous copy: never called inside a stream capture).
+int net_host_weights(hqmc_config* cfg, hqmc_net* net, cudaStream_t s) {
+  if (net->hw_valid) return HQMC_OK;
+  std::vector<__nv_bfloat16> hb(net->total);
+  CK(cudaMemcpyAsync(hb.data(), net->wb, net->total * sizeof(__nv_bfloat16), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  net->hw.resize(net->total);
+  for (int e = 0; e < net->total; ++e) net->hw[e] = __bfloat162float(hb[e]);
+  net->hw_valid = 1;
+  return HQMC_OK;
+}
+
 int net_forward(hqmc_config* cfg, hqmc_net* net, const double2* r, double2* z, cudaStream_t s,
                 bool host_weights = true) {
-  if (host_weights && !net->hw_valid) {
-    std::vector<__nv_bfloat16> hb(net->total);
-    CK(cudaMemcpyAsync(hb.data(), net->wb, net->total * sizeof(__nv_bfloat16), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    net->hw.resize(net->total);
-    for (int e = 0; e < net->total; ++e) net->hw[e] = __bfloat162float(hb[e]);
-    net->hw_valid = 1;
-  }
+  if (host_weights) RET(net_host_weights(cfg, net, s));
   LK(1, launch_net_convert(r, cfg->net_h[0], 1, 1.0, cfg->n, s));
   for (int l = 0; l < kNetLayers; ++l) {
     if (host_weights)
       LK(1, launch_net_layer_host_weights(cfg->g, cfg->th32, net->hw.data() + net->off[l], net->cin[l], net->cout[l],
-                                          cfg->net_h[l], cfg->net_h[l + 1], s));
+                                          cfg->net_h[l], cfg->net_h[l + 1], nullptr, s));
     else
       LK(1, launch_net_layer(cfg->g, cfg->th32, (const char*)net->wb + 2 * (size_t)net->off[l], net->cin[l],
                              net->cout[l], cfg->net_h[l], cfg->net_h[l + 1], s));
   }
   if (z) LK(1, launch_net_convert(cfg->net_h[kNetLayers], z, 0, 1.0, cfg->n, s));
   return HQMC_OK;
+}
+
+// Flexible CG: z = K(theta) r in complex float, the first layer reading r and the
+// last writing z (one channel is the same in every layout); gated on a running
+// solve.  The float theta table must be current and the host weights valid.
+int net_forward32(hqmc_config* cfg, hqmc_net* net, const float2* r, float2* z, cudaStream_t s) {
+  const float2* in = r;
+  for (int l = 0; l < kNetLayers; ++l) {
+    float2* out = l == kNetLayers - 1 ? z : cfg->net_h[l + 1];
+    LK(1, launch_net_layer_host_weights(cfg->g, cfg->th32, net->hw.data() + net->off[l], net->cin[l], net->cout[l],
+                                        in, out, cfg->st, s));
+    in = out;
+  }
+  return HQMC_OK;
+}
+
+// Flexible CG's preconditioner step for the iteration that follows: z = K r (net)
+// or z = Otilde^{-1} r (tau-line), then the partials of Re<r, z> and Re<r_old, z>.
+int fcg_precondition(hqmc_config* cfg, bool use_net, cudaStream_t s) {
+  int slot;
+  RET(timer_begin(cfg, HQMC_TIMER_PRECOND, s, &slot));
+  if (use_net) RET(net_forward32(cfg, cfg->net, cfg->r32, cfg->z32, s));
+  else RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));
+  RET(timer_end(cfg, HQMC_TIMER_PRECOND, s, slot));
+  LK(1, launch_fcg_dots(cfg->n, cfg->r32, cfg->r_old32, cfg->z32, cfg->act_grid, cfg->part_fz, cfg->part_fx, cfg->st, s));
+  return HQMC_OK;
+}
+
+// One flexible-CG iteration c of a mixed loop body (FP32 recurrence, Notay's FCG
+// with one kept direction = Polak-Ribiere beta): p = z + beta p_old and q = O p
+// (the direction kernel, beta from the <r, z> and <r_old, z> partials), r_old = r,
+// x += alpha p, r -= alpha q, then the preconditioner of iteration c + 1 (the net
+// when (c + 1) % net_interval == 0).
+int fcg_iteration(hqmc_config* cfg, int c, cudaStream_t s) {
+  MdagmArgs<float> a = mdagm_args<float, MODE_CGDIR>(cfg);
+  a.U = cfg->U32;
+  a.y = cfg->q32;
+  a.r = cfg->z32;
+  a.part_rz = cfg->part_fz;
+  a.part_cross = cfg->part_fx;
+  a.n_part_rz = cfg->act_grid;
+  a.pbuf[0] = cfg->p32[0];
+  a.pbuf[1] = cfg->p32[1];
+  a.part_in = cfg->part_ew;
+  a.n_part_in = cfg->ew_grid;
+  a.part_out = cfg->part_mdagm;
+  a.st = cfg->st;
+  int slot;
+  RET(timer_begin(cfg, HQMC_TIMER_MDAGM32, s, &slot));
+  LK(1, (launch_fused<float, MODE_CGDIR>(cfg, a, s)));
+  RET(timer_end(cfg, HQMC_TIMER_MDAGM32, s, slot));
+  CK(cudaMemcpyAsync(cfg->r_old32, cfg->r32, sizeof(float2) * cfg->n, cudaMemcpyDeviceToDevice, s));
+  RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
+  LK(1, launch_cg_update<float>(cfg->n, cfg->ew_grid, cfg->xh32, 0, cfg->r32, cfg->p32, cfg->q32, cfg->part_mdagm,
+                                fused_shape<float>(cfg).grid, cfg->part_ew, cfg->st, s));
+  RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
+  return fcg_precondition(cfg, (c + 1) % cfg->net_interval == 0, s);
 }
 
 int theta_float(hqmc_config* cfg, const double* theta, cudaStream_t s) {
@@ -454,6 +531,20 @@ int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, c
   const bool mixed = solver_fp32(solver);
   const bool pc = solver_pc(solver);
   const int iters = mixed ? cfg->reliable : kBodyIters64;
+  if (solver_fcg(solver)) {
+    // flexible CG: the reliable update closes the body and the net preconditions
+    // the new residual (iteration 0 of the next body)
+    int nets = 0;
+    for (int c = 0; c < iters; ++c) {
+      RET(fcg_iteration(cfg, c, s));
+      nets += (c + 1) % cfg->net_interval == 0;
+    }
+    LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, cfg->st, GATE_ACTIVE, s));
+    RET(residual(cfg, phi, x, cfg->r32, true, FIN_RELIABLE, 0.0, 0, GATE_ACTIVE, s));
+    RET(fcg_precondition(cfg, true, s));
+    *nkernels = 3 * iters + 4 * (nets + 1) + (iters - nets) + 3 + 1;
+    return HQMC_OK;
+  }
   // the fused preconditioned update alternates two residual buffers, so an even
   // number of iterations per body leaves r where the body's residual expects it
   const bool fuse = pc && (iters % 2 == 0) && (mixed ? cfg->fuse_pc32 : cfg->fuse_pc64) && cfg->p.variant != 1;
@@ -481,8 +572,9 @@ int enqueue_body(hqmc_config* cfg, int solver, const double2* phi, double2* x, c
 // Builds (or finds) the graph that runs loop bodies under a WHILE node until
 // the CG state leaves RUNNING: the loop condition is decided on the device.
 int get_graph(hqmc_config* cfg, int solver, const double2* phi, double2* x, SolveGraph** out) {
+  const long long ver = solver_fcg(solver) && cfg->net ? cfg->net->version : 0;
   for (auto& g : cfg->graphs)
-    if (g.phi == phi && g.x == x && g.solver == solver) {
+    if (g.phi == phi && g.x == x && g.solver == solver && g.net_version == ver) {
       *out = &g;
       return HQMC_OK;
     }
@@ -530,7 +622,7 @@ int get_graph(hqmc_config* cfg, int solver, const double2* phi, double2* x, Solv
     cudaGraphExecDestroy(cfg->graphs.front().exec);
     cfg->graphs.erase(cfg->graphs.begin());
   }
-  cfg->graphs.push_back(SolveGraph{phi, x, solver, nk + 1, exec});
+  cfg->graphs.push_back(SolveGraph{phi, x, solver, ver, nk + 1, exec});
   *out = &cfg->graphs.back();
   return HQMC_OK;
 }
@@ -575,7 +667,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
     // decides whether the candidate is kept.  The FP64 residual of x1 is computed as
     // the start of the mixed recurrence, so a kept candidate costs no FP64 residual
     // beyond the one any solve starts with; a rejected one restores x and starts again.
-    solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
+    if (!solver_fcg(solver)) solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
     LK(1, launch_net_convert(x, cfg->xh32, 1, 1.0, cfg->n, s));  // x as float (xh32 is free until the loop)
     {
       MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
@@ -605,7 +697,10 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   if (!started)
     RET(residual(cfg, phi, x, mixed ? (void*)cfg->r32 : (void*)cfg->r64, mixed, FIN_START, tol, maxit, GATE_ALWAYS, s));
   if (mixed) CK(cudaMemsetAsync(cfg->xh32, 0, sizeof(float2) * cfg->n, s));
-  if (pc) {
+  if (solver_fcg(solver)) {
+    RET(net_host_weights(cfg, cfg->net, s));  // outside any capture: the loop bodies take them by value
+    RET(fcg_precondition(cfg, true, s));
+  } else if (pc) {
     if (mixed) RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));
     else RET(precondition<double>(cfg, cfg->r64, cfg->z64, cfg->st, s));
   }
@@ -619,6 +714,18 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
       break;
     }
     if (st.done == CG_CONVERGED) break;
+    if ((st.done == CG_BREAKDOWN || st.done == CG_STAGNATED) && solver_fcg(cur)) {
+      // the net made Re<r, z> or <p, O p> non-positive, or stalled the recurrence:
+      // fold in the correction and continue with the tau-line preconditioned mixed
+      // solver from the FP64 residual of x (the fixed-preconditioner fallback)
+      inf.restarts++;
+      inf.fcg_fallback = 1;
+      LK(1, launch_accumulate_correction(cfg->n, x, cfg->xh32, nullptr, GATE_ALWAYS, s));
+      cur = HQMC_SOLVER_PMIXED;
+      RET(residual(cfg, phi, x, cfg->r32, true, FIN_RESTART, tol, maxit, GATE_ALWAYS, s));
+      RET(precondition<float>(cfg, cfg->r32, cfg->z32, cfg->st, s));
+      continue;
+    }
     if ((st.done == CG_BREAKDOWN || st.done == CG_STAGNATED) && solver_fp32(cur)) {
       // <p, O32 p> <= 0 or a stalled residual: FP32 rounding cannot resolve the
       // lowest modes of this field.  Fold in the correction and restart from the
@@ -706,7 +813,7 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
 }
 
 int check_solver(hqmc_config* cfg, int solver) {
-  if (solver < HQMC_SOLVER_CG64 || solver > HQMC_SOLVER_PLEARNED)
+  if (solver < HQMC_SOLVER_CG64 || solver > HQMC_SOLVER_FLEARNED)
     return fail(cfg, HQMC_EINVAL, "unknown solver %d", solver);
   if (solver_base(solver) == HQMC_SOLVER_LEARNED && !cfg->net)
     return fail(cfg, HQMC_EINVAL, "the learned solver needs a net attached with hqmc_set_preconditioner");
@@ -2107,6 +2214,7 @@ int net_upload(hqmc_net* net, const float* host) {
   for (int e = 0; e < net->total; ++e) net->hw[e] = __bfloat162float(hb[e]);
   net->hw_valid = 1;
   net->steps = 0;
+  net->version++;
   return HQMC_OK;
 }
 
@@ -2198,6 +2306,7 @@ int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, co
   RET(theta_float(cfg, theta, s));
   RET(net_forward(cfg, net, (const double2*)phi, nullptr, s, false));  // activations h0..h4
   net->hw_valid = 0;  // this step's Adam update changes the device weights
+  net->version++;
   // ||x||^2 on the device, then the loss and its gradient with respect to h4
   LK(2, launch_action_terms(cfg->g, cfg->bp, theta, nullptr, (const double2*)x, (const double2*)x, cfg->act_grid,
                             cfg->part_act, cfg->terms, s));
@@ -2232,6 +2341,16 @@ int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, co
     for (double v : lp) sum += v;
     *loss_host = sum;
   }
+  return HQMC_OK;
+}
+
+int hqmc_set_net_interval(hqmc_config* cfg, int k) {
+  if (!cfg || k < 1) return HQMC_EINVAL;
+  if (k == cfg->net_interval) return HQMC_OK;
+  cfg->net_interval = k;
+  CK(cudaDeviceSynchronize());  // no cached loop graph may still be running
+  for (auto& g : cfg->graphs) cudaGraphExecDestroy(g.exec);
+  cfg->graphs.clear();
   return HQMC_OK;
 }
 

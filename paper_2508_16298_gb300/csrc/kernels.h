@@ -58,6 +58,7 @@ struct MdagmArgs {
   const double* part_rz;   // CGDIR, preconditioned CG: partials of <r, z> (z = Otilde^{-1} r; x/r read z)
   int n_part_rz;
   int* err;                // set to 1 by a kernel whose bounded device-side wait gave up (NULL: not recorded)
+  const double* part_cross;  // CGDIR, flexible CG: partials of Re<r_old, z> (Polak-Ribiere beta), n_part_rz of them
 };
 
 // First step of a CG-direction launch (one warp): read the CG state, decide
@@ -108,7 +109,9 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
     } else {
       const double rr = head_sum<R>(a.part_in, a.n_part_in);
       const double rz = a.part_rz ? head_sum<R>(a.part_rz, a.n_part_rz) : rr;
-      if (!isfinite(rr) || !isfinite(rz)) {
+      // flexible CG: beta = Re<z_k, r_k - r_{k-1}> / Re<z_{k-1}, r_{k-1}> (Polak-Ribiere)
+      const double cross = a.part_cross ? head_sum<R>(a.part_cross, a.n_part_rz) : 0.0;
+      if (!isfinite(rr) || !isfinite(rz) || !isfinite(cross)) {
         flags = 1;
         new_done = CG_NONFINITE;
       } else if (rr <= st->tol2bb) {
@@ -118,7 +121,7 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
         flags = 1;
         new_done = CG_BREAKDOWN;
       } else {
-        beta = rz / st->rr[(k - 1) & 1];
+        beta = (rz - cross) / st->rr[(k - 1) & 1];
       }
       if (writer && lane == 0) {
         if (!a.part_rz) {
@@ -302,6 +305,11 @@ cudaError_t launch_resid_finalize(const double* part, int n, int mode, double to
                                   double* part_rr_out, int n_rr_out, CgState* st, double* report,
                                   int gate, cudaStream_t s);
 
+// Flexible CG: partials of Re<r, z> and Re<r_old, z> (grid blocks each), skipped
+// unless the solve is running.
+cudaError_t launch_fcg_dots(long long n, const float2* r, const float2* r_old, const float2* z, int grid,
+                            double* part_rz, double* part_cross, const CgState* st, cudaStream_t s);
+
 // x64 += xh32; xh32 = 0 (gated on st->done unless st is NULL).
 cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, const CgState* st, int gate,
                                          cudaStream_t s);
@@ -352,8 +360,9 @@ cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, in
                              float2* out, cudaStream_t s);
 // Inference layer with the weights passed by value from host memory ([7][cout][cin] FP32 values of
 // the BF16 weights): the same arithmetic as launch_net_layer.
+// st (nullable): skip the launch unless the solve is running (flexible CG).
 cudaError_t launch_net_layer_host_weights(const Geo& g, const float2* th32, const float* w, int cin, int cout,
-                                         const float2* in, float2* out, cudaStream_t s);
+                                         const float2* in, float2* out, const CgState* st, cudaStream_t s);
 cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
                              double* partials, int nchunks, cudaStream_t s);
 cudaError_t launch_net_loss(const float2* h, const double2* x, const double* xx, float2* d, double* part, int nblocks,

@@ -198,7 +198,8 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) net_layer_cw_kernel(Geo g, const float2* __restrict__ th32,
                                                            const __grid_constant__ NetLayerW<CIN, COUT> W,
                                                            const float2* __restrict__ in, float2* __restrict__ out,
-                                                           int n) {
+                                                           int n, const CgState* st) {
+  if (st && *(volatile const int*)&st->done != CG_RUNNING) return;  // flexible CG: the solve has stopped
   const int V = g.V, L = g.L, N = g.Ntau;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int tau = i / V, s = i - tau * V, y = s / L, x = s - y * L;
@@ -254,45 +255,104 @@ __global__ void __launch_bounds__(256) net_layer_cw_kernel(Geo g, const float2* 
 
 template <int CIN, int COUT>
 static cudaError_t layer_cw(const Geo& g, const float2* th32, const float* w, const float2* in, float2* out,
-                            int n, int nb, cudaStream_t s) {
+                            int n, int nb, const CgState* st, cudaStream_t s) {
   NetLayerW<CIN, COUT> W;
   for (int mu = 0; mu < 7; ++mu)
     for (int c = 0; c < COUT; ++c)
       for (int cp = 0; cp < CIN; ++cp) W.w[mu][cp][c] = w[(mu * COUT + c) * CIN + cp];
-  net_layer_cw_kernel<CIN, COUT><<<nb, 256, 0, s>>>(g, th32, W, in, out, n);
+  net_layer_cw_kernel<CIN, COUT><<<nb, 256, 0, s>>>(g, th32, W, in, out, n, st);
   return cudaGetLastError();
 }
 
-// Weight gradient: G[mu][c][c'] = sum_x Re(conj(d(x, c)) (T_mu h)(x, c')), one
-// thread per weight entry over a chunk of sites; partials[chunk][entry].
+// Weight gradient: G[mu][c][c'] = sum_x Re(conj(d(x, c)) (T_mu h)(x, c')), a
+// reduction over the sites of seven 16 x 16 (at most) products.  Block b owns a
+// contiguous chunk of sites and walks it in tiles of WG_TILE sites: the tile's
+// d rows are staged in shared memory once, then for each direction mu the
+// transported neighbour rows (T_mu h) are staged and every thread adds the
+// tile's contribution to the weight entry (c, c') it owns (the threads of a warp
+// read one or two d rows, broadcast, and 16 consecutive h entries: no bank
+// conflicts).  Per tile the FP32 sums go into FP64 accumulators, and each
+// block writes one partial per entry: partials[b][mu][c][c'].
+constexpr int WG_TILE = 64;
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) net_wgrad_kernel(Geo g, const float2* __restrict__ th32,
                                                         const float2* __restrict__ d, const float2* __restrict__ h,
-                                                        double* __restrict__ partials, long long n, long long chunk) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 7 * COUT * CIN) return;
-  const int mu = e / (COUT * CIN);
-  const int c = (e / CIN) % COUT;
-  const int cp = e % CIN;
-  const long long i0 = (long long)blockIdx.y * chunk;
-  const long long i1 = (i0 + chunk < n) ? i0 + chunk : n;
-  float acc = 0.f;
-  double accd = 0.0;
-  int cnt = 0;
-  for (long long i = i0; i < i1; ++i) {
-    long long j;
-    float2 ph;
-    net_neighbour(g, th32, i, mu, j, ph);
-    const float2 v = cmulf(ph, h[j * CIN + cp]);
-    const float2 dd = d[i * COUT + c];
-    acc = fmaf(dd.x, v.x, fmaf(dd.y, v.y, acc));
-    if (++cnt == 256) {  // bounded float runs, summed in double
-      accd += acc;
-      acc = 0.f;
-      cnt = 0;
+                                                        double* __restrict__ partials, int n, int chunk) {
+  constexpr int E = CIN * COUT;  // weight entries per direction (<= 256)
+  __shared__ float2 Ds[WG_TILE * COUT];
+  __shared__ float2 Hs[WG_TILE * CIN];
+  const int t = threadIdx.x;
+  const int c = t / CIN, cp = t - (t / CIN) * CIN;  // the entry this thread owns (t < E)
+  double accd[7];
+#pragma unroll
+  for (int mu = 0; mu < 7; ++mu) accd[mu] = 0.0;
+  const int i0 = blockIdx.x * chunk;
+  const int i1 = min(n, i0 + chunk);
+  const int V = g.V, L = g.L, N = g.Ntau;
+  for (int tb = i0; tb < i1; tb += WG_TILE) {
+    const int cnt = min(WG_TILE, i1 - tb);
+    for (int k = t; k < WG_TILE * COUT; k += blockDim.x) {
+      const int sl = k / COUT;
+      Ds[k] = sl < cnt ? d[(size_t)tb * COUT + k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+    for (int mu = 0; mu < 7; ++mu) {
+      for (int k = t; k < WG_TILE * CIN; k += blockDim.x) {
+        const int sl = k / CIN, ch = k - sl * CIN;
+        float2 v = make_float2(0.f, 0.f);
+        if (sl < cnt) {
+          const int i = tb + sl;
+          const int tau = i / V, s = i - tau * V, y = s / L, x = s - y * L, base = tau * V;
+          int j = i;
+          float2 ph = make_float2(1.f, 0.f);
+          float sn, cs;
+          if (mu == 1) {
+            j = base + y * L + (x + 1 == L ? 0 : x + 1);
+            __sincosf(__ldg(th32 + i).x, &sn, &cs);
+            ph = make_float2(cs, sn);
+          } else if (mu == 2) {
+            j = base + y * L + (x == 0 ? L - 1 : x - 1);
+            __sincosf(__ldg(th32 + j).x, &sn, &cs);
+            ph = make_float2(cs, -sn);
+          } else if (mu == 3) {
+            j = base + (y + 1 == L ? 0 : y + 1) * L + x;
+            __sincosf(__ldg(th32 + i).y, &sn, &cs);
+            ph = make_float2(cs, sn);
+          } else if (mu == 4) {
+            j = base + (y == 0 ? L - 1 : y - 1) * L + x;
+            __sincosf(__ldg(th32 + j).y, &sn, &cs);
+            ph = make_float2(cs, -sn);
+          } else if (mu == 5) {
+            const int tp = tau + 1 == N ? 0 : tau + 1;
+            j = tp * V + s;
+            ph = make_float2(tp == 0 ? -1.f : 1.f, 0.f);
+          } else if (mu == 6) {
+            const int tm = tau == 0 ? N - 1 : tau - 1;
+            j = tm * V + s;
+            ph = make_float2(tau == 0 ? -1.f : 1.f, 0.f);
+          }
+          v = cmulf(ph, __ldg(h + (size_t)j * CIN + ch));
+        }
+        Hs[k] = v;
+      }
+      __syncthreads();  // Ds (first direction) and Hs complete
+      if (t < E) {
+        float acc = 0.f;
+#pragma unroll 8
+        for (int sl = 0; sl < WG_TILE; ++sl) {
+          const float2 dd = Ds[sl * COUT + c], hv = Hs[sl * CIN + cp];
+          acc = fmaf(dd.x, hv.x, fmaf(dd.y, hv.y, acc));
+        }
+        accd[mu] += (double)acc;
+      }
+      __syncthreads();  // Hs (and, after the last direction, Ds) may be overwritten
     }
   }
-  partials[(long long)blockIdx.y * (7 * COUT * CIN) + e] = accd + acc;
+  if (t < E) {
+#pragma unroll
+    for (int mu = 0; mu < 7; ++mu) partials[(size_t)blockIdx.x * (7 * E) + mu * E + t] = accd[mu];
+  }
 }
 
 // loss = ||h - x||^2 / ||x||^2 (partials) and d = 2 (h - x) / ||x||^2; *xx = ||x||^2
@@ -368,24 +428,22 @@ cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, in
 }
 
 cudaError_t launch_net_layer_host_weights(const Geo& g, const float2* th32, const float* w, int cin, int cout,
-                                         const float2* in, float2* out, cudaStream_t s) {
+                                         const float2* in, float2* out, const CgState* st, cudaStream_t s) {
   const int n = g.V * g.Ntau;
   const int nb = blocks_for(n, 256);
-  if (cin == 1 && cout == 16) return layer_cw<1, 16>(g, th32, w, in, out, n, nb, s);
-  if (cin == 16 && cout == 16) return layer_cw<16, 16>(g, th32, w, in, out, n, nb, s);
-  if (cin == 16 && cout == 1) return layer_cw<16, 1>(g, th32, w, in, out, n, nb, s);
+  if (cin == 1 && cout == 16) return layer_cw<1, 16>(g, th32, w, in, out, n, nb, st, s);
+  if (cin == 16 && cout == 16) return layer_cw<16, 16>(g, th32, w, in, out, n, nb, st, s);
+  if (cin == 16 && cout == 1) return layer_cw<16, 1>(g, th32, w, in, out, n, nb, st, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
                              double* partials, int nchunks, cudaStream_t s) {
-  const long long n = (long long)g.V * g.Ntau;
-  const long long chunk = (n + nchunks - 1) / nchunks;
-  const int ne = 7 * cin * cout;
-  dim3 grid((ne + 255) / 256, nchunks);
-  if (cin == 1 && cout == 16) net_wgrad_kernel<1, 16><<<grid, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
-  else if (cin == 16 && cout == 16) net_wgrad_kernel<16, 16><<<grid, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
-  else if (cin == 16 && cout == 1) net_wgrad_kernel<16, 1><<<grid, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
+  const int n = g.V * g.Ntau;
+  const int chunk = (n + nchunks - 1) / nchunks;
+  if (cin == 1 && cout == 16) net_wgrad_kernel<1, 16><<<nchunks, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
+  else if (cin == 16 && cout == 16) net_wgrad_kernel<16, 16><<<nchunks, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
+  else if (cin == 16 && cout == 1) net_wgrad_kernel<16, 1><<<nchunks, 256, 0, s>>>(g, th32, d, h, partials, n, chunk);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

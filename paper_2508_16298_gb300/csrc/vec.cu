@@ -319,6 +319,33 @@ cudaError_t launch_loop_condition(CgState* st, cudaGraphConditionalHandle h, cud
   return cudaGetLastError();
 }
 
+// Flexible CG (Notay's FCG with one kept direction, i.e. the Polak-Ribiere form):
+// the two dot products of the direction's beta after a variable preconditioner
+// z = P_k(r), summed per thread in float like the other FP32 reductions.
+__global__ void __launch_bounds__(256) fcg_dots_kernel(long long n, const float2* __restrict__ r,
+                                                       const float2* __restrict__ r_old, const float2* __restrict__ z,
+                                                       double* __restrict__ part_rz, double* __restrict__ part_cross,
+                                                       const CgState* st) {
+  __shared__ double red[32];
+  if (st && *(volatile const int*)&st->done != CG_RUNNING) return;  // uniform: the next head skips too
+  float a = 0.f, b = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 zv = z[i];
+    a += cdot_re_own(r[i], zv);
+    b += cdot_re_own(r_old[i], zv);
+  }
+  double t = block_sum((double)a, red);
+  if (threadIdx.x == 0) part_rz[blockIdx.x] = t;
+  t = block_sum((double)b, red);
+  if (threadIdx.x == 0) part_cross[blockIdx.x] = t;
+}
+
+cudaError_t launch_fcg_dots(long long n, const float2* r, const float2* r_old, const float2* z, int grid,
+                            double* part_rz, double* part_cross, const CgState* st, cudaStream_t s) {
+  fcg_dots_kernel<<<grid, 256, 0, s>>>(n, r, r_old, z, part_rz, part_cross, st);
+  return cudaGetLastError();
+}
+
 __global__ void accumulate_correction_kernel(long long n, double2* __restrict__ x, float2* __restrict__ xh,
                                              const CgState* st, int gate) {
   if (st && !gate_open(gate, *(volatile const int*)&st->done)) return;  // st is not written here

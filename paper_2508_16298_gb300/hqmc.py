@@ -27,9 +27,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
 FP64, FP32 = 0, 1
 ACTION_COMPACT, ACTION_NONCOMPACT = 0, 1
-SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED, SOLVER_PCG64, SOLVER_PMIXED, SOLVER_PLEARNED = range(6)
+SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED, SOLVER_PCG64, SOLVER_PMIXED, SOLVER_PLEARNED, SOLVER_FLEARNED = range(7)
 SOLVERS = {"cg64": SOLVER_CG64, "mixed": SOLVER_MIXED, "learned": SOLVER_LEARNED, "pcg64": SOLVER_PCG64,
-           "pmixed": SOLVER_PMIXED, "plearned": SOLVER_PLEARNED}
+           "pmixed": SOLVER_PMIXED, "plearned": SOLVER_PLEARNED, "flearned": SOLVER_FLEARNED}
 TIMER_MDAGM, TIMER_CG_UPDATE, TIMER_FORCE, TIMER_MDAGM32, TIMER_PRECOND = 0, 1, 2, 3, 4
 
 # Every function declared in include/hqmc.h.
@@ -44,7 +44,8 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory",
            "hqmc_batch_set_solver",
            "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
-           "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner")
+           "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner",
+           "hqmc_set_net_interval")
 
 
 class Params(ctypes.Structure):
@@ -58,7 +59,7 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("true_residual", ctypes.c_double),
                 ("recursive_residual", ctypes.c_double), ("fp64_fallback", ctypes.c_int),
-                ("net_guess_used", ctypes.c_int)]
+                ("net_guess_used", ctypes.c_int), ("fcg_fallback", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -121,6 +122,7 @@ _sig = {
     "hqmc_net_apply": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hqmc_net_train_step": ([_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_set_preconditioner": ([_vp, _vp], _i),
+    "hqmc_set_net_interval": ([_vp, _i], _i),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -550,4 +552,12 @@ class Net:
 
 
 def set_preconditioner(cfg: Config, net):
+    """Attach (or with None detach) the net of the learned solvers; the first attach
+    allocates the config's net workspace."""
     cfg.check(_lib.hqmc_set_preconditioner(cfg.handle, None if net is None else net.handle))
+
+
+def set_net_interval(cfg: Config, k: int):
+    """Flexible CG ("flearned"): the net preconditions every k-th iteration, the
+    tau-line preconditioner the others."""
+    cfg.check(_lib.hqmc_set_net_interval(cfg.handle, int(k)))

@@ -47,9 +47,30 @@ def test_strerror_is_host_only(lib_path):
     assert lib.hqmc_free_config(None) == 0
 
 
-def test_params_struct_layout_matches_header(lib_path):
+def test_params_struct_layout_matches_header(lib_path, tmp_path):
+    """The binding's ctypes structs have the sizes and field offsets the C compiler
+    gives the header's structs."""
+    import shutil
+    import subprocess
     from paper_2508_16298_gb300 import hqmc
-    # int L, int Ntau, 4 doubles, int action, int reliable_interval, int autotune, int variant
-    assert ctypes.sizeof(hqmc.Params) == 4 + 4 + 4 * 8 + 4 * 4
-    assert ctypes.sizeof(hqmc.SolveInfo) == 4 * 4 + 2 * 8 + 2 * 4
-    assert ctypes.sizeof(hqmc.TrajInfo) == 4 * 4 + 5 * 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"hqmc_params": hqmc.Params, "hqmc_solve_info": hqmc.SolveInfo, "hqmc_traj_info": hqmc.TrajInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hqmc.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
