@@ -114,7 +114,9 @@ def test_flexible_solve_against_oracle(hq, interval):
                                      x0=xg, tol=1e-8)
         print("oracle FCG iterations", n, status)
         assert status == "converged"
-        assert abs(info["iterations"] - n) <= max(3, 0.1 * n)
+        # the FP32 recurrence may need a few more iterations than the FP64 one to meet
+        # 1e-8, and one reliable update (every 50 iterations) restarts its drift
+        assert abs(info["iterations"] - n) <= max(12, 0.25 * n)
 
 
 def test_a_net_that_breaks_fcg_falls_back(hq):
