@@ -364,7 +364,15 @@ HQMC_API int hqmc_batch_cg_solve(hqmc_batch* b, const double* const* theta, cons
 
 /* One HQMC update of every chain (as hqmc_trajectory with device draws:
  * seeds[c], the shared traj_counter, nsteps steps of dt[c]); theta[c] in/out;
- * infos (host, nchains entries, nullable).  Synchronises. */
+ * infos (host, nchains entries, nullable).  The whole trajectory of all chains is
+ * ONE CUDA graph launch (Methods, "CUDA Graph acceleration"): batched draws, link
+ * tables, phi = M^dagger R, Hamiltonian terms, forces and kicks over a table of
+ * every chain's blocks or slices, the N_lf + 1 batched solves as conditional WHILE
+ * nodes, and the Metropolis test and restore on the device.  The graph is captured
+ * on first use for (nsteps, tol, maxit, solver) and replayed; per-chain field
+ * pointers, seeds, dt and the counter are uploaded before each launch.  A chain
+ * whose solve fails is rejected (its status in infos[c]).  Returns the worst chain
+ * status.  Synchronises once. */
 HQMC_API int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* seeds, uint64_t traj_counter,
                                    int nsteps, const double* dt, double tol, int maxit, hqmc_traj_info* infos,
                                    void* stream);

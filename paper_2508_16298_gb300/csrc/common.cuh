@@ -42,9 +42,10 @@ template <class T, class R> __device__ __forceinline__ T caxpy(T a, R s, T b) {
   return mk(fma(s, b.x, a.x), fma(s, b.y, a.y));
 }
 template <class T, class R> __device__ __forceinline__ T cscale(R s, T b) { return mk(s * b.x, s * b.y); }
-// Re(conj(a) * b)
+// Re(conj(a) * b), with its rounding written out (one product rounded, one fused)
+// so that every kernel that inlines it rounds alike
 template <class T> __device__ __forceinline__ double cdot_re(T a, T b) {
-  return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+  return fma((double)a.x, (double)b.x, __dmul_rn((double)a.y, (double)b.y));
 }
 // Re(conj(a) * b) in the vector's own precision.  FP32 kernels sum a thread's
 // few terms this way and promote once: FP64 arithmetic runs at a small
@@ -276,11 +277,12 @@ struct CgState {
 
 // Gates of the kernels that close a loop body: run always, only after the
 // recursive residual converged, or whenever the solve is still active.
-enum { GATE_ALWAYS = 0, GATE_REC = 1, GATE_ACTIVE = 2 };
+enum { GATE_ALWAYS = 0, GATE_REC = 1, GATE_ACTIVE = 2, GATE_UNCONVERGED = 3 };
 
 __device__ __forceinline__ bool gate_open(int gate, int done) {
   if (gate == GATE_ALWAYS) return true;
   if (gate == GATE_REC) return done == CG_REC_CONVERGED;
+  if (gate == GATE_UNCONVERGED) return done != CG_CONVERGED;
   return done == CG_RUNNING || done == CG_REC_CONVERGED;
 }
 

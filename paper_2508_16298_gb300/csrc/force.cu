@@ -22,14 +22,13 @@ namespace hqmc {
 
 __constant__ static const int kFam[7] = {4, 3, 2, 1, 2, 3, 4};  // P(1) ... P(7)
 
-__global__ void __launch_bounds__(1024, 1)
-force_kernel(Geo g, double cB, double inv1, double inv2, const double2* __restrict__ U,
-             const double2* __restrict__ X, double* __restrict__ dSf) {
+__device__ __forceinline__ void force_slice(const Geo& g, double cB, double inv1, double inv2,
+                                            const double2* __restrict__ U, const double2* __restrict__ X,
+                                            double* __restrict__ dSf, int tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int V = g.V, N = g.Ntau;
   double2* u = reinterpret_cast<double2*>(smem_raw);
   double2* w = u + V;
-  const int tau = blockIdx.x;
   const int taup = (tau == N - 1) ? 0 : tau + 1;
   const double sigp = (taup == 0) ? -1.0 : 1.0;  // sign of the B term in row tau+1 of M
   const double sgn = (tau < N - 1) ? 1.0 : -1.0;
@@ -60,13 +59,15 @@ force_kernel(Geo g, double cB, double inv1, double inv2, const double2* __restri
       bond_of(g, fam, b, i, j, c);
       const double2 uu = __ldg(Ut + 2 * i + c);
       const double2 wi = w[i], wj = w[j], ui = u[i], uj = u[j];
-      // val = conj(w_i) U u_j - conj(w_j) conj(U) u_i ; only Im(val) is needed
-      const double2 Uuj = make_double2(uu.x * uj.x - uu.y * uj.y, uu.x * uj.y + uu.y * uj.x);
-      const double2 cUui = make_double2(uu.x * ui.x + uu.y * ui.y, uu.x * ui.y - uu.y * ui.x);
-      const double im = (wi.x * Uuj.y - wi.y * Uuj.x) - (wj.x * cUui.y - wj.y * cUui.x);
+      // val = conj(w_i) U u_j - conj(w_j) conj(U) u_i ; only Im(val) is needed.  Every
+      // product-sum is written as an explicit fma so that the single-chain and the
+      // batched kernel, which both inline this, round alike.
+      const double2 Uuj = make_double2(fma(uu.x, uj.x, -__dmul_rn(uu.y, uj.y)), fma(uu.x, uj.y, __dmul_rn(uu.y, uj.x)));
+      const double2 cUui = make_double2(fma(uu.x, ui.x, __dmul_rn(uu.y, ui.y)), fma(uu.x, ui.y, -__dmul_rn(uu.y, ui.x)));
+      const double im = __dsub_rn(fma(wi.x, Uuj.y, -__dmul_rn(wi.y, Uuj.x)), fma(wj.x, cUui.y, -__dmul_rn(wj.y, cUui.x)));
       // bond b of a family is handled by the same thread at both of its positions
       double* o = reinterpret_cast<double*>(out + i) + c;
-      *o += coef * im;
+      *o = fma(coef, im, *o);
     }
     if (k == 6) break;
     __syncthreads();
@@ -74,6 +75,28 @@ force_kernel(Geo g, double cB, double inv1, double inv2, const double2* __restri
     factor_pass_inverse(g, kFam[k + 1], u, Ut, inv_of(kFam[k + 1]));  // u_{k+1} = P(k+1)^{-1} u_k
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(1024, 1)
+force_kernel(Geo g, double cB, double inv1, double inv2, const double2* __restrict__ U,
+             const double2* __restrict__ X, double* __restrict__ dSf) {
+  force_slice(g, cB, inv1, inv2, U, X, dSf, blockIdx.x);
+}
+
+// The force of every chain of a batch: one CTA per (chain, slice) tile.
+__global__ void __launch_bounds__(1024, 1) batch_force_kernel(const ChainDesc* __restrict__ descs,
+                                                              const int2* __restrict__ tiles) {
+  const int2 t = tiles[blockIdx.x];
+  const ChainDesc& d = descs[t.x];
+  force_slice(d.g, d.cB, d.inv1, d.inv2, d.U64, d.X, d.dSf, t.y);
+}
+
+cudaError_t launch_batch_force(const ChainDesc* d, const int2* tiles, int ntiles, int threads, size_t smem,
+                               cudaStream_t s) {
+  cudaError_t e = raise_smem_limit(batch_force_kernel, smem);
+  if (e != cudaSuccess) return e;
+  batch_force_kernel<<<ntiles, threads, smem, s>>>(d, tiles);
+  return cudaGetLastError();
 }
 
 cudaError_t prepare_force(const SliceLaunch& sl) {

@@ -1729,6 +1729,29 @@ struct hqmc_batch {
   cudaGraphExec_t exec = nullptr;
   int body_kernels = 0;
   long long launches = 0;
+  // one graph per trajectory: per-chain descriptors, block tables, device info
+  MdagmArgs<double>* d_resid_report = nullptr;  // residual of unconverged chains after a loop (FIN_REPORT)
+  ChainDesc* d_chain = nullptr;
+  ChainDesc* h_chain = nullptr;        // pinned staging
+  uint64_t* d_counter = nullptr;       // trajectory counter (device; read by the draws and the Metropolis uniform)
+  unsigned long long* d_bodies = nullptr;  // loop bodies run by the last trajectory graph
+  hqmc_traj_info* d_info = nullptr;
+  struct TrajMirror {
+    uint64_t counter;
+    unsigned long long bodies;
+  }* h_mirror = nullptr;               // pinned: counter to upload, bodies read back
+  hqmc_traj_info* h_info = nullptr;    // pinned mirror of d_info
+  int4 *d_site_tab = nullptr, *d_act_tab = nullptr, *d_ff_tab = nullptr;
+  int n_site_tab = 0, n_act_tab = 0, n_ff_tab = 0;
+  int2* d_stiles = nullptr;            // (chain, slice) of the slice kernels (M^dagger R, force)
+  int n_stiles = 0;
+  int slice_threads = 64;
+  size_t smem_apply = 0, smem_force = 0;
+  cudaStream_t cap2 = nullptr;         // captures the loop bodies while a trajectory is being captured
+  cudaGraphExec_t traj_exec = nullptr;
+  int traj_nsteps = -1, traj_maxit = -1, traj_solver = -1;
+  double traj_tol = -1.0;
+  long long traj_static_kernels = 0;   // kernels of a trajectory graph outside its loop bodies
   char err[512] = {0};
 };
 
@@ -1760,7 +1783,21 @@ int bfail(hqmc_batch* b, int code, const char* fmt, ...) {
 
 void batch_release(hqmc_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->traj_exec) cudaGraphExecDestroy(b->traj_exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
+  cudaFree(b->d_resid_report);
+  cudaFree(b->d_chain);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_bodies);
+  cudaFree(b->d_info);
+  cudaFree(b->d_site_tab);
+  cudaFree(b->d_act_tab);
+  cudaFree(b->d_ff_tab);
+  cudaFree(b->d_stiles);
+  if (b->h_chain) cudaFreeHost(b->h_chain);
+  if (b->h_mirror) cudaFreeHost(b->h_mirror);
+  if (b->h_info) cudaFreeHost(b->h_info);
   cudaFree(b->d_cgdir);
   cudaFree(b->d_resid_start);
   cudaFree(b->d_resid_loop);
@@ -1787,6 +1824,7 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
   auto* up = (UpdArgs<double>*)(rl + nc);
   auto* fin = (FinArgs*)(up + nc);
   auto* ld = (LineBatchDesc<double>*)(fin + nc);
+  auto* rep = (MdagmArgs<double>*)(ld + nc);
   const bool pc = b->solver == HQMC_SOLVER_PCG64;
   for (int c = 0; c < nc; ++c) {
     hqmc_config* cfg = b->cfgs[c];
@@ -1822,6 +1860,9 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
     rs[c] = r;
     r.gate = GATE_REC;
     rl[c] = r;
+    r.gate = GATE_UNCONVERGED;  // after a loop: the true residual of chains that did not converge
+    r.r_out = cfg->vscratch;
+    rep[c] = r;
     up[c] = UpdArgs<double>{cfg->n, x[c], 1, cfg->r64, cfg->p64[0], cfg->p64[1], cfg->q64, cfg->part_mdagm,
                             nslots, cfg->part_ew, cfg->st};
     fin[c] = FinArgs{cfg->part_resid, nslots, cfg->part_ew, cfg->ew_grid, cfg->st, cfg->report};
@@ -1832,6 +1873,7 @@ int batch_descriptors(hqmc_batch* b, const double2* const* phi, double2* const* 
   BCK(cudaMemcpyAsync(b->d_upd, up, nc * sizeof(UpdArgs<double>), cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(b->d_fin, fin, nc * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(b->d_line, ld, nc * sizeof(LineBatchDesc<double>), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(b->d_resid_report, rep, nc * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
   return HQMC_OK;
 }
 
@@ -1937,6 +1979,132 @@ int batch_solve(hqmc_batch* b, const double2* const* phi, double2* const* x, dou
   return worst;
 }
 
+// One batched solve of (M^dagger M) X_c = eta_c for every chain, enqueued while a
+// trajectory graph is being captured on s: the start residual, a conditional WHILE
+// node (added to the capture's graph) whose body is the batched CG loop body,
+// captured on a second stream, then the true residual of the chains that did not
+// converge and the per-chain bookkeeping of the trajectory info.
+int traj_solve(hqmc_batch* b, double tol, int maxit, long long* nk, cudaStream_t s) {
+  const int nc = (int)b->cfgs.size();
+  const bool pc = b->solver == HQMC_SOLVER_PCG64;
+  BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_start, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
+  BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_START, tol, maxit, GATE_ALWAYS, s));
+  *nk += 2;
+  if (pc) {
+    BCK(launch_line_precond_batch(b->d_line, b->d_ltiles, b->nltiles, b->maxW, b->maxtc, s));
+    *nk += 1;
+  }
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  BCK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return bfail(b, HQMC_ECUDA, "trajectory capture is not active");
+  cudaGraphConditionalHandle h;
+  BCK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  BCK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  BCK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  BCK(cudaStreamBeginCaptureToGraph(b->cap2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed));
+  int rc = batch_body(b, b->cap2);
+  if (rc == HQMC_OK) {
+    const cudaError_t le = launch_loop_condition_batch(b->d_states, nc, h, b->cap2, b->d_bodies);
+    if (le != cudaSuccess) rc = bfail(b, HQMC_ECUDA, "loop condition: %s", cudaGetErrorString(le));
+  }
+  cudaGraph_t body = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap2, &body);
+  if (rc != HQMC_OK) return rc;
+  BCK(e);
+  BCK((launch_mdagm_batch<double, MODE_RESID>(b->d_resid_report, b->d_tiles, b->ntiles, b->C, b->threads, b->smem, s)));
+  BCK(launch_resid_finalize_batch(b->d_fin, nc, FIN_REPORT, tol, maxit, GATE_UNCONVERGED, s));
+  BCK(launch_batch_solve_close(b->d_chain, nc, s));
+  *nk += 3;
+  return HQMC_OK;
+}
+
+// The whole trajectory of every chain as one graph (rebuilt when nsteps, tol, maxit
+// or the solver change): draws, links, phi = M^dagger R, H0, the leapfrog with its
+// N_lf + 1 batched solves and forces, H1, the Metropolis test and the restore of
+// rejected fields.  Every kernel reads the per-chain descriptors and the trajectory
+// counter from device memory, which the host rewrites before each launch.
+int traj_graph(hqmc_batch* b, int nsteps, double tol, int maxit) {
+  if (b->traj_exec && b->traj_nsteps == nsteps && b->traj_tol == tol && b->traj_maxit == maxit &&
+      b->traj_solver == b->solver)
+    return HQMC_OK;
+  if (b->traj_exec) {
+    BCK(cudaDeviceSynchronize());
+    cudaGraphExecDestroy(b->traj_exec);
+    b->traj_exec = nullptr;
+  }
+  const int nc = (int)b->cfgs.size();
+  cudaStream_t s = b->cap;
+  long long nk = 0;
+  BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  auto ew = [&](int op) -> int {
+    BCK(launch_batch_elementwise(b->d_chain, b->d_site_tab, b->n_site_tab, op, b->d_counter, s));
+    nk += 1;
+    return HQMC_OK;
+  };
+  auto force = [&]() -> int {
+    BCK(launch_batch_force(b->d_chain, b->d_stiles, b->n_stiles, b->slice_threads, b->smem_force, s));
+    BCK(launch_batch_force_finish(b->d_chain, b->d_ff_tab, b->n_ff_tab, s));
+    nk += 2;
+    return HQMC_OK;
+  };
+  auto body = [&]() -> int {
+    BCK(launch_batch_info_init(b->d_chain, nc, b->d_counter, s));
+    nk += 1;
+    RET(ew(BT_DRAW));
+    RET(ew(BT_LINKS));
+    BCK(launch_batch_apply_Mdag(b->d_chain, b->d_stiles, b->n_stiles, b->slice_threads, b->smem_apply, s));
+    BCK(launch_batch_action(b->d_chain, b->d_act_tab, b->n_act_tab, nc, 0, s));  // H0
+    nk += 3;
+    RET(ew(BT_SAVE));
+    RET(ew(BT_ZERO_X));
+    RET(traj_solve(b, tol, maxit, &nk, s));
+    RET(force());
+    for (int step = 0; step < nsteps; ++step) {
+      RET(ew(BT_KICK_DRIFT));
+      RET(ew(BT_LINKS));
+      RET(traj_solve(b, tol, maxit, &nk, s));
+      RET(force());
+      RET(ew(BT_KICK));
+    }
+    BCK(launch_batch_action(b->d_chain, b->d_act_tab, b->n_act_tab, nc, 1, s));  // H1
+    BCK(launch_batch_metropolis(b->d_chain, nc, s));
+    nk += 3;
+    return ew(BT_RESTORE);
+  };
+  int rc = body();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (rc == HQMC_OK && e != cudaSuccess) rc = bfail(b, HQMC_ECUDA, "trajectory capture: %s", cudaGetErrorString(e));
+  if (rc == HQMC_OK) {
+    e = cudaGraphInstantiate(&b->traj_exec, graph, 0);
+    if (e != cudaSuccess) {
+      b->traj_exec = nullptr;
+      rc = bfail(b, HQMC_ECUDA, "trajectory graph instantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != HQMC_OK) {
+    cudaGetLastError();
+    return rc;
+  }
+  b->traj_nsteps = nsteps;
+  b->traj_tol = tol;
+  b->traj_maxit = maxit;
+  b->traj_solver = b->solver;
+  b->traj_static_kernels = nk;
+  return HQMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2019,12 +2187,58 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
       rc = bfail(b, HQMC_ENOMEM, "batch tables");
       break;
     }
-    b->stage_bytes = nchains * (3 * sizeof(MdagmArgs<double>) + sizeof(UpdArgs<double>) + sizeof(FinArgs) +
+    b->stage_bytes = nchains * (4 * sizeof(MdagmArgs<double>) + sizeof(UpdArgs<double>) + sizeof(FinArgs) +
                                 sizeof(LineBatchDesc<double>));
     if (cudaMallocHost(&b->h_stage, b->stage_bytes) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       rc = bfail(b, HQMC_ENOMEM, "batch staging");
+      break;
+    }
+    // trajectory graphs: block tables of the batched kernels over every chain
+    std::vector<int4> site_tab, act_tab, ff_tab;
+    std::vector<int2> stiles;
+    auto ew = [](long long count) { return (int)std::max(1LL, std::min(4096LL, (count + 255) / 256)); };
+    int maxSliceThreads = 64;
+    for (int c = 0; c < nchains; ++c) {
+      hqmc_config* cfg = b->cfgs[c];
+      const int nsb = ew(2 * cfg->n);  // the longest loop of the element-wise ops (2 per site)
+      for (int j = 0; j < nsb; ++j) site_tab.push_back(make_int4(c, j, nsb, 0));
+      for (int j = 0; j < cfg->act_grid; ++j) act_tab.push_back(make_int4(c, j, cfg->act_grid, 0));
+      const long long nff = (long long)cfg->g.V * ((cfg->p.Ntau + 31) / 32);
+      const int nfb = ew(nff);
+      for (int j = 0; j < nfb; ++j) ff_tab.push_back(make_int4(c, j, nfb, 0));
+      for (int t = 0; t < cfg->p.Ntau; ++t) stiles.push_back(make_int2(c, t));
+      maxSliceThreads = std::max(maxSliceThreads, cfg->sl1.threads);
+      b->smem_apply = std::max(b->smem_apply, (size_t)cfg->g.V * sizeof(double2));
+      b->smem_force = std::max(b->smem_force, 2 * (size_t)cfg->g.V * sizeof(double2));
+    }
+    b->slice_threads = maxSliceThreads;
+    b->n_site_tab = (int)site_tab.size();
+    b->n_act_tab = (int)act_tab.size();
+    b->n_ff_tab = (int)ff_tab.size();
+    b->n_stiles = (int)stiles.size();
+    if (!dal((void**)&b->d_resid_report, nchains * sizeof(MdagmArgs<double>)) ||
+        !dal((void**)&b->d_chain, nchains * sizeof(ChainDesc)) || !dal((void**)&b->d_counter, sizeof(uint64_t)) ||
+        !dal((void**)&b->d_bodies, sizeof(unsigned long long)) ||
+        !dal((void**)&b->d_info, nchains * sizeof(hqmc_traj_info)) ||
+        !dal((void**)&b->d_site_tab, site_tab.size() * sizeof(int4)) ||
+        !dal((void**)&b->d_act_tab, act_tab.size() * sizeof(int4)) ||
+        !dal((void**)&b->d_ff_tab, ff_tab.size() * sizeof(int4)) ||
+        !dal((void**)&b->d_stiles, stiles.size() * sizeof(int2)) ||
+        cudaMallocHost(&b->h_chain, nchains * sizeof(ChainDesc)) != cudaSuccess ||
+        cudaMallocHost(&b->h_mirror, sizeof(*b->h_mirror)) != cudaSuccess ||
+        cudaMallocHost(&b->h_info, nchains * sizeof(hqmc_traj_info)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      rc = bfail(b, HQMC_ENOMEM, "batch trajectory tables");
+      break;
+    }
+    if (cudaMemcpy(b->d_site_tab, site_tab.data(), site_tab.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_act_tab, act_tab.data(), act_tab.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_ff_tab, ff_tab.data(), ff_tab.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_stiles, stiles.data(), stiles.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = bfail(b, HQMC_ECUDA, "batch trajectory table upload");
       break;
     }
     if (cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -2060,10 +2274,12 @@ int hqmc_batch_set_solver(hqmc_batch* b, int solver) {
   if (!b) return HQMC_EINVAL;
   if (solver != HQMC_SOLVER_CG64 && solver != HQMC_SOLVER_PCG64)
     return bfail(b, HQMC_EINVAL, "batched solver must be HQMC_SOLVER_CG64 or HQMC_SOLVER_PCG64");
-  if (solver != b->solver && b->exec) {  // the loop body changes: capture it again on next use
+  if (solver != b->solver && (b->exec || b->traj_exec)) {  // the loop body changes: capture again on next use
     cudaDeviceSynchronize();
-    cudaGraphExecDestroy(b->exec);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->traj_exec) cudaGraphExecDestroy(b->traj_exec);
     b->exec = nullptr;
+    b->traj_exec = nullptr;
   }
   b->solver = solver;
   return HQMC_OK;
@@ -2097,92 +2313,60 @@ int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* s
   for (int c = 0; c < nc; ++c)
     if (!aligned16(theta[c]) || !std::isfinite(dt[c])) return bfail(b, HQMC_EINVAL, "chain %d: bad theta or dt", c);
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<hqmc_traj_info> ti(nc);
-  std::vector<hqmc_solve_info> si(nc);
+  // per-chain descriptors of this trajectory (field pointer, seed and dt may change between calls)
   std::vector<const double2*> eta(nc);
   std::vector<double2*> X(nc);
   for (int c = 0; c < nc; ++c) {
     hqmc_config* cfg = b->cfgs[c];
-    const long long n = cfg->n;
-    BRET([&]() -> int {
-      LK(1, launch_draw(n, seeds[c], traj_counter, cfg->pm, cfg->Rw, s));
-      philox_uniform_host(seeds[c], traj_counter, &ti[c].u);
-      RET(links(cfg, theta[c], true, false, s));
-      LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, cfg->Rw, cfg->eta, 1, s));
-      LK(2, launch_action_terms(cfg->g, cfg->bp, theta[c], cfg->pm, cfg->Rw, cfg->Rw, cfg->act_grid, cfg->part_act,
-                                cfg->terms, s));
-      CK(cudaMemcpyAsync(cfg->th0, theta[c], 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemsetAsync(cfg->Xw, 0, n * sizeof(double2), s));
-      return HQMC_OK;
-    }(), cfg);
+    ChainDesc& d = b->h_chain[c];
+    d = ChainDesc{};
+    d.g = cfg->g;
+    d.bp = cfg->bp;
+    d.cB = cfg->cB;
+    d.t1 = cfg->t1;
+    d.t2 = cfg->t2;
+    d.inv1 = 1.0 / (1.0 - cfg->t1 * cfg->t1);  // as the single-chain force launch forms them
+    d.inv2 = 1.0 / (1.0 - cfg->t2 * cfg->t2);
+    d.n = cfg->n;
+    d.theta = theta[c];
+    d.th0 = cfg->th0;
+    d.p = cfg->pm;
+    d.R = cfg->Rw;
+    d.eta = cfg->eta;
+    d.X = cfg->Xw;
+    d.F = cfg->F;
+    d.dSf = cfg->dSf;
+    d.U64 = cfg->U64;
+    d.part_act = cfg->part_act;
+    d.act_grid = cfg->act_grid;
+    d.terms = cfg->terms;
+    d.st = cfg->st;
+    d.report = cfg->report;
+    d.seed = seeds[c];
+    d.dt = dt[c];
+    d.info = b->d_info + c;
     eta[c] = cfg->eta;
     X[c] = cfg->Xw;
   }
+  int rc = batch_descriptors(b, eta.data(), X.data(), s);
+  if (rc != HQMC_OK) return rc;
+  BCK(cudaMemcpyAsync(b->d_chain, b->h_chain, nc * sizeof(ChainDesc), cudaMemcpyHostToDevice, s));
+  b->h_mirror->counter = traj_counter;
+  BCK(cudaMemcpyAsync(b->d_counter, &b->h_mirror->counter, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemsetAsync(b->d_bodies, 0, sizeof(unsigned long long), s));
+  if ((rc = traj_graph(b, nsteps, tol, maxit)) != HQMC_OK) return rc;
+  BCK(cudaGraphLaunch(b->traj_exec, s));
+  BCK(cudaMemcpyAsync(b->h_info, b->d_info, nc * sizeof(hqmc_traj_info), cudaMemcpyDeviceToHost, s));
+  BCK(cudaMemcpyAsync(&b->h_mirror->bodies, b->d_bodies, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  const bool pc = b->solver == HQMC_SOLVER_PCG64;
+  const long long body = (pc ? 3 : 2) * kBodyIters64 + 3 + (pc ? 1 : 0) + 1;  // with the loop condition
+  b->launches += b->traj_static_kernels + (long long)b->h_mirror->bodies * body;
   int worst = HQMC_OK;
-  auto solve_all = [&]() -> int {
-    const int rc = batch_solve(b, eta.data(), X.data(), tol, maxit, si.data(), s);
-    if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
-    worst = merge_status(worst, rc);
-    for (int c = 0; c < nc; ++c) {
-      ti[c].cg_solves++;
-      ti[c].cg_iterations += si[c].iterations;
-      ti[c].max_true_residual = std::fmax(ti[c].max_true_residual, si[c].true_residual);
-      ti[c].status = merge_status(ti[c].status, si[c].status);
-    }
-    return HQMC_OK;
-  };
-  int rc = solve_all();
-  for (int c = 0; c < nc && rc == HQMC_OK; ++c) BRET(force(b->cfgs[c], theta[c], X[c], b->cfgs[c]->F, b->cfgs[c]->dSf, s), b->cfgs[c]);
-  for (int step = 0; step < nsteps && rc == HQMC_OK; ++step) {
-    for (int c = 0; c < nc; ++c) {
-      hqmc_config* cfg = b->cfgs[c];
-      BRET([&]() -> int {
-        LK(1, launch_kick_drift(2 * cfg->n, cfg->pm, theta[c], cfg->F, dt[c] / 2, dt[c], s));
-        RET(links(cfg, theta[c], true, false, s));
-        return HQMC_OK;
-      }(), cfg);
-    }
-    rc = solve_all();
-    if (rc != HQMC_OK) break;
-    for (int c = 0; c < nc; ++c) {
-      hqmc_config* cfg = b->cfgs[c];
-      BRET(force(cfg, theta[c], X[c], cfg->F, cfg->dSf, s), cfg);
-      BRET([&]() -> int {
-        LK(1, launch_kick(2 * cfg->n, cfg->pm, cfg->F, dt[c] / 2, s));
-        return HQMC_OK;
-      }(), cfg);
-    }
-  }
-  if (rc != HQMC_OK) {
-    for (int c = 0; c < nc; ++c)
-      BCK(cudaMemcpyAsync(theta[c], b->cfgs[c]->th0, 2 * b->cfgs[c]->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    BCK(cudaStreamSynchronize(s));
-    return rc;
-  }
   for (int c = 0; c < nc; ++c) {
-    hqmc_config* cfg = b->cfgs[c];
-    BRET([&]() -> int {
-      LK(2, launch_action_terms(cfg->g, cfg->bp, theta[c], cfg->pm, cfg->eta, cfg->Xw, cfg->act_grid, cfg->part_act,
-                                cfg->terms + 3, s));
-      CK(cudaMemcpyAsync(cfg->terms_h, cfg->terms, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      return HQMC_OK;
-    }(), cfg);
+    if (infos) infos[c] = b->h_info[c];
+    worst = merge_status(worst, b->h_info[c].status);
   }
-  BCK(cudaStreamSynchronize(s));
-  for (int c = 0; c < nc; ++c) {
-    hqmc_config* cfg = b->cfgs[c];
-    const double* t = cfg->terms_h;
-    ti[c].H0 = t[0] + t[1] + t[2];
-    ti[c].H1 = t[3] + t[4] + t[5];
-    ti[c].dH = ti[c].H1 - ti[c].H0;
-    ti[c].accepted = std::isfinite(ti[c].dH) && ti[c].u < std::exp(-ti[c].dH);
-    if (!std::isfinite(ti[c].dH)) ti[c].status = merge_status(ti[c].status, HQMC_ENONFINITE);
-    if (!ti[c].accepted)
-      BCK(cudaMemcpyAsync(theta[c], cfg->th0, 2 * cfg->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (infos) infos[c] = ti[c];
-    worst = merge_status(worst, ti[c].status);
-  }
-  BCK(cudaStreamSynchronize(s));
   return worst;
 }
 

@@ -295,11 +295,14 @@ cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const 
                                    cudaStream_t s);
 
 enum { FIN_START = 0, FIN_RESTART = 1, FIN_RELIABLE = 2, FIN_REPORT = 3 };
+
+
 // Batched finalize (START or RESTART), one block per chain; descs: device array of FinArgs.
 cudaError_t launch_resid_finalize_batch(const void* descs, int nchains, int mode, double tol, int maxit, int gate,
                                         cudaStream_t s);
+// bodies (nullable): device counter of loop bodies, incremented once per body.
 cudaError_t launch_loop_condition_batch(CgState* const* states, int nchains, cudaGraphConditionalHandle h,
-                                        cudaStream_t s);
+                                        cudaStream_t s, unsigned long long* bodies = nullptr);
 // Sums the RESID partials into the CG state.
 cudaError_t launch_resid_finalize(const double* part, int n, int mode, double tol, int maxit,
                                   double* part_rr_out, int n_rr_out, CgState* st, double* report,
@@ -371,5 +374,50 @@ cudaError_t launch_net_adam(float* w, float* m, float* v, const double* partials
                             float lr, float b1, float b2, float c1, float c2, float eps, float scale, cudaStream_t s);
 cudaError_t launch_net_adjoint_weights(const void* W, void* Wt, int cin, int cout, cudaStream_t s);
 cudaError_t launch_net_convert(const void* in, void* out, int to_float, double scale, long long n, cudaStream_t s);
+
+// ---- batched trajectories (one graph per trajectory of many chains) ----------
+// One chain of a batch as the batched trajectory kernels see it (device array,
+// rewritten before every trajectory: the field pointer, seed and dt may change).
+struct ChainDesc {
+  Geo g;
+  BosonParams bp;
+  double cB, t1, t2;
+  double inv1, inv2;         // 1 / (1 - t1^2), 1 / (1 - t2^2), computed on the host as for a single chain
+  long long n;               // sites
+  double* theta;             // the caller's field (in/out)
+  double* th0;               // the field at the start of the trajectory
+  double* p;                 // momenta
+  double2* R;                // pseudofermion draw
+  double2* eta;              // phi = M^dagger R
+  double2* X;                // CG solution (and initial guess)
+  double* F;                 // total force
+  double* dSf;               // fermion part
+  double2* U64;              // link table
+  double* part_act;          // action partials (4 per block)
+  int act_grid;              // blocks of the chain's action reduction (as in its own launch)
+  double* terms;             // H0 terms [0..2], H1 terms [3..5]
+  const CgState* st;         // CG state of the chain's solves
+  const double* report;      // true <r, r>, <phi, phi> of the last residual
+  uint64_t seed;
+  double dt;
+  hqmc_traj_info* info;      // device copy of the chain's trajectory info
+};
+// Block tables of the batched kernels: int4 (chain, local block, blocks of that chain, 0).
+enum { BT_DRAW = 0, BT_LINKS = 1, BT_ZERO_X = 2, BT_SAVE = 3, BT_RESTORE = 4, BT_KICK_DRIFT = 5, BT_KICK = 6 };
+cudaError_t launch_batch_elementwise(const ChainDesc* d, const int4* tab, int nblocks, int op, const uint64_t* counter,
+                                     cudaStream_t s);
+// Hamiltonian terms of every chain: which = 0 (H0: p, R, R) or 1 (H1: p, eta, X), into terms[3 * which ...].
+cudaError_t launch_batch_action(const ChainDesc* d, const int4* tab, int nblocks, int nchains, int which,
+                                cudaStream_t s);
+cudaError_t launch_batch_force_finish(const ChainDesc* d, const int4* tab, int nblocks, cudaStream_t s);
+// Per-chain bookkeeping: info reset (with the Metropolis uniform), after each solve, and the Metropolis test.
+cudaError_t launch_batch_info_init(const ChainDesc* d, int nchains, const uint64_t* counter, cudaStream_t s);
+cudaError_t launch_batch_solve_close(const ChainDesc* d, int nchains, cudaStream_t s);
+cudaError_t launch_batch_metropolis(const ChainDesc* d, int nchains, cudaStream_t s);
+// eta = M^dagger R (FP64) and the fermion force, one CTA per (chain, slice) of `tiles`.
+cudaError_t launch_batch_apply_Mdag(const ChainDesc* d, const int2* tiles, int ntiles, int threads, size_t smem,
+                                    cudaStream_t s);
+cudaError_t launch_batch_force(const ChainDesc* d, const int2* tiles, int ntiles, int threads, size_t smem,
+                               cudaStream_t s);
 
 }  // namespace hqmc

@@ -323,14 +323,13 @@ template cudaError_t prepare_mdagm<float, MODE_CGDIR>(const SliceLaunch&);
 // y = M x:        y_tau = x_tau - s_tau  cB P_{tau-1} x_{tau-1}
 // y = M^dagger x: y_tau = x_tau - s'_tau cB P_tau x_{tau+1}   (B Hermitian)
 template <class R>
-__global__ void __launch_bounds__(1024, 1)
-apply_M_kernel(Geo g, R cB, const C2<R>* __restrict__ U, const C2<R>* __restrict__ x,
-               C2<R>* __restrict__ y, int dagger) {
+__device__ __forceinline__ void apply_M_slice(const Geo& g, R cB, const C2<R>* __restrict__ U,
+                                              const C2<R>* __restrict__ x, C2<R>* __restrict__ y, int dagger,
+                                              int tau) {
   using T = C2<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* W = reinterpret_cast<T*>(smem_raw);
   const int V = g.V, N = g.Ntau;
-  const int tau = blockIdx.x;
   int src, uslice;
   R sign;
   if (!dagger) {
@@ -347,6 +346,29 @@ apply_M_kernel(Geo g, R cB, const C2<R>* __restrict__ U, const C2<R>* __restrict
   __syncthreads();
   apply_P(g, W, U + (size_t)uslice * V * 2);
   for (int s = threadIdx.x; s < V; s += blockDim.x) y[bt + s] = caxpy(x[bt + s], sign * cB, W[s]);
+}
+
+template <class R>
+__global__ void __launch_bounds__(1024, 1)
+apply_M_kernel(Geo g, R cB, const C2<R>* __restrict__ U, const C2<R>* __restrict__ x,
+               C2<R>* __restrict__ y, int dagger) {
+  apply_M_slice<R>(g, cB, U, x, y, dagger, blockIdx.x);
+}
+
+// phi = M^dagger R of every chain of a batch: one CTA per (chain, slice) tile.
+__global__ void __launch_bounds__(1024, 1) batch_apply_Mdag_kernel(const ChainDesc* __restrict__ descs,
+                                                                   const int2* __restrict__ tiles) {
+  const int2 t = tiles[blockIdx.x];
+  const ChainDesc& d = descs[t.x];
+  apply_M_slice<double>(d.g, d.cB, d.U64, d.R, d.eta, 1, t.y);
+}
+
+cudaError_t launch_batch_apply_Mdag(const ChainDesc* d, const int2* tiles, int ntiles, int threads, size_t smem,
+                                    cudaStream_t s) {
+  cudaError_t e = raise_smem_limit(batch_apply_Mdag_kernel, smem);
+  if (e != cudaSuccess) return e;
+  batch_apply_Mdag_kernel<<<ntiles, threads, smem, s>>>(d, tiles);
+  return cudaGetLastError();
 }
 
 template <class R>

@@ -4,6 +4,12 @@
 
 #include "hqmc.h"
 
+#if defined(__CUDACC__)
+#define HQMC_HOST_DEVICE __host__ __device__
+#else
+#define HQMC_HOST_DEVICE
+#endif
+
 namespace hqmc {
 
 // CG_REC_CONVERGED: the recursive residual met tol; the true residual still has
@@ -19,7 +25,7 @@ enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_NONF
 // device-side wait gave up during the solve (the kernel that waited poisons its
 // outputs with NaN, so the loop itself ends as CG_NONFINITE or worse); that
 // cause is reported in preference to the symptom.
-inline int solve_status(int done, bool timed_out) {
+HQMC_HOST_DEVICE inline int solve_status(int done, bool timed_out) {
   if (timed_out) return HQMC_ETIMEOUT;
   switch (done) {
     case CG_CONVERGED: return HQMC_OK;

@@ -16,11 +16,22 @@ static inline int ew_blocks(long long n, int threads, int cap) {
 // ---------------------------------------------------------------------------
 // Link tables: U[site][c] = t_f e^{i theta}, t1 = tanh(a) for x-bonds with even
 // tail x (family 1, the merged middle factor), t2 = tanh(a/2) for all others.
+__device__ __forceinline__ void links_site(const Geo& g, const double* __restrict__ theta, double t1, double t2,
+                                           double2* __restrict__ U64, float2* __restrict__ U32,
+                                           float2* __restrict__ th32, long long i);
+
 __global__ void links_kernel(Geo g, const double* __restrict__ theta, double t1, double t2,
                              double2* __restrict__ U64, float2* __restrict__ U32, float2* __restrict__ th32,
                              long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+       i += (long long)gridDim.x * blockDim.x)
+    links_site(g, theta, t1, t2, U64, U32, th32, i);
+}
+
+__device__ __forceinline__ void links_site(const Geo& g, const double* __restrict__ theta, double t1, double t2,
+                                           double2* __restrict__ U64, float2* __restrict__ U32,
+                                           float2* __restrict__ th32, long long i) {
+  {
     const int s = (int)(i % g.V);
     const int x = s % g.L;
     const double2 th = reinterpret_cast<const double2*>(theta)[i];
@@ -279,7 +290,9 @@ cudaError_t launch_resid_finalize_batch(const void* descs, int nchains, int mode
 }
 
 // WHILE condition over many chains: continue while any chain is still active.
-__global__ void loop_condition_batch_kernel(CgState* const* states, int nchains, cudaGraphConditionalHandle h) {
+__global__ void loop_condition_batch_kernel(CgState* const* states, int nchains, cudaGraphConditionalHandle h,
+                                            unsigned long long* bodies) {
+  if (bodies) *bodies += 1;  // loop bodies run (launch accounting of a trajectory graph)
   bool cont = false;
   for (int c = 0; c < nchains; ++c) {
     CgState* st = states[c];
@@ -297,8 +310,8 @@ __global__ void loop_condition_batch_kernel(CgState* const* states, int nchains,
 }
 
 cudaError_t launch_loop_condition_batch(CgState* const* states, int nchains, cudaGraphConditionalHandle h,
-                                        cudaStream_t s) {
-  loop_condition_batch_kernel<<<1, 1, 0, s>>>(states, nchains, h);
+                                        cudaStream_t s, unsigned long long* bodies) {
+  loop_condition_batch_kernel<<<1, 1, 0, s>>>(states, nchains, h, bodies);
   return cudaGetLastError();
 }
 
@@ -382,11 +395,21 @@ __device__ __forceinline__ double fprime(double d, int noncompact) { return nonc
 // (the same operands in the same order: results identical to evaluating it twice).
 constexpr int kFinishChunk = 32;
 
+__device__ __forceinline__ void force_finish_unit(const Geo& g, const BosonParams& bp, const double* __restrict__ theta,
+                                                  const double* __restrict__ dSf, double* __restrict__ F, long long k);
+
 __global__ void force_finish_kernel(Geo g, BosonParams bp, const double* __restrict__ theta,
                                     const double* __restrict__ dSf, double* __restrict__ F, int nchunk) {
   const long long nt = (long long)g.V * nchunk;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nt;
-       k += (long long)gridDim.x * blockDim.x) {
+       k += (long long)gridDim.x * blockDim.x)
+    force_finish_unit(g, bp, theta, dSf, F, k);
+}
+
+// One (site, chunk of kFinishChunk slices) unit of the force's bosonic part.
+__device__ __forceinline__ void force_finish_unit(const Geo& g, const BosonParams& bp, const double* __restrict__ theta,
+                                                  const double* __restrict__ dSf, double* __restrict__ F, long long k) {
+  {
     const int ch = (int)(k / g.V);
     const int s = (int)(k - (long long)ch * g.V);
     const int x = s % g.L, y = s / g.L;
@@ -399,17 +422,21 @@ __global__ void force_finish_kernel(Geo g, BosonParams bp, const double* __restr
       const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
       const double2 thp = reinterpret_cast<const double2*>(theta + (size_t)tp * g.V * 2)[s];
       const double dnext[2] = {fprime(thp.x - th.x, bp.noncompact), fprime(thp.y - th.y, bp.noncompact)};
-      double dB[2] = {bp.cK * (dprev[0] - dnext[0]), bp.cK * (dprev[1] - dnext[1])};
+      // rounding written out (products rounded, no fused multiply-add) so that the
+      // single-chain and the batched kernel that inline this give identical bits
+      double dB[2] = {__dmul_rn(bp.cK, dprev[0] - dnext[0]), __dmul_rn(bp.cK, dprev[1] - dnext[1])};
       if (bp.Kdtau != 0.0) {
         const double* ths = theta + (size_t)tau * g.V * 2;
         const int xm = (x == 0) ? g.L - 1 : x - 1, ym = (y == 0) ? g.L - 1 : y - 1;
         const double s00 = sin(curl_at(ths, g.L, x, y));
-        dB[0] += -bp.Kdtau * s00 + bp.Kdtau * sin(curl_at(ths, g.L, x, ym));
-        dB[1] += bp.Kdtau * s00 - bp.Kdtau * sin(curl_at(ths, g.L, xm, y));
+        dB[0] = __dadd_rn(dB[0], __dadd_rn(__dmul_rn(-bp.Kdtau, s00),
+                                            __dmul_rn(bp.Kdtau, sin(curl_at(ths, g.L, x, ym)))));
+        dB[1] = __dadd_rn(dB[1], __dsub_rn(__dmul_rn(bp.Kdtau, s00),
+                                            __dmul_rn(bp.Kdtau, sin(curl_at(ths, g.L, xm, y)))));
       }
       const size_t i = (size_t)tau * g.V + s;
       const double2 f = reinterpret_cast<const double2*>(dSf)[i];
-      reinterpret_cast<double2*>(F)[i] = make_double2(-f.x - dB[0], -f.y - dB[1]);
+      reinterpret_cast<double2*>(F)[i] = make_double2(__dsub_rn(-f.x, dB[0]), __dsub_rn(-f.y, dB[1]));
       dprev[0] = dnext[0];
       dprev[1] = dnext[1];
       th = thp;
@@ -428,16 +455,16 @@ cudaError_t launch_force_finish(const Geo& g, const BosonParams& bp, const doubl
 __global__ void kick_kernel(long long nb, double* __restrict__ p, const double* __restrict__ F, double h) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
        i += (long long)gridDim.x * blockDim.x)
-    p[i] += F[i] * h;
+    p[i] = fma(F[i], h, p[i]);
 }
 
 __global__ void kick_drift_kernel(long long nb, double* __restrict__ p, double* __restrict__ theta,
                                   const double* __restrict__ F, double h, double dt) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
        i += (long long)gridDim.x * blockDim.x) {
-    const double pn = p[i] + F[i] * h;
+    const double pn = fma(F[i], h, p[i]);  // fused as in the batched kernel
     p[i] = pn;
-    theta[i] += (2.0 * pn) * dt;
+    theta[i] = fma(2.0 * pn, dt, theta[i]);
   }
 }
 
@@ -455,14 +482,15 @@ cudaError_t launch_kick_drift(long long nb, double* p, double* theta, const doub
 // ---------------------------------------------------------------------------
 // Hamiltonian terms: S_B(theta), sum p^2, Re <a, b>.  Per-block partials, then
 // one block sums them in a fixed order.
-__global__ void action_partials_kernel(Geo g, BosonParams bp, const double* __restrict__ theta,
-                                       const double* __restrict__ p, const double2* __restrict__ a,
-                                       const double2* __restrict__ b, double* __restrict__ part) {
+// Partials of block j of nb (the same element grouping for a chain alone or in a batch).
+__device__ __forceinline__ void action_partials_block(const Geo& g, const BosonParams& bp,
+                                                      const double* __restrict__ theta, const double* __restrict__ p,
+                                                      const double2* __restrict__ a, const double2* __restrict__ b,
+                                                      double* __restrict__ part, int j, int nb) {
   __shared__ double red[32];
   const long long n = (long long)g.V * g.Ntau;
   double kin = 0.0, pot = 0.0, pp = 0.0, ab = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = j * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) {
     const int tau = (int)(i / g.V);
     const int s = (int)(i - (long long)tau * g.V);
     const int tp = (tau + 1 == g.Ntau) ? 0 : tau + 1;
@@ -470,28 +498,42 @@ __global__ void action_partials_kernel(Geo g, BosonParams bp, const double* __re
     const double* thp = theta + (size_t)tp * g.V * 2;
     for (int c = 0; c < 2; ++c) {
       const double d = thp[2 * s + c] - th[2 * s + c];
-      kin += bp.noncompact ? d * d : 1.0 - cos(d);
+      kin += bp.noncompact ? __dmul_rn(d, d) : 1.0 - cos(d);
     }
     if (bp.Kdtau != 0.0) pot += cos(curl_at(th, g.L, s % g.L, s / g.L));
     if (p) {
       const double2 pv = reinterpret_cast<const double2*>(p)[i];
-      pp += pv.x * pv.x + pv.y * pv.y;
+      pp += cdot_re(pv, pv);
     }
     if (a && b) ab += cdot_re(a[i], b[i]);
   }
   double t;
   t = block_sum(kin, red);
-  if (threadIdx.x == 0) part[4 * blockIdx.x + 0] = t;
+  if (threadIdx.x == 0) part[4 * j + 0] = t;
   t = block_sum(pot, red);
-  if (threadIdx.x == 0) part[4 * blockIdx.x + 1] = t;
+  if (threadIdx.x == 0) part[4 * j + 1] = t;
   t = block_sum(pp, red);
-  if (threadIdx.x == 0) part[4 * blockIdx.x + 2] = t;
+  if (threadIdx.x == 0) part[4 * j + 2] = t;
   t = block_sum(ab, red);
-  if (threadIdx.x == 0) part[4 * blockIdx.x + 3] = t;
+  if (threadIdx.x == 0) part[4 * j + 3] = t;
 }
+
+__global__ void action_partials_kernel(Geo g, BosonParams bp, const double* __restrict__ theta,
+                                       const double* __restrict__ p, const double2* __restrict__ a,
+                                       const double2* __restrict__ b, double* __restrict__ part) {
+  action_partials_block(g, bp, theta, p, a, b, part, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void action_finalize_warp(const BosonParams& bp, const double* __restrict__ part, int nblk,
+                                                     double* __restrict__ terms);
 
 __global__ void action_finalize_kernel(BosonParams bp, const double* __restrict__ part, int nblk,
                                        double* __restrict__ terms) {
+  action_finalize_warp(bp, part, nblk, terms);
+}
+
+__device__ __forceinline__ void action_finalize_warp(const BosonParams& bp, const double* __restrict__ part, int nblk,
+                                                     double* __restrict__ terms) {
   double s[4];
   for (int c = 0; c < 4; ++c) {
     double acc = 0.0;
@@ -500,7 +542,7 @@ __global__ void action_finalize_kernel(BosonParams bp, const double* __restrict_
     s[c] = __shfl_sync(0xffffffffu, acc, 0);
   }
   if (threadIdx.x == 0) {
-    terms[0] = bp.cK * s[0] + bp.Kdtau * s[1];
+    terms[0] = __dadd_rn(__dmul_rn(bp.cK, s[0]), __dmul_rn(bp.Kdtau, s[1]));
     terms[1] = s[2];
     terms[2] = s[3];
   }
@@ -558,21 +600,26 @@ __device__ inline void gauss_pair(uint64_t seed, uint32_t stream, uint64_t count
   *g1 = r * sn;
 }
 
+// p ~ N(0, 1/2) per bond (stream 0) and R ~ CN(0, 1) per site (stream 1) at site i.
+__device__ __forceinline__ void draw_site(uint64_t seed, uint64_t counter, double* __restrict__ p,
+                                          double2* __restrict__ R, long long i) {
+  const double h = 0.70710678118654752440;  // sqrt(1/2)
+  double g0, g1;
+  if (p) {
+    gauss_pair(seed, 0u, counter, (uint32_t)i, &g0, &g1);
+    reinterpret_cast<double2*>(p)[i] = make_double2(g0 * h, g1 * h);
+  }
+  if (R) {
+    gauss_pair(seed, 1u, counter, (uint32_t)i, &g0, &g1);
+    R[i] = make_double2(g0 * h, g1 * h);
+  }
+}
+
 __global__ void draw_kernel(long long n, uint64_t seed, uint64_t counter, double* __restrict__ p,
                             double2* __restrict__ R) {
-  const double h = 0.70710678118654752440;  // sqrt(1/2)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    double g0, g1;
-    if (p) {
-      gauss_pair(seed, 0u, counter, (uint32_t)i, &g0, &g1);
-      reinterpret_cast<double2*>(p)[i] = make_double2(g0 * h, g1 * h);
-    }
-    if (R) {
-      gauss_pair(seed, 1u, counter, (uint32_t)i, &g0, &g1);
-      R[i] = make_double2(g0 * h, g1 * h);
-    }
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    draw_site(seed, counter, p, R, i);
 }
 
 cudaError_t launch_draw(long long n_sites, uint64_t seed, uint64_t counter, double* p, double2* R,
@@ -668,6 +715,155 @@ __global__ void fp64_probe_kernel(double* out, int iters, double a, double b) {
 
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s) {
   fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched trajectory kernels: every chain's element loop keeps the grouping of its
+// own launch (block j of nb), so a batch reproduces single-chain runs bit for bit.
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t counter) {
+  U4 c = {{0u, 2u, (uint32_t)counter, (uint32_t)(counter >> 32)}};
+  const U4 w = philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return u53(w.v[0], w.v[1]);
+}
+
+__global__ void __launch_bounds__(256) batch_elementwise_kernel(const ChainDesc* __restrict__ descs,
+                                                                const int4* __restrict__ tab, int op,
+                                                                const uint64_t* __restrict__ counter) {
+  const int4 e = tab[blockIdx.x];
+  const ChainDesc& d = descs[e.x];
+  if (op == BT_RESTORE && d.info->accepted) return;
+  const long long n = d.n;
+  const long long i0 = e.y * (long long)blockDim.x + threadIdx.x, step = (long long)e.z * blockDim.x;
+  switch (op) {
+    case BT_DRAW: {
+      const uint64_t ctr = *counter;
+      for (long long i = i0; i < n; i += step) draw_site(d.seed, ctr, d.p, d.R, i);
+    } break;
+    case BT_LINKS:
+      for (long long i = i0; i < n; i += step) links_site(d.g, d.theta, d.t1, d.t2, d.U64, nullptr, nullptr, i);
+      break;
+    case BT_ZERO_X:
+      for (long long i = i0; i < n; i += step) d.X[i] = make_double2(0.0, 0.0);
+      break;
+    case BT_SAVE:
+      for (long long i = i0; i < 2 * n; i += step) d.th0[i] = d.theta[i];
+      break;
+    case BT_RESTORE:
+      for (long long i = i0; i < 2 * n; i += step) d.theta[i] = d.th0[i];
+      break;
+    case BT_KICK_DRIFT: {  // p += F dt/2; theta += 2 p dt (as kick_drift_kernel)
+      const double h = d.dt / 2, dt = d.dt;
+      for (long long i = i0; i < 2 * n; i += step) {
+        const double pn = fma(d.F[i], h, d.p[i]);
+        d.p[i] = pn;
+        d.theta[i] = fma(2.0 * pn, dt, d.theta[i]);
+      }
+    } break;
+    default: {  // BT_KICK: p += F dt/2 (as kick_kernel)
+      const double h = d.dt / 2;
+      for (long long i = i0; i < 2 * n; i += step) d.p[i] = fma(d.F[i], h, d.p[i]);
+    } break;
+  }
+}
+
+cudaError_t launch_batch_elementwise(const ChainDesc* d, const int4* tab, int nblocks, int op, const uint64_t* counter,
+                                     cudaStream_t s) {
+  batch_elementwise_kernel<<<nblocks, 256, 0, s>>>(d, tab, op, counter);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) batch_action_partials_kernel(const ChainDesc* __restrict__ descs,
+                                                                    const int4* __restrict__ tab, int which) {
+  const int4 e = tab[blockIdx.x];
+  const ChainDesc& d = descs[e.x];
+  if (which == 0) action_partials_block(d.g, d.bp, d.theta, d.p, d.R, d.R, d.part_act, e.y, e.z);
+  else action_partials_block(d.g, d.bp, d.theta, d.p, d.eta, d.X, d.part_act, e.y, e.z);
+}
+
+__global__ void batch_action_finalize_kernel(const ChainDesc* __restrict__ descs, int which) {
+  const ChainDesc& d = descs[blockIdx.x];
+  action_finalize_warp(d.bp, d.part_act, d.act_grid, d.terms + 3 * which);
+}
+
+cudaError_t launch_batch_action(const ChainDesc* d, const int4* tab, int nblocks, int nchains, int which,
+                                cudaStream_t s) {
+  batch_action_partials_kernel<<<nblocks, 256, 0, s>>>(d, tab, which);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_action_finalize_kernel<<<nchains, 32, 0, s>>>(d, which);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) batch_force_finish_kernel(const ChainDesc* __restrict__ descs,
+                                                                 const int4* __restrict__ tab) {
+  const int4 e = tab[blockIdx.x];
+  const ChainDesc& d = descs[e.x];
+  const long long nt = (long long)d.g.V * ((d.g.Ntau + kFinishChunk - 1) / kFinishChunk);
+  for (long long k = e.y * (long long)blockDim.x + threadIdx.x; k < nt; k += (long long)e.z * blockDim.x)
+    force_finish_unit(d.g, d.bp, d.theta, d.dSf, d.F, k);
+}
+
+cudaError_t launch_batch_force_finish(const ChainDesc* d, const int4* tab, int nblocks, cudaStream_t s) {
+  batch_force_finish_kernel<<<nblocks, 256, 0, s>>>(d, tab);
+  return cudaGetLastError();
+}
+
+__global__ void batch_info_init_kernel(const ChainDesc* __restrict__ descs, int nchains,
+                                       const uint64_t* __restrict__ counter) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchains) return;
+  const ChainDesc& d = descs[c];
+  hqmc_traj_info t = {};
+  t.u = philox_uniform(d.seed, *counter);
+  *d.info = t;
+}
+
+cudaError_t launch_batch_info_init(const ChainDesc* d, int nchains, const uint64_t* counter, cudaStream_t s) {
+  batch_info_init_kernel<<<(nchains + 63) / 64, 64, 0, s>>>(d, nchains, counter);
+  return cudaGetLastError();
+}
+
+// After a batched solve: count it, add its iterations, keep the largest true
+// residual and the worst status (the report holds the last true residual of a
+// converged chain, or the residual recomputed for an unconverged one).
+__global__ void batch_solve_close_kernel(const ChainDesc* __restrict__ descs, int nchains) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchains) return;
+  const ChainDesc& d = descs[c];
+  hqmc_traj_info* t = d.info;
+  const CgState* st = d.st;
+  const int status = solve_status(st->done, false);
+  t->cg_solves += 1;
+  t->cg_iterations += st->k;
+  const double res = st->bb > 0 ? sqrt(d.report[0] / st->bb) : 0.0;
+  t->max_true_residual = fmax(t->max_true_residual, res);
+  if (t->status == HQMC_OK) t->status = status;
+}
+
+cudaError_t launch_batch_solve_close(const ChainDesc* d, int nchains, cudaStream_t s) {
+  batch_solve_close_kernel<<<(nchains + 63) / 64, 64, 0, s>>>(d, nchains);
+  return cudaGetLastError();
+}
+
+// H0 = S_B + sum p^2 + R^dagger R, H1 = S_B + sum p^2 + phi^dagger X; accept iff u < e^{-(H1 - H0)}.
+__global__ void batch_metropolis_kernel(const ChainDesc* __restrict__ descs, int nchains) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchains) return;
+  const ChainDesc& d = descs[c];
+  hqmc_traj_info* t = d.info;
+  const double* tm = d.terms;
+  t->H0 = tm[0] + tm[1] + tm[2];
+  t->H1 = tm[3] + tm[4] + tm[5];
+  t->dH = t->H1 - t->H0;
+  const bool fin = isfinite(t->dH);
+  if (!fin && t->status == HQMC_OK) t->status = HQMC_ENONFINITE;
+  const bool ok = t->status == HQMC_OK || t->status == HQMC_ENOTCONV;
+  t->accepted = (ok && fin && t->u < exp(-t->dH)) ? 1 : 0;
+}
+
+cudaError_t launch_batch_metropolis(const ChainDesc* d, int nchains, cudaStream_t s) {
+  batch_metropolis_kernel<<<(nchains + 63) / 64, 64, 0, s>>>(d, nchains);
   return cudaGetLastError();
 }
 

@@ -93,3 +93,54 @@ def test_batched_preconditioned_trajectory_equals_independent_trajectories(hq):
         assert infos[i]["dH"] == info1["dH"] and infos[i]["accepted"] == info1["accepted"], i
         assert infos[i]["cg_iterations"] == info1["cg_iterations"]
         assert torch.equal(thetas[i], t1), i
+
+
+def test_batched_trajectory_graph_replays_with_new_counters(hq):
+    """The trajectory graph is captured once and replayed: the trajectory counter,
+    seeds and dt are read from device memory at every launch, so two trajectories
+    in a row still equal two single-chain trajectories in a row."""
+    th0 = [inputs.theta_hot(L, N, 1100 + i) for i, (L, N) in enumerate(LATS)]
+    seeds = [41 + i for i in range(len(LATS))]
+    dts = [0.02, 0.015, 0.01, 0.02]
+    with hq.Batch(LATS) as b:
+        thetas = [torch.from_numpy(t).cuda() for t in th0]
+        inf_a = b.trajectory(thetas, seeds, traj_counter=7, nsteps=2, dts=dts, tol=1e-10)
+        inf_b = b.trajectory(thetas, seeds, traj_counter=8, nsteps=2, dts=[d * 0.5 for d in dts], tol=1e-10)
+    for i, (L, N) in enumerate(LATS):
+        with hq.Config(L, N, variant=1) as cfg:
+            t1 = torch.from_numpy(th0[i]).cuda()
+            a = hq.trajectory(cfg, t1, seed=seeds[i], traj_counter=7, nsteps=2, dt=dts[i], tol=1e-10)
+            bb = hq.trajectory(cfg, t1, seed=seeds[i], traj_counter=8, nsteps=2, dt=dts[i] * 0.5, tol=1e-10)
+        assert inf_a[i]["dH"] == a["dH"] and inf_b[i]["dH"] == bb["dH"], i
+        assert inf_a[i]["u"] == a["u"] and inf_b[i]["u"] == bb["u"]
+        assert torch.equal(thetas[i], t1), i
+
+
+@pytest.mark.parametrize("solver", ["cg64", "pcg64"])
+def test_batched_trajectory_against_oracle(hq, solver):
+    """Each chain of a batched trajectory against the FP64 oracle's trajectory with the
+    same Philox draws (p, R, u from oracle/philox.py) and CG at 1e-12: dH to 1e-7 and
+    the field to 1e-8, as for single-chain trajectories."""
+    import oracle
+    from oracle import philox
+    lats = [(4, 8), (6, 12), (8, 16)]
+    th0 = [inputs.theta_ordered(L, N, 1200 + i, tau_walk=0.0) for i, (L, N) in enumerate(lats)]
+    seeds = [51 + i for i in range(len(lats))]
+    dts = [0.02, 0.02, 0.015]
+    ctr = 9
+    with hq.Batch(lats) as b:
+        b.set_solver(solver)
+        thetas = [torch.from_numpy(t).cuda() for t in th0]
+        infos = b.trajectory(thetas, seeds, traj_counter=ctr, nsteps=3, dts=dts, tol=1e-12)
+    for i, (L, N) in enumerate(lats):
+        lat = oracle.Lattice(L, N)
+        p = philox.draw_momenta(seeds[i], ctr, L, N)
+        R = philox.draw_pseudofermion(seeds[i], ctr, L, N)
+        u = philox.draw_metropolis(seeds[i], ctr)
+        ref = oracle.trajectory(lat, th0[i], p, R, u=u, nsteps=3, dt=dts[i], tol=1e-12)
+        assert infos[i]["status"] == 0 and infos[i]["max_true_residual"] <= 1e-12
+        assert abs(infos[i]["u"] - u) == 0.0
+        assert abs(infos[i]["dH"] - ref["dH"]) < 1e-7, (i, infos[i]["dH"], ref["dH"])
+        assert bool(infos[i]["accepted"]) == ref["accepted"]
+        want = ref["theta"] if ref["accepted"] else th0[i]
+        assert np.max(np.abs(thetas[i].cpu().numpy() - want)) < 1e-8
