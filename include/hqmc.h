@@ -285,6 +285,22 @@ HQMC_API int hqmc_estimate(hqmc_config* cfg, const double* theta, uint64_t seed,
                            double tol, int maxit, int solver, void* Gxi, void* xi, double* g_host,
                            hqmc_solve_info* infos, void* stream);
 
+/* The same estimate with the right-hand sides solved as a set on one field:
+ * every solve after the first starts from the Galerkin projection of its solution
+ * onto the earlier ones, x0 = sum_{i<k} c_i X_i with G c = (<X_i, R_k>)_i and
+ * G_ij = <X_i, (M^dagger M) X_j> = <X_i, R_j> (known from the earlier solves, no
+ * extra operator application).  The solutions share the lowest modes of
+ * M^dagger M, which dominate them and set the iteration count, so x0 already
+ * carries most of them (not a method of the paper: its Methods solve the
+ * N_rv = 40 systems independently).  Gxi is required (the earlier solutions are
+ * the projection basis).  If the small Hermitian system is numerically singular
+ * (pivot below 1e-12), or 2 nrv (blocks + 1) doubles exceed the config's scratch
+ * vector (not at the paper's sizes), a solve starts from the previous solution as
+ * in hqmc_estimate.  Outputs, errors and synchronisation as hqmc_estimate. */
+HQMC_API int hqmc_estimate_projected(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter,
+                                     int nrv, double tol, int maxit, int solver, void* Gxi, void* xi,
+                                     double* g_host, hqmc_solve_info* infos, void* stream);
+
 /* ---- force (Supplement SI, Eqs. (force&CG) and (fermion_force)) -------- */
 
 /* Given X = (M^dagger M)^{-1} phi (complex double), writes the total force

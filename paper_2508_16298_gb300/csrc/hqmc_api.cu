@@ -1480,41 +1480,129 @@ int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* 
   return solve(cfg, (const double2*)phi, (double2*)x, tol, maxit, solver, info, s);
 }
 
-int hqmc_estimate(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
-                  int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos, void* stream) {
-  if (!cfg) return HQMC_EINVAL;
-  if (!aligned16(theta) || (Gxi && !aligned16(Gxi)) || (xi && !aligned16(xi)))
-    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
-  if (nrv < 1) return fail(cfg, HQMC_EINVAL, "nrv must be >= 1");
-  if (!(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "tol must be > 0 and maxit >= 0");
-  const size_t vb = (size_t)cfg->n * sizeof(double2);
-  if (Gxi && xi && overlap(Gxi, vb * nrv, xi, vb * nrv)) return fail(cfg, HQMC_EINVAL, "Gxi and xi overlap");
-  RET(check_solver(cfg, solver));
-  RET(check_device(cfg));
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Solves the Hermitian positive definite k x k system A c = b in place (b -> c) by
+// Cholesky; false if a pivot falls below 1e-12 of its diagonal entry (the earlier
+// solutions are then too close to linearly dependent for the projection).
+bool hermitian_solve(int k, std::vector<double>& A, std::vector<double>& b) {
+  // A: k x k complex, row-major, interleaved (re, im); b: k complex
+  auto re = [&](int i, int j) -> double& { return A[2 * (i * k + j)]; };
+  auto im = [&](int i, int j) -> double& { return A[2 * (i * k + j) + 1]; };
+  for (int j = 0; j < k; ++j) {
+    double d = re(j, j);
+    for (int p = 0; p < j; ++p) d -= re(j, p) * re(j, p) + im(j, p) * im(j, p);
+    if (!(d > 1e-12 * std::fabs(re(j, j)))) return false;
+    const double ljj = std::sqrt(d);
+    re(j, j) = ljj;
+    im(j, j) = 0.0;
+    for (int i = j + 1; i < k; ++i) {
+      double sr = re(i, j), si = im(i, j);
+      for (int p = 0; p < j; ++p) {  // - L_ip conj(L_jp)
+        sr -= re(i, p) * re(j, p) + im(i, p) * im(j, p);
+        si -= im(i, p) * re(j, p) - re(i, p) * im(j, p);
+      }
+      re(i, j) = sr / ljj;
+      im(i, j) = si / ljj;
+    }
+  }
+  for (int i = 0; i < k; ++i) {  // L y = b
+    double sr = b[2 * i], si = b[2 * i + 1];
+    for (int p = 0; p < i; ++p) {
+      sr -= re(i, p) * b[2 * p] - im(i, p) * b[2 * p + 1];
+      si -= re(i, p) * b[2 * p + 1] + im(i, p) * b[2 * p];
+    }
+    b[2 * i] = sr / re(i, i);
+    b[2 * i + 1] = si / re(i, i);
+  }
+  for (int i = k - 1; i >= 0; --i) {  // L^dagger c = y
+    double sr = b[2 * i], si = b[2 * i + 1];
+    for (int p = i + 1; p < k; ++p) {  // - conj(L_pi) c_p
+      sr -= re(p, i) * b[2 * p] + im(p, i) * b[2 * p + 1];
+      si -= re(p, i) * b[2 * p + 1] - im(p, i) * b[2 * p];
+    }
+    b[2 * i] = sr / re(i, i);
+    b[2 * i + 1] = si / re(i, i);
+  }
+  return true;
+}
+
+// Stochastic estimation (Methods, "Stochastic estimation of fermionic observables").
+// project: every solve after the first starts from the Galerkin projection of its
+// solution onto the earlier solutions X_0..X_{k-1} (all on the same field):
+// x0 = sum_i c_i X_i with G c = (<X_i, R_k>)_i, G_ij = <X_i, O X_j> = <X_i, R_j>.
+// The low modes of O, which dominate every solution and set the iteration count,
+// are then mostly present in x0.  Needs the solutions stored (Gxi).
+int estimate_impl(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
+                  int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos, bool project,
+                  cudaStream_t s) {
   RET(links(cfg, theta, true, solver_fp32(solver), s, false, solver_base(solver) == HQMC_SOLVER_LEARNED));
+  const size_t vb = (size_t)cfg->n * sizeof(double2);
   double sum_re = 0.0, sum_im = 0.0;
   int status = HQMC_OK;
   double2* prev = nullptr;
+  // projection workspace: the many-dot partials and results in the scratch vector
+  const int grid = cfg->act_grid;
+  double* dscratch = reinterpret_cast<double*>(cfg->vscratch);
+  const bool room = 2 * (size_t)grid * nrv + 2 * (size_t)nrv <= 2 * (size_t)cfg->n;
+  std::vector<double> G(project ? 2 * (size_t)nrv * nrv : 0, 0.0);
+  std::vector<double> col, A;
   for (int k = 0; k < nrv; ++k) {
     double2* v = xi ? (double2*)xi + (size_t)k * cfg->n : cfg->Rw;           // xi_k
     double2* X = Gxi ? (double2*)Gxi + (size_t)k * cfg->n : cfg->Xw;          // M^{-1} xi_k
     LK(1, launch_draw_vector(cfg->n, seed, 3u, counter + (uint64_t)k, v, s));
     LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, v, cfg->eta, 1, s));  // R = M^dagger xi
-    if (k == 0)
-      CK(cudaMemsetAsync(X, 0, vb, s));
-    else if (prev != X)
-      CK(cudaMemcpyAsync(X, prev, vb, cudaMemcpyDeviceToDevice, s));           // start from the previous solution
+    bool guessed = false;
+    if (project && k > 0 && room) {
+      const double2* X0 = (const double2*)Gxi;
+      LK(2, launch_cdot_many(cfg->n, X0, cfg->n, k, cfg->eta, grid, dscratch, dscratch + 2 * (size_t)grid * k, s));
+      col.assign(2 * (size_t)k, 0.0);
+      CK(cudaMemcpyAsync(col.data(), dscratch + 2 * (size_t)grid * k, 2 * (size_t)k * sizeof(double),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      A.assign(2 * (size_t)k * k, 0.0);
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+          A[2 * (i * k + j)] = G[2 * (i * nrv + j)];
+          A[2 * (i * k + j) + 1] = G[2 * (i * nrv + j) + 1];
+        }
+      std::vector<double> c = col;
+      if (hermitian_solve(k, A, c)) {
+        CK(cudaMemsetAsync(X, 0, vb, s));
+        for (int i = 0; i < k; ++i)
+          LK(1, launch_caxpy(cfg->n, c[2 * i], c[2 * i + 1], X0 + (size_t)i * cfg->n, X, s));
+        guessed = true;
+      }
+      for (int i = 0; i < k; ++i) {  // G_ik = <X_i, R_k>, G_ki = conj(G_ik)
+        G[2 * (i * nrv + k)] = col[2 * i];
+        G[2 * (i * nrv + k) + 1] = col[2 * i + 1];
+        G[2 * (k * nrv + i)] = col[2 * i];
+        G[2 * (k * nrv + i) + 1] = -col[2 * i + 1];
+      }
+    }
+    if (!guessed) {
+      if (k == 0)
+        CK(cudaMemsetAsync(X, 0, vb, s));
+      else if (prev != X)
+        CK(cudaMemcpyAsync(X, prev, vb, cudaMemcpyDeviceToDevice, s));  // start from the previous solution
+    }
     hqmc_solve_info si{};
     const int rc = solve(cfg, cfg->eta, X, tol, maxit, solver, &si, s);
     if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
     status = merge_status(status, rc);
     if (infos) infos[k] = si;
     LK(2, launch_cdot(cfg->n, v, X, cfg->act_grid, cfg->part_act, cfg->terms + 4, s));
-    CK(cudaMemcpyAsync(cfg->terms_h + 4, cfg->terms + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (project) LK(2, launch_cdot(cfg->n, X, cfg->eta, cfg->act_grid, cfg->part_act, cfg->terms + 6, s));
+    CK(cudaMemcpyAsync(cfg->terms_h + 4, cfg->terms + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     sum_re += cfg->terms_h[4];
     sum_im += cfg->terms_h[5];
+    if (project) {
+      G[2 * (k * nrv + k)] = cfg->terms_h[6];  // <X_k, R_k> (real up to the solve's tolerance)
+      G[2 * (k * nrv + k) + 1] = 0.0;
+    }
     prev = X;
   }
   if (g_host) {
@@ -1523,6 +1611,40 @@ int hqmc_estimate(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t
     g_host[1] = sum_im * norm;
   }
   return status;
+}
+
+int check_estimate(hqmc_config* cfg, const double* theta, int nrv, double tol, int maxit, int solver, void* Gxi,
+                   void* xi) {
+  if (!aligned16(theta) || (Gxi && !aligned16(Gxi)) || (xi && !aligned16(xi)))
+    return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  if (nrv < 1) return fail(cfg, HQMC_EINVAL, "nrv must be >= 1");
+  if (!(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "tol must be > 0 and maxit >= 0");
+  const size_t vb = (size_t)cfg->n * sizeof(double2);
+  if (Gxi && xi && overlap(Gxi, vb * nrv, xi, vb * nrv)) return fail(cfg, HQMC_EINVAL, "Gxi and xi overlap");
+  RET(check_solver(cfg, solver));
+  return check_device(cfg);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hqmc_estimate(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
+                  int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  RET(check_estimate(cfg, theta, nrv, tol, maxit, solver, Gxi, xi));
+  return estimate_impl(cfg, theta, seed, counter, nrv, tol, maxit, solver, Gxi, xi, g_host, infos, false,
+                       (cudaStream_t)stream);
+}
+
+int hqmc_estimate_projected(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv,
+                            double tol, int maxit, int solver, void* Gxi, void* xi, double* g_host,
+                            hqmc_solve_info* infos, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!Gxi) return fail(cfg, HQMC_EINVAL, "the projected estimate needs the solution array Gxi");
+  RET(check_estimate(cfg, theta, nrv, tol, maxit, solver, Gxi, xi));
+  return estimate_impl(cfg, theta, seed, counter, nrv, tol, maxit, solver, Gxi, xi, g_host, infos, true,
+                       (cudaStream_t)stream);
 }
 
 int hqmc_force(hqmc_config* cfg, const double* theta, const void* X, double* F, double* dSf, void* stream) {

@@ -355,6 +355,11 @@ cudaError_t launch_draw_vector(long long n_sites, uint64_t seed, uint32_t stream
 cudaError_t launch_resid_from_fp32(long long n, const double2* phi, const float2* y, double2* r, cudaStream_t s);
 cudaError_t launch_cdot(long long n, const double2* a, const double2* b, int grid, double* part, double* out,
                         cudaStream_t s);
+// out[2 i], out[2 i + 1] = <X_i, b> (re, im) for X_i = X + i * stride, i < k; part holds 2 * grid * k doubles.
+cudaError_t launch_cdot_many(long long n, const double2* X, long long stride, int k, const double2* b, int grid,
+                             double* part, double* out, cudaStream_t s);
+// y += (cr + i ci) x
+cudaError_t launch_caxpy(long long n, double cr, double ci, const double2* x, double2* y, cudaStream_t s);
 // FP64 FMA throughput probe (16 flops per thread per iteration).
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);
 

@@ -689,6 +689,59 @@ __global__ void cdot_finalize_kernel(const double* __restrict__ part, int nblk, 
   }
 }
 
+// <X_i, b> for i < k, X_i = X + i * stride: partials (grid per vector), then one warp
+// per vector sums them in a fixed order into out[2 i], out[2 i + 1] (re, im).
+__global__ void cdot_many_partials_kernel(long long n, const double2* __restrict__ X, long long stride,
+                                          const double2* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[32];
+  const double2* a = X + (size_t)blockIdx.y * stride;
+  double re = 0.0, im = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    re += fma(x.x, y.x, __dmul_rn(x.y, y.y));
+    im += fma(x.x, y.y, -__dmul_rn(x.y, y.x));
+  }
+  const size_t o = 2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+  double t = block_sum(re, red);
+  if (threadIdx.x == 0) part[o] = t;
+  t = block_sum(im, red);
+  if (threadIdx.x == 0) part[o + 1] = t;
+}
+
+__global__ void cdot_many_finalize_kernel(const double* __restrict__ part, int grid, double* __restrict__ out) {
+  const double* p = part + 2 * (size_t)blockIdx.x * grid;
+  for (int c = 0; c < 2; ++c) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < grid; k += 32) acc += p[2 * k + c];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) out[2 * blockIdx.x + c] = acc;
+  }
+}
+
+cudaError_t launch_cdot_many(long long n, const double2* X, long long stride, int k, const double2* b, int grid,
+                             double* part, double* out, cudaStream_t s) {
+  cdot_many_partials_kernel<<<dim3(grid, k), 256, 0, s>>>(n, X, stride, b, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cdot_many_finalize_kernel<<<k, 32, 0, s>>>(part, grid, out);
+  return cudaGetLastError();
+}
+
+// y += c x (complex c).
+__global__ void caxpy_kernel(long long n, double cr, double ci, const double2* __restrict__ x, double2* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i], w = y[i];
+    y[i] = make_double2(fma(cr, v.x, fma(-ci, v.y, w.x)), fma(cr, v.y, fma(ci, v.x, w.y)));
+  }
+}
+
+cudaError_t launch_caxpy(long long n, double cr, double ci, const double2* x, double2* y, cudaStream_t s) {
+  caxpy_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, cr, ci, x, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cdot(long long n, const double2* a, const double2* b, int grid, double* part, double* out,
                         cudaStream_t s) {
   cdot_partials_kernel<<<grid, 256, 0, s>>>(n, a, b, part);

@@ -37,7 +37,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_launch_count", "hqmc_get_launch_shape",
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_apply_precond", "hqmc_get_precond", "hqmc_get_precond_shape",
            "hqmc_set_precond_fused", "hqmc_cg_solve",
-           "hqmc_estimate",
+           "hqmc_estimate", "hqmc_estimate_projected",
            "hqmc_force", "hqmc_action_terms",
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
@@ -95,6 +95,8 @@ _sig = {
     "hqmc_cg_solve": ([_vp, _vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_estimate": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _i, _d, _i, _i, _vp, _vp,
                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), _vp], _i),
+    "hqmc_estimate_projected": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _i, _d, _i, _i, _vp, _vp,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_force": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hqmc_action_terms": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_draw": ([_vp, _u64, _u64, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
@@ -306,20 +308,24 @@ def cg_solve(cfg: Config, theta, phi, x=None, tol: float = 1e-8, maxit: int = 10
 
 
 def estimate(cfg: Config, theta, nrv: int, seed: int = 0, counter: int = 0, tol: float = 1e-8,
-             maxit: int = 100000, solver="cg64", want_vectors: bool = False, raise_on_fail: bool = True):
-    """Stochastic estimation with nrv CN(0, 1) vectors (hqmc_estimate).  Returns
-    (g, infos, Gxi, xi): g the complex estimate of the mean diagonal of M^{-1}, the
-    per-vector solve infos, and (if want_vectors) M^{-1} xi_k and xi_k as tensors of
-    shape (nrv, Ntau, L, L)."""
+             maxit: int = 100000, solver="cg64", want_vectors: bool = False, raise_on_fail: bool = True,
+             projected: bool = False, Gxi=None):
+    """Stochastic estimation with nrv CN(0, 1) vectors (hqmc_estimate, or with
+    projected=True hqmc_estimate_projected, which needs the solutions: Gxi is then
+    allocated here unless given).  Returns (g, infos, Gxi, xi): g the complex estimate
+    of the mean diagonal of M^{-1}, the per-vector solve infos, and (if want_vectors)
+    M^{-1} xi_k and xi_k as tensors of shape (nrv, Ntau, L, L)."""
     cfg._bonds(theta, "theta")
-    Gxi = xi = None
-    if want_vectors:
+    xi = None
+    if Gxi is None and (want_vectors or projected):
         Gxi = torch.empty((nrv, cfg.Ntau, cfg.L, cfg.L), dtype=torch.complex128, device=theta.device)
+    if want_vectors:
         xi = torch.empty_like(Gxi)
     g = (ctypes.c_double * 2)()
     infos = (SolveInfo * nrv)()
-    rc = _lib.hqmc_estimate(cfg.handle, _ptr(theta), seed, counter, nrv, tol, maxit, _solver(solver), _ptr(Gxi),
-                            _ptr(xi), g, infos, _stream())
+    fn = _lib.hqmc_estimate_projected if projected else _lib.hqmc_estimate
+    rc = fn(cfg.handle, _ptr(theta), seed, counter, nrv, tol, maxit, _solver(solver), _ptr(Gxi), _ptr(xi), g, infos,
+            _stream())
     if raise_on_fail:
         cfg.check(rc, allow=(OK, ENOTCONV))
     return complex(g[0], g[1]), [i.as_dict() for i in infos], Gxi, xi

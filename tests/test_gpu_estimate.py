@@ -64,3 +64,38 @@ def test_estimate_edge_cases(hq):
         assert e.value.status == hq.EINVAL
         g, infos, _, _ = hq.estimate(cfg, th, 2, tol=1e-14, maxit=2, raise_on_fail=False)
         assert all(i["status"] == hq.ENOTCONV for i in infos)
+
+
+@pytest.mark.parametrize("L,N,solver,tol", [(4, 6, "cg64", 1e-12), (8, 40, "pmixed", 1e-9)])
+def test_projected_estimate_matches_oracle(hq, L, N, solver, tol):
+    """The projected initial guesses change how each X_k is reached, not X_k: the
+    solutions and the estimate equal the oracle's within kappa * tol."""
+    lat = oracle.Lattice(L, N)
+    th = inputs.theta_hot(L, N, 22)
+    g_o, X_o, _ = oest.estimate(lat, th, seed=6, counter=200, nrv=4, tol=1e-13)
+    with hq.Config(L, N) as cfg:
+        g, infos, Gxi, xi = hq.estimate(cfg, cuda(th), 4, seed=6, counter=200, tol=tol, solver=solver,
+                                        want_vectors=True, projected=True)
+    assert all(i["status"] == 0 and i["true_residual"] <= tol for i in infos)
+    scale = np.max(np.abs(X_o))
+    assert np.max(np.abs(Gxi.cpu().numpy() - X_o)) < max(1e-7, 1e4 * tol) * scale
+    assert abs(g - g_o) < max(1e-9, 1e4 * tol)
+
+
+def test_projected_and_sequential_estimates_agree(hq):
+    """24 vectors on one L = 24 field, solved with the Galerkin guesses from the earlier
+    solutions and from the previous solution: both estimates agree to the solves'
+    accuracy, and the projection never costs iterations.  (Measured: 114 against
+    115 per vector; with the tau-line preconditioner the low end of the spectrum is
+    a dense band of about V modes, which 24 earlier solutions do not capture.)"""
+    L, N, nrv = 24, 240, 24
+    th = cuda(inputs.theta_ordered(L, N, 32, tau_walk=0.0))
+    with hq.Config(L, N) as cfg:
+        g0, inf0, _, _ = hq.estimate(cfg, th, nrv, seed=9, tol=1e-8, solver="pmixed")
+        g1, inf1, _, _ = hq.estimate(cfg, th, nrv, seed=9, tol=1e-8, solver="pmixed", projected=True)
+    assert all(i["status"] == 0 and i["true_residual"] <= 1e-8 for i in inf0 + inf1)
+    it0 = [i["iterations"] for i in inf0]
+    it1 = [i["iterations"] for i in inf1]
+    print("iterations, previous-solution guess:", it0, "projected:", it1)
+    assert sum(it1) <= sum(it0)
+    assert abs(g1 - g0) < 1e-5
