@@ -56,7 +56,8 @@ typedef enum {
     HQMC_ECUDA = 6,        /* a CUDA runtime call failed (text in hqmc_last_error) */
     HQMC_ENOMEM = 7,       /* workspace allocation failed (hqmc_make_config, hqmc_make_batch,
                               hqmc_net_create, hqmc_set_preconditioner) */
-    HQMC_EUNSUPPORTED = 8  /* option not available for these sizes or this device */
+    HQMC_EUNSUPPORTED = 8, /* option not available for these sizes or this device */
+    HQMC_EIO = 9           /* checkpoint file missing, unwritable, truncated or corrupted */
 } hqmc_status;
 
 enum { HQMC_FP64 = 0, HQMC_FP32 = 1 };
@@ -433,6 +434,41 @@ HQMC_API int hqmc_set_net_interval(hqmc_config* cfg, int k);
  * config keeps until hqmc_free_config; make this call before any stream capture.
  * The net must belong to the config's device.  Errors: HQMC_EINVAL, HQMC_ENOMEM. */
 HQMC_API int hqmc_set_preconditioner(hqmc_config* cfg, hqmc_net* net);
+
+/* ---- checkpoint / resume (not in the paper; its production runs imply it) -- */
+
+/* Everything that fixes a chain's future besides theta: the model, the Philox
+ * key and the counter of the next trajectory (every random number of trajectory
+ * k is a function of (seed, k), so a resumed chain continues bit for bit), the
+ * leapfrog parameters and the acceptance statistics. */
+typedef struct hqmc_checkpoint {
+    int L, Ntau;
+    double dtau, t, J, K;
+    int action;
+    int n_weights;            /* learned net's FP32 master weights stored after theta (0: none) */
+    uint64_t seed;            /* Philox key of the chain */
+    uint64_t traj_counter;    /* counter of the next trajectory */
+    double dt;                /* leapfrog step */
+    int nsteps;               /* leapfrog steps per trajectory */
+    int solver;               /* HQMC_SOLVER_* of the chain */
+    long long trajectories;   /* trajectories run so far */
+    long long accepted;       /* of which accepted */
+    int version;              /* file format version (1) */
+    int reserved;
+} hqmc_checkpoint;
+
+/* Writes the checkpoint: magic, *c, theta (HOST, double[Ntau][L][L][2]), the
+ * weights (HOST, c->n_weights floats, nullable when 0) and a 64-bit FNV-1a hash
+ * of the rest.  Host-only; HQMC_EINVAL for a bad header, HQMC_EIO on a file
+ * error. */
+HQMC_API int hqmc_checkpoint_write(const char* path, const hqmc_checkpoint* c, const double* theta_host,
+                                   const float* weights_host);
+
+/* Reads a checkpoint into *c.  With theta_host NULL only the header is read (to
+ * size the buffers); otherwise theta (HOST, 2 Ntau L L doubles) and, if
+ * weights_host is given, the weights are read and the hash is checked.
+ * HQMC_EIO for a missing, truncated or corrupted file (nothing written to *c). */
+HQMC_API int hqmc_checkpoint_read(const char* path, hqmc_checkpoint* c, double* theta_host, float* weights_host);
 
 /* ---- instrumentation ---------------------------------------------------- */
 

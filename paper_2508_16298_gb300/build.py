@@ -22,7 +22,8 @@ LIB = os.path.join(HERE, "libhqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["mdagm.cu", "mdagm_block.cu", "mdagm_walk.cu", "vec.cu", "force.cu", "hqmc_api.cu", "hqmc_static.cu", "net.cu", "precond.cu"]
+SOURCES = ["mdagm.cu", "mdagm_block.cu", "mdagm_walk.cu", "vec.cu", "force.cu", "hqmc_api.cu", "hqmc_static.cu", "net.cu",
+           "precond.cu", "checkpoint.cu"]
 
 
 def nvcc() -> str:
@@ -66,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]  # NVTX loads a profiler's injection library
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

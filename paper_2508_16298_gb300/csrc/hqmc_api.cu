@@ -11,6 +11,7 @@
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hqmc.h"
 #include "kernels.h"
@@ -18,6 +19,15 @@
 using namespace hqmc;
 
 namespace {
+
+// NVTX range over a scope (CG solve, force, leapfrog, trajectory, estimate), so
+// that a profiler's timeline shows the path's phases; free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxL = 68;             // 3 complex-double slices must fit in 227 KB of shared memory
 constexpr int kBodyIters64 = 16;      // FP64 CG iterations per loop body
@@ -658,6 +668,7 @@ int run_loop(hqmc_config* cfg, int solver, const double2* phi, double2* x, int* 
 // FP64 true residual stays the judge and the fallback).
 int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
           hqmc_solve_info* info, cudaStream_t s) {
+  NvtxRange nv("hqmc cg solve");
   int net_used = 0;
   const bool pc = solver_pc(solver);
   bool started = false;  // the FP64 residual that starts the recurrence is already in place
@@ -771,6 +782,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
 
 
 int force(hqmc_config* cfg, const double* theta, const double2* X, double* F, double* dSf, cudaStream_t s) {
+  NvtxRange nv("hqmc force");
   int slot;
   RET(timer_begin(cfg, HQMC_TIMER_FORCE, s, &slot));
   LK(1, launch_force(cfg->sl1, cfg->cB, cfg->t1, cfg->t2, cfg->U64, X, dSf, s));
@@ -783,6 +795,7 @@ int merge_status(int a, int b) { return a != HQMC_OK ? a : b; }
 
 int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, double2* X, int nsteps, double dt,
              double tol, int maxit, int solver, hqmc_traj_info* ti, cudaStream_t s) {
+  NvtxRange nv("hqmc leapfrog");
   const bool mixed = solver_fp32(solver);
   const bool learned = solver_base(solver) == HQMC_SOLVER_LEARNED;
   const long long nb = 2 * cfg->n;
@@ -1095,6 +1108,7 @@ const char* hqmc_strerror(int status) {
     case HQMC_ECUDA: return "CUDA runtime error";
     case HQMC_ENOMEM: return "device allocation failed";
     case HQMC_EUNSUPPORTED: return "unsupported configuration or device";
+    case HQMC_EIO: return "checkpoint file error";
     default: return "unknown status";
   }
 }
@@ -1538,6 +1552,7 @@ bool hermitian_solve(int k, std::vector<double>& A, std::vector<double>& b) {
 int estimate_impl(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
                   int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos, bool project,
                   cudaStream_t s) {
+  NvtxRange nv("hqmc estimate");
   RET(links(cfg, theta, true, solver_fp32(solver), s, false, solver_base(solver) == HQMC_SOLVER_LEARNED));
   const size_t vb = (size_t)cfg->n * sizeof(double2);
   double sum_re = 0.0, sum_im = 0.0;
@@ -1712,6 +1727,7 @@ int hqmc_trajectory(hqmc_config* cfg, double* theta, uint64_t seed, uint64_t tra
   if (nsteps < 0 || !std::isfinite(dt) || !(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "bad step parameters");
   RET(check_solver(cfg, solver));
   RET(check_device(cfg));
+  NvtxRange nv("hqmc trajectory");
   cudaStream_t s = (cudaStream_t)stream;
   const long long n = cfg->n;
   hqmc_traj_info ti{};
@@ -2477,6 +2493,7 @@ int hqmc_batch_trajectory(hqmc_batch* b, double* const* theta, const uint64_t* s
   BCK(cudaMemcpyAsync(b->d_counter, &b->h_mirror->counter, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   BCK(cudaMemsetAsync(b->d_bodies, 0, sizeof(unsigned long long), s));
   if ((rc = traj_graph(b, nsteps, tol, maxit)) != HQMC_OK) return rc;
+  NvtxRange nv("hqmc batched trajectory");
   BCK(cudaGraphLaunch(b->traj_exec, s));
   BCK(cudaMemcpyAsync(b->h_info, b->d_info, nc * sizeof(hqmc_traj_info), cudaMemcpyDeviceToHost, s));
   BCK(cudaMemcpyAsync(&b->h_mirror->bodies, b->d_bodies, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));

@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
                       "(needs the CUDA toolkit); there is no CPU fallback")
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
+OK, EINVAL, ENOTCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED, EIO = range(10)
 FP64, FP32 = 0, 1
 ACTION_COMPACT, ACTION_NONCOMPACT = 0, 1
 SOLVER_CG64, SOLVER_MIXED, SOLVER_LEARNED, SOLVER_PCG64, SOLVER_PMIXED, SOLVER_PLEARNED, SOLVER_FLEARNED = range(7)
@@ -45,7 +45,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_batch_set_solver",
            "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
            "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner",
-           "hqmc_set_net_interval")
+           "hqmc_set_net_interval", "hqmc_checkpoint_write", "hqmc_checkpoint_read")
 
 
 class Params(ctypes.Structure):
@@ -69,6 +69,17 @@ class TrajInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("accepted", ctypes.c_int), ("cg_solves", ctypes.c_int),
                 ("cg_iterations", ctypes.c_int), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
                 ("dH", ctypes.c_double), ("u", ctypes.c_double), ("max_true_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Checkpoint(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("Ntau", ctypes.c_int), ("dtau", ctypes.c_double), ("t", ctypes.c_double),
+                ("J", ctypes.c_double), ("K", ctypes.c_double), ("action", ctypes.c_int), ("n_weights", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("traj_counter", ctypes.c_uint64), ("dt", ctypes.c_double),
+                ("nsteps", ctypes.c_int), ("solver", ctypes.c_int), ("trajectories", ctypes.c_longlong),
+                ("accepted", ctypes.c_longlong), ("version", ctypes.c_int), ("reserved", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +136,8 @@ _sig = {
     "hqmc_net_train_step": ([_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_set_preconditioner": ([_vp, _vp], _i),
     "hqmc_set_net_interval": ([_vp, _i], _i),
+    "hqmc_checkpoint_write": ([ctypes.c_char_p, ctypes.POINTER(Checkpoint), _vp, _vp], _i),
+    "hqmc_checkpoint_read": ([ctypes.c_char_p, ctypes.POINTER(Checkpoint), _vp, _vp], _i),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -567,3 +580,45 @@ def set_net_interval(cfg: Config, k: int):
     """Flexible CG ("flearned"): the net preconditions every k-th iteration, the
     tau-line preconditioner the others."""
     cfg.check(_lib.hqmc_set_net_interval(cfg.handle, int(k)))
+
+
+def save_checkpoint(path: str, theta, seed: int, traj_counter: int, dt: float, nsteps: int, solver="cg64",
+                    trajectories: int = 0, accepted: int = 0, dtau: float = 0.1, t: float = 1.0, J: float = 1.0,
+                    K: float = 0.0, noncompact: bool = False, net=None):
+    """Write a chain checkpoint (hqmc_checkpoint_write): theta (CPU or CUDA float64
+    tensor of shape (Ntau, L, L, 2)) is copied to host memory first."""
+    import numpy as np
+    th = np.ascontiguousarray(theta.detach().cpu().numpy(), dtype=np.float64)
+    Ntau, L = th.shape[0], th.shape[1]
+    w = net.get_weights() if net is not None else None
+    c = Checkpoint(L, Ntau, dtau, t, J, K, ACTION_NONCOMPACT if noncompact else ACTION_COMPACT,
+                   0 if w is None else w.size, seed, traj_counter, dt, nsteps, _solver(solver), trajectories,
+                   accepted, 1, 0)
+    rc = _lib.hqmc_checkpoint_write(path.encode(), ctypes.byref(c), th.ctypes.data,
+                                    None if w is None else w.ctypes.data)
+    if rc != OK:
+        raise HQMCError(rc, path)
+
+
+def load_checkpoint(path: str):
+    """Read a chain checkpoint (hqmc_checkpoint_read).  Returns (header dict, theta as a
+    CPU float64 tensor, net weights as a float32 numpy array or None)."""
+    import numpy as np
+    c = Checkpoint()
+    rc = _lib.hqmc_checkpoint_read(path.encode(), ctypes.byref(c), None, None)
+    if rc != OK:
+        raise HQMCError(rc, path)
+    th = np.empty((c.Ntau, c.L, c.L, 2), dtype=np.float64)
+    w = np.empty(c.n_weights, dtype=np.float32) if c.n_weights else None
+    rc = _lib.hqmc_checkpoint_read(path.encode(), ctypes.byref(c), th.ctypes.data, None if w is None else w.ctypes.data)
+    if rc != OK:
+        raise HQMCError(rc, path)
+    return c.as_dict(), torch.from_numpy(th), w
+
+
+def log_trajectory(fp, info: dict, **extra):
+    """Append one JSON line for a trajectory (its info dict plus any extra fields,
+    e.g. the step time) to an open text file."""
+    import json
+    fp.write(json.dumps(dict(info, **extra)) + "\n")
+    fp.flush()

@@ -56,7 +56,8 @@ def test_params_struct_layout_matches_header(lib_path, tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no host C compiler")
-    structs = {"hqmc_params": hqmc.Params, "hqmc_solve_info": hqmc.SolveInfo, "hqmc_traj_info": hqmc.TrajInfo}
+    structs = {"hqmc_params": hqmc.Params, "hqmc_solve_info": hqmc.SolveInfo, "hqmc_traj_info": hqmc.TrajInfo,
+               "hqmc_checkpoint": hqmc.Checkpoint}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hqmc.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')

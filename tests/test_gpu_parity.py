@@ -378,3 +378,24 @@ def test_timing_counters(hq):
         n, ms = hq.get_timing(cfg, hq.TIMER_MDAGM)
         hq.set_timing(cfg, False)
     assert n == 3 and ms > 0
+
+
+def test_resume_from_checkpoint_is_bit_exact(hq, tmp_path):
+    """Every random number of trajectory k is a function of (seed, k): a chain saved
+    after two trajectories and resumed continues bit for bit."""
+    L, N = 8, 16
+    th = cuda(inputs.theta_hot(L, N, 61))
+    kw = dict(nsteps=3, dt=0.02, tol=1e-10)
+    path = str(tmp_path / "chain.ckp")
+    with hq.Config(L, N) as cfg:
+        acc = 0
+        for k in range(2):
+            acc += hq.trajectory(cfg, th, seed=9, traj_counter=k, **kw)["accepted"]
+        hq.save_checkpoint(path, th, seed=9, traj_counter=2, dt=0.02, nsteps=3, trajectories=2, accepted=acc)
+        a = hq.trajectory(cfg, th, seed=9, traj_counter=2, **kw)
+        hdr, th_b, _ = hq.load_checkpoint(path)
+        th_b = th_b.cuda()
+        b = hq.trajectory(cfg, th_b, seed=hdr["seed"], traj_counter=hdr["traj_counter"], nsteps=hdr["nsteps"],
+                          dt=hdr["dt"], tol=1e-10)
+    assert a["dH"] == b["dH"] and a["accepted"] == b["accepted"]
+    assert torch.equal(th, th_b)
