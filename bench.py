@@ -78,7 +78,7 @@ WORKLOADS["hmc_learned_fp32_L66_Nt660"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, 
                                                therm=400, therm_s=200.0,
                                                compare="cg64", compare_steps=5, factors=("pcg64", "mixed", "pmixed", "flearned"),
                                                factor_steps=3, triple_trajs=8, rhs_per_traj=4, epochs=8,
-                                               lr=1e-3)
+                                               lr=1e-3, guess=4)
 # stochastic estimation (Methods): 40 CN(0,1) vectors on one field, M^{-1} xi by preconditioned mixed CG
 WORKLOADS["estimate_L66_Nt660_40rv"] = dict(L=66, Ntau=660, dtau=0.1, t=1.0, J=1.0, nsteps=0, dt=0.0, tol=1e-8,
                                             solver="pmixed", seed=1, start="cold", estimate=True, nrv=40)
@@ -292,6 +292,9 @@ def config_of(wl_name, wl):
                    f"{wl['dt']}, then frozen (value in the line's dt)") if wl.get("therm") else wl["dt"],
             "cg_tol": wl["tol"],
             "solver": SOLVER_TEXT[wl["solver"]],
+            "initial_guess": (f"chronological: each leapfrog solve after the first starts from the Galerkin solution "
+                              f"in the span of the last {wl['guess']} solutions of the integration (O in FP32)")
+                             if wl.get("guess") else "the previous solution of the integration",
             "l2": "flushed between timed steps (512 MiB write; step times exclude the flush)"}
 
 
@@ -318,6 +321,7 @@ def thermalize(hqmc, cfg, theta, wl, seed):
     that their levelling off can be read."""
     dt = wl["dt"]
     rows, window = [], []
+    hqmc.set_guess_history(cfg, wl.get("guess", 0))
     t0 = time.perf_counter()
     k = 0
     while k < wl["therm"] and time.perf_counter() - t0 < wl["therm_s"]:
@@ -391,11 +395,14 @@ def train_net(hqmc, inputs, cfg, wl, theta, dt, seed, dev):
                  "loss_per_epoch": curve, "loss": "||K(theta) phi - x||^2 / ||x||^2"}
 
 
-def same_draws_arm(hqmc, cfg, theta_start, seed, first_counter, n, solver, wl, dt, flush, stream):
+def same_draws_arm(hqmc, cfg, theta_start, seed, first_counter, n, solver, wl, dt, flush, stream, guess=0):
     """The chain advanced from theta_start with `solver` on the draws of the first n timed
     steps (counters first_counter ...), dt, N_lf and tolerance unchanged; one untimed
-    single-solve trajectory first builds the solver's CUDA graph.  Returns per-step data."""
+    single-solve trajectory first builds the solver's CUDA graph.  guess: the
+    chronological guess history of the arm (0: the previous solution).  Returns
+    per-step data; the config's guess setting is restored to the workload's."""
     import torch
+    hqmc.set_guess_history(cfg, guess)
     th = theta_start.clone()
     kw = dict(nsteps=wl["nsteps"], dt=dt, tol=wl["tol"], solver=solver)
     hqmc.trajectory(cfg, th.clone(), seed=seed, traj_counter=first_counter, **dict(kw, nsteps=0))
@@ -407,8 +414,9 @@ def same_draws_arm(hqmc, cfg, theta_start, seed, first_counter, n, solver, wl, d
         infos.append(hqmc.trajectory(cfg, th, seed=seed, traj_counter=first_counter + k, **kw))
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    hqmc.set_guess_history(cfg, wl.get("guess", 0))
     ms = [a.elapsed_time(b) for a, b in ev]
-    return {"solver": solver, "traj_per_s": n / (sum(ms) / 1e3), "steps": n,
+    return {"solver": solver, "guess_history": guess, "traj_per_s": n / (sum(ms) / 1e3), "steps": n,
             "acceptance": statistics.mean(i["accepted"] for i in infos),
             "accepted": [i["accepted"] for i in infos],
             "cg_iterations_per_traj": statistics.mean(i["cg_iterations"] for i in infos),
@@ -534,8 +542,12 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
         compare["same_accept_decisions"] = all(a == b["accepted"] for a, b in zip(compare["accepted"], infos[:n64]))
     if wl.get("factors"):
         nf = min(wl.get("factor_steps", 3), args.steps)
-        arms = {sv: same_draws_arm(hqmc, cfg, theta_start, seed, args.warmup, nf, sv, wl, dt, flush, stream)
+        g = wl.get("guess", 0)
+        arms = {sv: same_draws_arm(hqmc, cfg, theta_start, seed, args.warmup, nf, sv, wl, dt, flush, stream, g)
                 for sv in wl["factors"]}
+        if g:  # the same solver without the chronological guess
+            arms["pmixed_previous_guess"] = same_draws_arm(hqmc, cfg, theta_start, seed, args.warmup, nf, "pmixed",
+                                                           wl, dt, flush, stream, 0)
         t = {sv: sum(a["step_ms"]) for sv, a in arms.items()}
         t[wl["solver"]] = sum(step_ms[:nf])
         factors = {"steps": nf, "ms_same_draws": {k: round(v, 1) for k, v in t.items()},
@@ -544,9 +556,13 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
                    "precond_gain": t["mixed"] / t["pmixed"] if "mixed" in t and "pmixed" in t else None,
                    "net_gain": t["pmixed"] / t[wl["solver"]] if "pmixed" in t else None,
                    "fcg_net_gain": t["pmixed"] / t["flearned"] if "flearned" in t and "pmixed" in t else None,
+                   "guess_gain": t["pmixed_previous_guess"] / t["pmixed"] if "pmixed_previous_guess" in t else None,
+                   "guess_history": g,
                    "definition": "fp32_over_fp64 = t(pcg64)/t(pmixed); precond_gain = t(mixed)/t(pmixed); "
                                  "net_gain = t(pmixed)/t(" + wl["solver"] + "); fcg_net_gain = t(pmixed)/t(flearned) "
-                                 "(flexible CG, net every iteration); same draws and start state"}
+                                 "(flexible CG, net every iteration); guess_gain = t(pmixed, previous-solution "
+                                 "guess)/t(pmixed, chronological guess); every arm but the last with the "
+                                 "chronological guess of guess_history solutions; same draws and start state"}
 
     # ---- the fused M^dagger M apply alone, L2 flushed: FP32 against HBM, FP64 against the FP64 rate
     x32 = torch.from_numpy(inputs.complex_gaussian(L, N, 77).astype(np.complex64)).to(dev)

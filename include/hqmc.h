@@ -145,8 +145,9 @@ typedef struct hqmc_traj_info {
 
 /* Validates *p, chooses launch shapes for the current device and allocates
  * the workspace.  On a config, device memory is allocated only here and, for
- * the learned net's activation fields, in hqmc_set_preconditioner; no apply,
- * solve, force, leapfrog, trajectory or net call allocates.
+ * the learned net's activation fields, in hqmc_set_preconditioner and, for the
+ * chronological guess, in hqmc_set_guess_history; no apply, solve, force,
+ * leapfrog, trajectory or net call allocates.
  * *out receives the config; free it with hqmc_free_config.
  * Errors: HQMC_EINVAL (parameters), HQMC_EUNSUPPORTED (device is not
  * compute capability 10.x, the sm_103a build's family), HQMC_ENOMEM, HQMC_ECUDA. */
@@ -427,6 +428,22 @@ HQMC_API int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* 
  * c % k == 0 of each reliable-update segment, the tau-line preconditioner the
  * others (k >= 1; 1 = every iteration).  Host-only; HQMC_EINVAL for k < 1. */
 HQMC_API int hqmc_set_net_interval(hqmc_config* cfg, int k);
+
+/* Chronological initial guess of the solves inside hqmc_leapfrog and
+ * hqmc_trajectory (Brower, Ivanenko, Levi and Orginos, "Chronological inversion
+ * method for the Dirac matrix in hybrid Monte Carlo", Nucl. Phys. B 484 (1997);
+ * not a method of the paper, which starts every pCG from X_0 = 0).  With k >= 2
+ * the last k solutions of the current integration are kept; every solve after
+ * the first starts from the Galerkin solution in their span with the current
+ * operator: Q an orthonormal basis of them, G = Q^dagger (M^dagger M) Q (O applied
+ * in FP32, k applies), x0 = Q G^{-1} Q^dagger phi.  k = 0 (the default) keeps the
+ * previous solution as the guess; k = 1 is the same.  The first call with a
+ * given k allocates 2 k vectors (complex double) on the config, kept until
+ * hqmc_free_config; make it before any stream capture.  The solves' own
+ * tolerance and FP64 true residual are unchanged, so only the iteration counts
+ * change.  0 <= k <= 8.  Errors: HQMC_EINVAL, HQMC_ENOMEM, HQMC_EUNSUPPORTED
+ * (a lattice whose scratch vector cannot hold the k-vector dot partials). */
+HQMC_API int hqmc_set_guess_history(hqmc_config* cfg, int k);
 
 /* Attaches (or with NULL detaches) the net used by HQMC_SOLVER_LEARNED.  The
  * first attach on a config allocates the net workspace (activation and gradient

@@ -117,6 +117,12 @@ struct hqmc_config {
   float2* r_old32 = nullptr;                                           // flexible CG: residual before the update
   double *part_fz = nullptr, *part_fx = nullptr;                       // flexible CG: <r, z>, <r_old, z> partials
   int net_interval = 1;                                                // flexible CG: net on iterations c % k == 0
+  // chronological initial guess of leapfrog solves (hqmc_set_guess_history): the
+  // last guess_k solutions of the current integration and an orthonormal basis
+  double2* hist = nullptr;                                             // guess_k vectors, contiguous
+  double2* qbasis = nullptr;                                           // guess_k vectors, contiguous
+  int guess_k = 0, guess_cap = 0;                                      // in use, allocated
+  int hist_n = 0, hist_next = 0;                                       // stored solutions, next ring slot
   double* net_scal = nullptr;                                          // device scalars (norms)
 
   int timing = 0;
@@ -662,6 +668,51 @@ int run_loop(hqmc_config* cfg, int solver, const double2* phi, double2* x, int* 
   }
 }
 
+// Solves the Hermitian positive definite k x k system A c = b in place (b -> c) by
+// Cholesky; false if a pivot falls below 1e-12 of its diagonal entry (the earlier
+// solutions are then too close to linearly dependent for the projection).
+bool hermitian_solve(int k, std::vector<double>& A, std::vector<double>& b) {
+  // A: k x k complex, row-major, interleaved (re, im); b: k complex
+  auto re = [&](int i, int j) -> double& { return A[2 * (i * k + j)]; };
+  auto im = [&](int i, int j) -> double& { return A[2 * (i * k + j) + 1]; };
+  for (int j = 0; j < k; ++j) {
+    double d = re(j, j);
+    for (int p = 0; p < j; ++p) d -= re(j, p) * re(j, p) + im(j, p) * im(j, p);
+    if (!(d > 1e-12 * std::fabs(re(j, j)))) return false;
+    const double ljj = std::sqrt(d);
+    re(j, j) = ljj;
+    im(j, j) = 0.0;
+    for (int i = j + 1; i < k; ++i) {
+      double sr = re(i, j), si = im(i, j);
+      for (int p = 0; p < j; ++p) {  // - L_ip conj(L_jp)
+        sr -= re(i, p) * re(j, p) + im(i, p) * im(j, p);
+        si -= im(i, p) * re(j, p) - re(i, p) * im(j, p);
+      }
+      re(i, j) = sr / ljj;
+      im(i, j) = si / ljj;
+    }
+  }
+  for (int i = 0; i < k; ++i) {  // L y = b
+    double sr = b[2 * i], si = b[2 * i + 1];
+    for (int p = 0; p < i; ++p) {
+      sr -= re(i, p) * b[2 * p] - im(i, p) * b[2 * p + 1];
+      si -= re(i, p) * b[2 * p + 1] + im(i, p) * b[2 * p];
+    }
+    b[2 * i] = sr / re(i, i);
+    b[2 * i + 1] = si / re(i, i);
+  }
+  for (int i = k - 1; i >= 0; --i) {  // L^dagger c = y
+    double sr = b[2 * i], si = b[2 * i + 1];
+    for (int p = i + 1; p < k; ++p) {  // - conj(L_pi) c_p
+      sr -= re(p, i) * b[2 * p] + im(p, i) * b[2 * p + 1];
+      si -= re(p, i) * b[2 * p + 1] - im(p, i) * b[2 * p];
+    }
+    b[2 * i] = sr / re(i, i);
+    b[2 * i + 1] = si / re(i, i);
+  }
+  return true;
+}
+
 // CG on (M^dagger M) x = phi with the link tables already built for theta.
 // HQMC_SOLVER_LEARNED: x <- x + K(theta)(phi - O x) from the attached net, kept
 // only if it lowers the FP64 residual, then the mixed solver (plain CG with its
@@ -793,14 +844,110 @@ int force(hqmc_config* cfg, const double* theta, const double2* X, double* F, do
 
 int merge_status(int a, int b) { return a != HQMC_OK ? a : b; }
 
+// Chronological initial guess (Brower, Ivanenko, Levi, Orginos, "Chronological
+// inversion method for the Dirac matrix in hybrid Monte Carlo", 1997): the
+// solutions of the last hist_n solves of this integration, at fields a few
+// leapfrog steps back, span a space that holds most of the new solution.  The
+// guess is the Galerkin solution in that space with the current operator:
+// Q = orthonormal basis of the stored solutions (classical Gram-Schmidt, twice),
+// G = Q^dagger O Q with O applied in FP32, b = Q^dagger phi, x = Q G^{-1} b.
+// Uses the FP32 link tables of the current field and, as scratch, xh32, q32 and
+// vscratch (free before a solve).  Leaves x unchanged (the previous solution)
+// if the basis or G degenerates.
+int chrono_guess(hqmc_config* cfg, const double2* phi, double2* x, cudaStream_t s) {
+  const int m0 = cfg->hist_n;
+  if (m0 < 2) return HQMC_OK;
+  const long long n = cfg->n;
+  const size_t vb = (size_t)n * sizeof(double2);
+  const int grid = cfg->act_grid;
+  double* dsc = reinterpret_cast<double*>(cfg->vscratch);  // many-dot partials and results
+  double* dout = dsc + 2 * (size_t)grid * cfg->guess_cap;
+  std::vector<double> d(2 * (size_t)cfg->guess_cap);
+  auto dots = [&](int k, const double2* v) -> int {  // d = (<Q_i, v>)_{i<k}
+    LK(2, launch_cdot_many(n, cfg->qbasis, n, k, v, grid, dsc, dout, s));
+    CK(cudaMemcpyAsync(d.data(), dout, 2 * (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HQMC_OK;
+  };
+  int m = 0;
+  for (int j = 0; j < m0; ++j) {
+    double2* qj = cfg->qbasis + (size_t)m * n;
+    CK(cudaMemcpyAsync(qj, cfg->hist + (size_t)j * n, vb, cudaMemcpyDeviceToDevice, s));
+    RET(dots(m + 1, qj));
+    const double nrm0 = d[2 * m];
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass) RET(dots(m + 1, qj));
+      for (int i = 0; i < m; ++i)
+        LK(1, launch_caxpy(n, -d[2 * i], -d[2 * i + 1], cfg->qbasis + (size_t)i * n, qj, s));
+      RET(dots(m + 1, qj));
+    }
+    const double nrm = d[2 * m];
+    if (!(nrm > 1e-20 * nrm0) || !(nrm > 0.0)) continue;  // (nearly) in the span already: drop it
+    LK(1, launch_dscale(n, 1.0 / std::sqrt(nrm), qj, s));
+    ++m;
+  }
+  if (m == 0) return HQMC_OK;
+  // G = Q^dagger O Q, column by column: O q_j in FP32, widened to FP64 in vscratch
+  // (after the dot scratch has been read back, so the two uses do not overlap)
+  std::vector<double> G(2 * (size_t)m * m), b;
+  std::vector<double> col(2 * (size_t)m);
+  double2* w = cfg->vscratch;
+  for (int j = 0; j < m; ++j) {
+    LK(1, launch_net_convert(cfg->qbasis + (size_t)j * n, cfg->xh32, 1, 1.0, n, s));
+    MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
+    a.U = cfg->U32;
+    a.x = cfg->xh32;
+    a.y = cfg->q32;
+    LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
+    LK(1, launch_net_convert(cfg->q32, w, 0, 1.0, n, s));
+    // the dot partials would overwrite w: sum <Q_i, w> with the per-vector cdot instead
+    for (int i = 0; i < m; ++i) {
+      LK(2, launch_cdot(n, cfg->qbasis + (size_t)i * n, w, grid, cfg->part_act, cfg->terms + 6, s));
+      CK(cudaMemcpyAsync(&col[2 * i], cfg->terms + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < m; ++i) {
+      G[2 * (i * m + j)] = col[2 * i];
+      G[2 * (i * m + j) + 1] = col[2 * i + 1];
+    }
+  }
+  for (int i = 0; i < m; ++i)  // Hermitian part (FP32 rounding of O breaks the symmetry slightly)
+    for (int j = i; j < m; ++j) {
+      const double re = 0.5 * (G[2 * (i * m + j)] + G[2 * (j * m + i)]);
+      const double im = 0.5 * (G[2 * (i * m + j) + 1] - G[2 * (j * m + i) + 1]);
+      G[2 * (i * m + j)] = re;
+      G[2 * (i * m + j) + 1] = im;
+      G[2 * (j * m + i)] = re;
+      G[2 * (j * m + i) + 1] = -im;
+    }
+  RET(dots(m, phi));
+  b.assign(d.begin(), d.begin() + 2 * m);
+  if (!hermitian_solve(m, G, b)) return HQMC_OK;
+  CK(cudaMemsetAsync(x, 0, vb, s));
+  for (int i = 0; i < m; ++i) LK(1, launch_caxpy(n, b[2 * i], b[2 * i + 1], cfg->qbasis + (size_t)i * n, x, s));
+  return HQMC_OK;
+}
+
+// Stores a solution of the current integration in the guess history (ring).
+int chrono_push(hqmc_config* cfg, const double2* X, cudaStream_t s) {
+  if (cfg->guess_k <= 0) return HQMC_OK;
+  CK(cudaMemcpyAsync(cfg->hist + (size_t)cfg->hist_next * cfg->n, X, sizeof(double2) * cfg->n,
+                     cudaMemcpyDeviceToDevice, s));
+  cfg->hist_next = (cfg->hist_next + 1) % cfg->guess_k;
+  cfg->hist_n = std::min(cfg->hist_n + 1, cfg->guess_k);
+  return HQMC_OK;
+}
+
 int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, double2* X, int nsteps, double dt,
              double tol, int maxit, int solver, hqmc_traj_info* ti, cudaStream_t s) {
   NvtxRange nv("hqmc leapfrog");
-  const bool mixed = solver_fp32(solver);
+  const bool chrono = cfg->guess_k > 0;
+  const bool mixed = solver_fp32(solver) || chrono;  // the guess applies O in FP32
   const bool learned = solver_base(solver) == HQMC_SOLVER_LEARNED;
   const long long nb = 2 * cfg->n;
   hqmc_solve_info si;
   int status = HQMC_OK;
+  cfg->hist_n = cfg->hist_next = 0;  // a new integration: no earlier solutions
   RET(links(cfg, theta, true, mixed, s, false, learned));
   int rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
   if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
@@ -808,16 +955,19 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
   ti->cg_solves++;
   ti->cg_iterations += si.iterations;
   ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+  RET(chrono_push(cfg, X, s));
   RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
   for (int n = 0; n < nsteps; ++n) {
     LK(1, launch_kick_drift(nb, p, theta, cfg->F, dt / 2, dt, s));
     RET(links(cfg, theta, true, mixed, s, false, learned));
+    if (chrono) RET(chrono_guess(cfg, phi, X, s));  // else X is the previous solution
     rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
     if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
     status = merge_status(status, rc);
     ti->cg_solves++;
     ti->cg_iterations += si.iterations;
     ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+    RET(chrono_push(cfg, X, s));
     RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
     LK(1, launch_kick(nb, p, cfg->F, dt / 2, s));
   }
@@ -1497,51 +1647,6 @@ int hqmc_cg_solve(hqmc_config* cfg, const double* theta, const void* phi, void* 
 }  // extern "C"
 
 namespace {
-
-// Solves the Hermitian positive definite k x k system A c = b in place (b -> c) by
-// Cholesky; false if a pivot falls below 1e-12 of its diagonal entry (the earlier
-// solutions are then too close to linearly dependent for the projection).
-bool hermitian_solve(int k, std::vector<double>& A, std::vector<double>& b) {
-  // A: k x k complex, row-major, interleaved (re, im); b: k complex
-  auto re = [&](int i, int j) -> double& { return A[2 * (i * k + j)]; };
-  auto im = [&](int i, int j) -> double& { return A[2 * (i * k + j) + 1]; };
-  for (int j = 0; j < k; ++j) {
-    double d = re(j, j);
-    for (int p = 0; p < j; ++p) d -= re(j, p) * re(j, p) + im(j, p) * im(j, p);
-    if (!(d > 1e-12 * std::fabs(re(j, j)))) return false;
-    const double ljj = std::sqrt(d);
-    re(j, j) = ljj;
-    im(j, j) = 0.0;
-    for (int i = j + 1; i < k; ++i) {
-      double sr = re(i, j), si = im(i, j);
-      for (int p = 0; p < j; ++p) {  // - L_ip conj(L_jp)
-        sr -= re(i, p) * re(j, p) + im(i, p) * im(j, p);
-        si -= im(i, p) * re(j, p) - re(i, p) * im(j, p);
-      }
-      re(i, j) = sr / ljj;
-      im(i, j) = si / ljj;
-    }
-  }
-  for (int i = 0; i < k; ++i) {  // L y = b
-    double sr = b[2 * i], si = b[2 * i + 1];
-    for (int p = 0; p < i; ++p) {
-      sr -= re(i, p) * b[2 * p] - im(i, p) * b[2 * p + 1];
-      si -= re(i, p) * b[2 * p + 1] + im(i, p) * b[2 * p];
-    }
-    b[2 * i] = sr / re(i, i);
-    b[2 * i + 1] = si / re(i, i);
-  }
-  for (int i = k - 1; i >= 0; --i) {  // L^dagger c = y
-    double sr = b[2 * i], si = b[2 * i + 1];
-    for (int p = i + 1; p < k; ++p) {  // - conj(L_pi) c_p
-      sr -= re(p, i) * b[2 * p] + im(p, i) * b[2 * p + 1];
-      si -= re(p, i) * b[2 * p + 1] - im(p, i) * b[2 * p];
-    }
-    b[2 * i] = sr / re(i, i);
-    b[2 * i + 1] = si / re(i, i);
-  }
-  return true;
-}
 
 // Stochastic estimation (Methods, "Stochastic estimation of fermionic observables").
 // project: every solve after the first starts from the Galerkin projection of its
@@ -2664,6 +2769,25 @@ int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* theta, co
     for (double v : lp) sum += v;
     *loss_host = sum;
   }
+  return HQMC_OK;
+}
+
+int hqmc_set_guess_history(hqmc_config* cfg, int k) {
+  if (!cfg || k < 0 || k > 8) return HQMC_EINVAL;
+  if (k > cfg->guess_cap) {
+    RET(check_device(cfg));
+    // the guess's many-dot partials and results live in the config's scratch vector
+    if (2 * (size_t)cfg->act_grid * k + 2 * (size_t)k > 2 * (size_t)cfg->n)
+      return fail(cfg, HQMC_EUNSUPPORTED, "lattice too small for a guess history of %d", k);
+    double2 *h = nullptr, *q = nullptr;
+    RET(dalloc(cfg, &h, (size_t)k * cfg->n));
+    RET(dalloc(cfg, &q, (size_t)k * cfg->n));
+    cfg->hist = h;
+    cfg->qbasis = q;
+    cfg->guess_cap = k;
+  }
+  cfg->guess_k = k;
+  cfg->hist_n = cfg->hist_next = 0;
   return HQMC_OK;
 }
 

@@ -358,7 +358,9 @@ cudaError_t launch_cdot(long long n, const double2* a, const double2* b, int gri
 // out[2 i], out[2 i + 1] = <X_i, b> (re, im) for X_i = X + i * stride, i < k; part holds 2 * grid * k doubles.
 cudaError_t launch_cdot_many(long long n, const double2* X, long long stride, int k, const double2* b, int grid,
                              double* part, double* out, cudaStream_t s);
-// y += (cr + i ci) x
+// y *= a (real), in place
+cudaError_t launch_dscale(long long n, double a, double2* y, cudaStream_t s);
+// y += (cr + i ci) x (x and y distinct)
 cudaError_t launch_caxpy(long long n, double cr, double ci, const double2* x, double2* y, cudaStream_t s);
 // FP64 FMA throughput probe (16 flops per thread per iteration).
 cudaError_t launch_fp64_probe(int blocks, int threads, int iters, double* out, cudaStream_t s);

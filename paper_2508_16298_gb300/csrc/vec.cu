@@ -737,6 +737,20 @@ __global__ void caxpy_kernel(long long n, double cr, double ci, const double2* _
   }
 }
 
+// y *= a (real a), in place.
+__global__ void dscale_kernel(long long n, double a, double2* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 w = y[i];
+    y[i] = make_double2(a * w.x, a * w.y);
+  }
+}
+
+cudaError_t launch_dscale(long long n, double a, double2* y, cudaStream_t s) {
+  dscale_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, a, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_caxpy(long long n, double cr, double ci, const double2* x, double2* y, cudaStream_t s) {
   caxpy_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, cr, ci, x, y);
   return cudaGetLastError();

@@ -45,7 +45,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_batch_set_solver",
            "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
            "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner",
-           "hqmc_set_net_interval", "hqmc_checkpoint_write", "hqmc_checkpoint_read")
+           "hqmc_set_net_interval", "hqmc_set_guess_history", "hqmc_checkpoint_write", "hqmc_checkpoint_read")
 
 
 class Params(ctypes.Structure):
@@ -136,6 +136,7 @@ _sig = {
     "hqmc_net_train_step": ([_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_set_preconditioner": ([_vp, _vp], _i),
     "hqmc_set_net_interval": ([_vp, _i], _i),
+    "hqmc_set_guess_history": ([_vp, _i], _i),
     "hqmc_checkpoint_write": ([ctypes.c_char_p, ctypes.POINTER(Checkpoint), _vp, _vp], _i),
     "hqmc_checkpoint_read": ([ctypes.c_char_p, ctypes.POINTER(Checkpoint), _vp, _vp], _i),
 }
@@ -574,6 +575,12 @@ def set_preconditioner(cfg: Config, net):
     """Attach (or with None detach) the net of the learned solvers; the first attach
     allocates the config's net workspace."""
     cfg.check(_lib.hqmc_set_preconditioner(cfg.handle, None if net is None else net.handle))
+
+
+def set_guess_history(cfg: Config, k: int):
+    """Chronological initial guess of leapfrog solves from the last k solutions
+    (hqmc_set_guess_history; 0 = the previous solution)."""
+    cfg.check(_lib.hqmc_set_guess_history(cfg.handle, int(k)))
 
 
 def set_net_interval(cfg: Config, k: int):
