@@ -95,7 +95,7 @@ MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pm
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu capture of the τ-walking
 # FP32 kernel at L = 66 (cold caches; writes still in L2 at the kernel's end are not counted there).
 # Valid for the kernel as captured; set to None when the kernel changes.
-NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 77.954048e6 + 9.346304e6}
+NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 79.156736e6 + 9.892608e6}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -809,9 +809,9 @@ def run_profile_case(wl):
     loop driven from the host (kernels inside a graph with conditional nodes cannot
     be profiled one by one) and the default launch shapes (an autotuner timed under
     a profiler would not pick the bench's shapes): three fused M^dagger M applies in
-    the workload's precision, then one trajectory of 2 leapfrog steps with the
-    workload's solver and dt (the learned one with a freshly initialised net; its
-    cost does not depend on the weights).  Prints no JSON."""
+    the workload's precision, then one trajectory of 4 leapfrog steps with the
+    workload's solver, initial-guess history and first dt (the learned one with a
+    freshly initialised net; its cost does not depend on the weights).  Prints no JSON."""
     import numpy as np
     import torch
 
@@ -831,7 +831,8 @@ def run_profile_case(wl):
         if wl["solver"] in ("learned", "plearned"):
             net = hqmc.Net(seed=1)
             hqmc.set_preconditioner(cfg, net)
-        hqmc.trajectory(cfg, theta, seed=wl["seed"], traj_counter=0, nsteps=2, dt=wl["dt"], tol=wl["tol"],
+        hqmc.set_guess_history(cfg, wl.get("guess", 0))
+        hqmc.trajectory(cfg, theta, seed=wl["seed"], traj_counter=0, nsteps=4, dt=wl["dt"], tol=wl["tol"],
                         solver=wl["solver"])
         torch.cuda.synchronize()
         print("preconditioner shape (FP32):", hqmc.get_precond_shape(cfg, hqmc.FP32), file=sys.stderr)

@@ -875,8 +875,7 @@ int chrono_guess(hqmc_config* cfg, const double2* phi, double2* x, cudaStream_t 
     CK(cudaMemcpyAsync(qj, cfg->hist + (size_t)j * n, vb, cudaMemcpyDeviceToDevice, s));
     RET(dots(m + 1, qj));
     const double nrm0 = d[2 * m];
-    for (int pass = 0; pass < 2; ++pass) {
-      if (pass) RET(dots(m + 1, qj));
+    for (int pass = 0; pass < 2 && m > 0; ++pass) {  // d holds <Q_i, q_j> of the current q_j
       for (int i = 0; i < m; ++i)
         LK(1, launch_caxpy(n, -d[2 * i], -d[2 * i + 1], cfg->qbasis + (size_t)i * n, qj, s));
       RET(dots(m + 1, qj));
