@@ -851,8 +851,8 @@ int merge_status(int a, int b) { return a != HQMC_OK ? a : b; }
 // guess is the Galerkin solution in that space with the current operator:
 // Q = orthonormal basis of the stored solutions (classical Gram-Schmidt, twice),
 // G = Q^dagger O Q with O applied in FP32, b = Q^dagger phi, x = Q G^{-1} b.
-// Uses the FP32 link tables of the current field and, as scratch, xh32, q32 and
-// vscratch (free before a solve).  Leaves x unchanged (the previous solution)
+// Uses the FP32 link tables of the current field and, as scratch, xh32, q32, q64
+// and vscratch (free before a solve).  Leaves x unchanged (the previous solution)
 // if the basis or G degenerates.
 int chrono_guess(hqmc_config* cfg, const double2* phi, double2* x, cudaStream_t s) {
   const int m0 = cfg->hist_n;
@@ -886,11 +886,10 @@ int chrono_guess(hqmc_config* cfg, const double2* phi, double2* x, cudaStream_t 
     ++m;
   }
   if (m == 0) return HQMC_OK;
-  // G = Q^dagger O Q, column by column: O q_j in FP32, widened to FP64 in vscratch
-  // (after the dot scratch has been read back, so the two uses do not overlap)
+  // G = Q^dagger O Q, column by column: O q_j in FP32, widened to FP64 in q64 (the
+  // FP64 direction product, free outside a solve), then one many-dot per column
   std::vector<double> G(2 * (size_t)m * m), b;
-  std::vector<double> col(2 * (size_t)m);
-  double2* w = cfg->vscratch;
+  double2* w = cfg->q64;
   for (int j = 0; j < m; ++j) {
     LK(1, launch_net_convert(cfg->qbasis + (size_t)j * n, cfg->xh32, 1, 1.0, n, s));
     MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
@@ -899,15 +898,10 @@ int chrono_guess(hqmc_config* cfg, const double2* phi, double2* x, cudaStream_t 
     a.y = cfg->q32;
     LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
     LK(1, launch_net_convert(cfg->q32, w, 0, 1.0, n, s));
-    // the dot partials would overwrite w: sum <Q_i, w> with the per-vector cdot instead
+    RET(dots(m, w));
     for (int i = 0; i < m; ++i) {
-      LK(2, launch_cdot(n, cfg->qbasis + (size_t)i * n, w, grid, cfg->part_act, cfg->terms + 6, s));
-      CK(cudaMemcpyAsync(&col[2 * i], cfg->terms + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    CK(cudaStreamSynchronize(s));
-    for (int i = 0; i < m; ++i) {
-      G[2 * (i * m + j)] = col[2 * i];
-      G[2 * (i * m + j) + 1] = col[2 * i + 1];
+      G[2 * (i * m + j)] = d[2 * i];
+      G[2 * (i * m + j) + 1] = d[2 * i + 1];
     }
   }
   for (int i = 0; i < m; ++i)  // Hermitian part (FP32 rounding of O breaks the symmetry slightly)
