@@ -669,8 +669,9 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
     dts = [wl["dt"] * ((24 * 24 * 240) / (L * L * N)) ** 0.5 for L, N in lats]
     thetas = [torch.from_numpy(inputs.theta_ordered(L, N, s, tau_walk=0.0)).cuda() for (L, N), s in zip(lats, seeds)]
     stream = torch.cuda.current_stream()
-    with hqmc.Batch(lats) as b:
+    with hqmc.Batch(lats, autotune=True) as b:
         b.set_solver(wl["solver"])
+        shape = b.launch_shape()
         for k in range(args.warmup):
             b.trajectory(thetas, seeds, k, wl["nsteps"], dts, tol=wl["tol"])
         if world > 1:
@@ -709,7 +710,10 @@ def run_batched(args, wl_name, wl, rank, world, local_rank):
                        "n_leapfrog": wl["nsteps"], "dt": "0.0005 * sqrt(138240 / sites)", "cg_tol": wl["tol"],
                        "solver": wl["solver"] + " (batched: one fused launch + one update launch" +
                                  (" + one preconditioner launch" if wl["solver"] == "pcg64" else "") +
-                                 " per CG iteration for all chains)"},
+                                 " per CG iteration for all chains)",
+                       "batched_tiles": {"cluster": shape["cluster"], "order": ["chain by chain", "largest first",
+                                                                                "round robin"][shape["order"]],
+                                         "threads": shape["threads"], "autotuned_launch_us": shape["tuned_us"]}},
             "gpu_launches": int(launches),
             "sequential_traj_per_s": len(lats) / (seq_ms / 1e3),
             "batched_over_sequential": value / (len(lats) / (seq_ms / 1e3)),

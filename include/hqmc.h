@@ -353,8 +353,11 @@ HQMC_API int hqmc_trajectory(hqmc_config* cfg, double* theta, uint64_t seed, uin
 
 /* A batch of nchains independent chains, chain c described by params[c] (L and
  * Ntau may differ; the batched kernels are the generic fused ones and every
- * chain gets the same cluster size, the smallest the chains admit).  Each
- * chain owns a config's workspace.  Inside a CG solve every iteration is ONE
+ * chain gets the same cluster size, by default the smallest the chains admit).
+ * If any params[c].autotune is set, hqmc_make_batch times the batched fused
+ * launch at every cluster size 1, 2, 4, 8 the device co-schedules and every
+ * tile order (hqmc_batch_launch_shape) and keeps the fastest; results do not
+ * depend on that choice.  Each chain owns a config's workspace.  Inside a CG solve every iteration is ONE
  * launch of the fused M^dagger M over a tile table covering every chain's
  * slices plus ONE launch of the vector update over every chain's blocks, under
  * a device-side WHILE loop that runs while any chain is unconverged.  Every
@@ -373,6 +376,12 @@ HQMC_API const char* hqmc_batch_last_error(const hqmc_batch* b);
 HQMC_API int hqmc_batch_set_solver(hqmc_batch* b, int solver);
 /* Kernels the batch has enqueued (including its chains' configs). */
 HQMC_API long long hqmc_batch_launch_count(const hqmc_batch* b);
+/* Tile shape of the batch's fused M^dagger M launch: cluster size along tau
+ * (slices per tile), tile order (0 chain by chain, 1 chains with the most sites
+ * per slice first, 2 round robin over the chains), block size, and the
+ * autotuner's time of one launch in microseconds (0 without autotune).  Any
+ * output pointer may be NULL.  HQMC_EINVAL for a NULL batch. */
+HQMC_API int hqmc_batch_launch_shape(const hqmc_batch* b, int* cluster, int* order, int* threads, float* tuned_us);
 
 /* CG on every chain: theta[c], phi[c], x[c] are HOST arrays of device
  * pointers with chain c's layouts (as in hqmc_cg_solve); infos (host, nchains

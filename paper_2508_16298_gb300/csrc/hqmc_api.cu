@@ -1940,9 +1940,12 @@ int hqmc_get_timing(hqmc_config* cfg, int timer, long long* launches, double* to
 struct hqmc_batch {
   std::vector<hqmc_config*> cfgs;
   int C = 1;           // cluster size (slices per tile), shared by all chains
+  int tile_order = 0;  // order of the tile table (batch_tiles)
+  float tuned_us = 0.f;  // autotuner: time of one batched fused launch (0: not tuned)
   int threads = 64;    // block size of the batched fused kernel
   size_t smem = 0;     // its dynamic shared memory (largest chain)
   int ntiles = 0;
+  int tiles_cap = 0;   // capacity of d_tiles (one tile per slice)
   int total_ublocks = 0;
   MdagmArgs<double>* d_cgdir = nullptr;
   MdagmArgs<double>* d_resid_start = nullptr;
@@ -2048,6 +2051,125 @@ void batch_release(hqmc_batch* b) {
   if (b->h_stage) cudaFreeHost(b->h_stage);
   for (hqmc_config* c : b->cfgs) hqmc_free_config(c);
   b->cfgs.clear();
+}
+
+// Cluster tiles (chain, first slice) of the batched fused kernel for cluster
+// size C, in one of three orders: 0 chain by chain as given, 1 the chains with
+// the most sites per slice first, 2 round robin over the chains.  The order
+// changes only which CTAs the hardware dispatches first, never a result.
+std::vector<int2> batch_tiles(const std::vector<hqmc_config*>& cfgs, int C, int order) {
+  const int nc = (int)cfgs.size();
+  std::vector<int> ch(nc);
+  for (int c = 0; c < nc; ++c) ch[c] = c;
+  if (order == 1)
+    std::stable_sort(ch.begin(), ch.end(), [&](int a, int b) { return cfgs[a]->g.V > cfgs[b]->g.V; });
+  std::vector<int2> tiles;
+  if (order == 2) {
+    for (int t0 = 0;; t0 += C) {
+      bool any = false;
+      for (int c : ch)
+        if (t0 < cfgs[c]->p.Ntau) {
+          tiles.push_back(make_int2(c, t0));
+          any = true;
+        }
+      if (!any) break;
+    }
+  } else {
+    for (int c : ch)
+      for (int t0 = 0; t0 < cfgs[c]->p.Ntau; t0 += C) tiles.push_back(make_int2(c, t0));
+  }
+  return tiles;
+}
+
+// Cluster size and tile order of the batched fused kernel; every chain's
+// partial-sum slots follow the cluster size.
+int batch_set_tiles(hqmc_batch* b, int C, int order) {
+  b->C = C;
+  b->tile_order = order;
+  for (hqmc_config* cfg : b->cfgs) {
+    cfg->sl.cluster = C;
+    cfg->sl.grid = (cfg->p.Ntau + C - 1) / C * C;
+    cfg->fused64.cluster = C;
+    cfg->fused64.grid = cfg->sl.grid;
+  }
+  const std::vector<int2> tiles = batch_tiles(b->cfgs, C, order);
+  if ((int)tiles.size() > b->tiles_cap) return bfail(b, HQMC_EINVAL, "tile table overflow");
+  b->ntiles = (int)tiles.size();
+  BCK(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  return HQMC_OK;
+}
+
+// Autotuner of the batch: times the batched fused launch (an FP64 residual
+// r = phi - O x of every chain, zero operands, links of theta = 0) at every
+// cluster size 1, 2, 4, 8 the device can co-schedule and every tile order, and
+// keeps the fastest.  Results do not depend on the choice: the neighbour's z_{tau-1}
+// is the same arithmetic as the recomputed halo, and the reduction slots are
+// per slice.
+int batch_autotune(hqmc_batch* b) {
+  const int nc = (int)b->cfgs.size();
+  int minN = 1 << 30;
+  std::vector<MdagmArgs<double>> descs(nc);
+  for (int c = 0; c < nc; ++c) {
+    hqmc_config* cfg = b->cfgs[c];
+    minN = std::min(minN, cfg->p.Ntau);
+    BCK(cudaMemset(cfg->th0, 0, 2 * cfg->n * sizeof(double)));
+    BCK(cudaMemset(cfg->p64[0], 0, cfg->n * sizeof(double2)));
+    BCK(cudaMemset(cfg->p64[1], 0, cfg->n * sizeof(double2)));
+    BCK(launch_links(cfg->g, cfg->th0, cfg->t1, cfg->t2, cfg->U64, cfg->U32, cfg->th32, 0));
+    MdagmArgs<double> r = mdagm_args<double, MODE_RESID>(cfg);
+    r.U = cfg->U64;
+    r.x = cfg->p64[0];
+    r.b = cfg->p64[1];
+    r.r_out = cfg->r64;
+    r.r_out_fp32 = 0;
+    r.part_out = cfg->part_resid;
+    r.st = cfg->st;
+    r.teff = cfg->sl.threads;
+    r.gate = GATE_ALWAYS;
+    descs[c] = r;
+  }
+  BCK(cudaMemcpy(b->d_resid_start, descs.data(), nc * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  const int reps = 5;
+  float best = 1e30f;
+  int bestC = b->C, bestOrder = b->tile_order;
+  int rc = HQMC_OK;
+  for (int C : {1, 2, 4, 8}) {
+    if (C > minN || (C > 1 && mdagm_batch_max_active_clusters(C, b->threads, b->smem) <= 0)) continue;
+    for (int order = 0; order < 3 && rc == HQMC_OK; ++order) {
+      if ((rc = batch_set_tiles(b, C, order)) != HQMC_OK) break;
+      auto go = [&]() {
+        return launch_mdagm_batch<double, MODE_RESID>(b->d_resid_start, b->d_tiles, b->ntiles, b->C, b->threads,
+                                                      b->smem, 0);
+      };
+      cudaError_t err = go();
+      if (err == cudaSuccess) err = cudaEventRecord(e0, 0);
+      for (int k = 0; k < reps && err == cudaSuccess; ++k) err = go();
+      if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err != cudaSuccess) {  // a shape the device refuses is skipped
+        cudaGetLastError();
+        continue;
+      }
+      b->launches += reps + 1;
+      const float us = 1e3f * ms / reps;
+      if (us < best) {
+        best = us;
+        bestC = C;
+        bestOrder = order;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HQMC_OK) return rc;
+  if (best >= 1e30f) return bfail(b, HQMC_EUNSUPPORTED, "no batched launch shape ran");
+  b->tuned_us = best;
+  return batch_set_tiles(b, bestC, bestOrder);
 }
 
 // Per-chain descriptors of the batched CG kernels for operands (phi, x).
@@ -2353,8 +2475,10 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
   int rc = HQMC_OK;
   do {
     int maxV = 0, minC = 8, maxThreads = 64;
+    bool tune = false;
     for (int c = 0; c < nchains; ++c) {
       hqmc_params p = params[c];
+      tune = tune || p.autotune;
       p.variant = 1;  // the batched kernel is the generic one; chains stay bit-identical to it
       p.autotune = 0;
       hqmc_config* cfg = nullptr;
@@ -2371,20 +2495,14 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
     b->C = minC;
     b->threads = maxThreads;
     b->smem = (size_t)3 * maxV * sizeof(double2);
-    std::vector<int2> tiles, ublocks;
+    std::vector<int2> ublocks;
     std::vector<int> unblocks;
     for (int c = 0; c < nchains; ++c) {
       hqmc_config* cfg = b->cfgs[c];
-      // each chain keeps its own cluster size C (equal to the batch's) and update grid
-      cfg->sl.cluster = b->C;
-      cfg->sl.grid = (cfg->p.Ntau + b->C - 1) / b->C * b->C;
-      cfg->fused64.cluster = b->C;
-      cfg->fused64.grid = cfg->sl.grid;
-      for (int t0 = 0; t0 < cfg->p.Ntau; t0 += b->C) tiles.push_back(make_int2(c, t0));
+      b->tiles_cap += cfg->p.Ntau;  // cluster size 1: one tile per slice
       for (int j = 0; j < cfg->ew_grid; ++j) ublocks.push_back(make_int2(c, j));
       unblocks.push_back(cfg->ew_grid);
     }
-    b->ntiles = (int)tiles.size();
     b->total_ublocks = (int)ublocks.size();
     // tiles of the batched preconditioner: every chain's own (bx, by) grid
     std::vector<int4> ltiles;
@@ -2414,7 +2532,7 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
         !dal((void**)&b->d_resid_start, nchains * sizeof(MdagmArgs<double>)) ||
         !dal((void**)&b->d_resid_loop, nchains * sizeof(MdagmArgs<double>)) ||
         !dal((void**)&b->d_upd, nchains * sizeof(UpdArgs<double>)) ||
-        !dal((void**)&b->d_fin, nchains * sizeof(FinArgs)) || !dal((void**)&b->d_tiles, tiles.size() * sizeof(int2)) ||
+        !dal((void**)&b->d_fin, nchains * sizeof(FinArgs)) || !dal((void**)&b->d_tiles, b->tiles_cap * sizeof(int2)) ||
         !dal((void**)&b->d_ublocks, ublocks.size() * sizeof(int2)) ||
         !dal((void**)&b->d_unblocks, unblocks.size() * sizeof(int)) ||
         !dal((void**)&b->d_states, states.size() * sizeof(CgState*)) ||
@@ -2477,14 +2595,16 @@ int hqmc_make_batch(const hqmc_params* params, int nchains, hqmc_batch** out) {
       rc = bfail(b, HQMC_ECUDA, "batch trajectory table upload");
       break;
     }
-    if (cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_ublocks, ublocks.data(), ublocks.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(b->d_ublocks, ublocks.data(), ublocks.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_unblocks, unblocks.data(), unblocks.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_states, states.data(), states.size() * sizeof(CgState*), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_ltiles, ltiles.data(), ltiles.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
       rc = bfail(b, HQMC_ECUDA, "batch table upload");
       break;
     }
+    // each chain keeps the batch's cluster size C in its own partial-sum slots
+    if ((rc = batch_set_tiles(b, b->C, 0)) != HQMC_OK) break;
+    if (tune && (rc = batch_autotune(b)) != HQMC_OK) break;
   } while (0);
   if (rc != HQMC_OK) {
     const int keep = rc;
@@ -2518,6 +2638,15 @@ int hqmc_batch_set_solver(hqmc_batch* b, int solver) {
     b->traj_exec = nullptr;
   }
   b->solver = solver;
+  return HQMC_OK;
+}
+
+int hqmc_batch_launch_shape(const hqmc_batch* b, int* cluster, int* order, int* threads, float* tuned_us) {
+  if (!b) return HQMC_EINVAL;
+  if (cluster) *cluster = b->C;
+  if (order) *order = b->tile_order;
+  if (threads) *threads = b->threads;
+  if (tuned_us) *tuned_us = b->tuned_us;
   return HQMC_OK;
 }
 

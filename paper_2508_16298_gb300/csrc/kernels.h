@@ -242,6 +242,8 @@ cudaError_t launch_line_update(const Geo& g, const LineCoef& lc, const LineLaunc
 template <class R, int MODE>
 cudaError_t launch_mdagm_batch(const MdagmArgs<R>* descs, const int2* tiles, int ntiles, int C, int threads,
                                size_t smem, cudaStream_t s);
+// Clusters of C CTAs (threads, smem each) of the batched FP64 kernel the device keeps resident.
+int mdagm_batch_max_active_clusters(int C, int threads, size_t smem);
 
 // y = M x or M^dagger x.
 template <class R>

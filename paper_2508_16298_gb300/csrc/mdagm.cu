@@ -284,6 +284,31 @@ int mdagm_max_active_clusters(const SliceLaunch& sl) {
   }
 }
 
+// Clusters of C CTAs of the batched kernel the device can keep resident (<= 0: none).
+int mdagm_batch_max_active_clusters(int C, int threads, size_t smem) {
+  if (raise_smem_limit(mdagm_batch_kernel<double, MODE_CGDIR>, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)mdagm_batch_kernel<double, MODE_CGDIR>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return n;
+}
+
 template <class R, int MODE>
 cudaError_t launch_mdagm_batch(const MdagmArgs<R>* descs, const int2* tiles, int ntiles, int C, int threads,
                                size_t smem, cudaStream_t s) {

@@ -42,7 +42,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
            "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory",
-           "hqmc_batch_set_solver",
+           "hqmc_batch_set_solver", "hqmc_batch_launch_shape",
            "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
            "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner",
            "hqmc_set_net_interval", "hqmc_set_guess_history", "hqmc_checkpoint_write", "hqmc_checkpoint_read")
@@ -123,6 +123,8 @@ _sig = {
     "hqmc_batch_last_error": ([_vp], ctypes.c_char_p),
     "hqmc_batch_launch_count": ([_vp], ctypes.c_longlong),
     "hqmc_batch_set_solver": ([_vp, _i], _i),
+    "hqmc_batch_launch_shape": ([_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                 ctypes.POINTER(ctypes.c_float)], _i),
     "hqmc_batch_cg_solve": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
                              ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_batch_trajectory": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64), _u64, _i,
@@ -450,11 +452,11 @@ class Batch:
     """Independent chains of possibly different lattices driven together (hqmc_make_batch)."""
 
     def __init__(self, lattices, dtau: float = 0.1, t: float = 1.0, J: float = 1.0, K: float = 0.0,
-                 noncompact: bool = False):
+                 noncompact: bool = False, autotune: bool = False):
         self.lattices = [(int(L), int(N)) for L, N in lattices]
         n = len(self.lattices)
         arr = (Params * n)(*[Params(L, N, dtau, t, J, K, ACTION_NONCOMPACT if noncompact else ACTION_COMPACT,
-                                    0, 0, 1) for L, N in self.lattices])
+                                    0, 1 if autotune else 0, 1) for L, N in self.lattices])
         h = _vp()
         rc = _lib.hqmc_make_batch(arr, n, ctypes.byref(h))
         if rc != OK:
@@ -480,6 +482,13 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(_lib.hqmc_batch_launch_count(self._h))
+
+    def launch_shape(self) -> dict:
+        """Tile shape of the batched fused launch (hqmc_batch_launch_shape)."""
+        c, o, t, us = _i(), _i(), _i(), ctypes.c_float()
+        self._check(_lib.hqmc_batch_launch_shape(self._h, ctypes.byref(c), ctypes.byref(o), ctypes.byref(t),
+                                                 ctypes.byref(us)))
+        return {"cluster": c.value, "order": o.value, "threads": t.value, "tuned_us": us.value}
 
     def set_solver(self, solver):
         """"cg64" (default) or "pcg64" for every chain (hqmc_batch_set_solver)."""

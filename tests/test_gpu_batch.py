@@ -50,6 +50,24 @@ def test_batched_trajectory_equals_independent_trajectories(hq):
         assert torch.equal(thetas[i], t1), i
 
 
+def test_autotuned_batch_equals_independent_solves(hq):
+    """The batch autotuner picks a cluster size and tile order; the results stay those
+    of single-chain runs bit for bit, whatever it picks."""
+    thetas = [torch.from_numpy(inputs.theta_hot(L, N, 540 + i)).cuda() for i, (L, N) in enumerate(LATS)]
+    phis = [torch.from_numpy(inputs.complex_gaussian(L, N, 640 + i)).cuda() for i, (L, N) in enumerate(LATS)]
+    with hq.Batch(LATS, autotune=True) as b:
+        shape = b.launch_shape()
+        xs, infos = b.cg_solve(thetas, phis, tol=1e-10)
+    print("autotuned batch shape:", shape)
+    assert shape["cluster"] in (1, 2, 4, 8) and shape["order"] in (0, 1, 2) and shape["tuned_us"] > 0
+    for i, (L, N) in enumerate(LATS):
+        with hq.Config(L, N, variant=1) as cfg:
+            x1, info1 = hq.cg_solve(cfg, thetas[i], phis[i], tol=1e-10)
+        assert infos[i]["status"] == 0 and infos[i]["iterations"] == info1["iterations"]
+        assert torch.equal(xs[i], x1), i
+        assert infos[i]["true_residual"] == info1["true_residual"]
+
+
 def test_batch_rejects_bad_lattice(hq):
     with pytest.raises(hq.HQMCError):
         hq.Batch([(8, 16), (9, 16)])
