@@ -437,6 +437,14 @@ HQMC_API int hqmc_net_train_step(hqmc_config* cfg, hqmc_net* net, const double* 
  * c % k == 0 of each reliable-update segment, the tau-line preconditioner the
  * others (k >= 1; 1 = every iteration).  Host-only; HQMC_EINVAL for k < 1. */
 HQMC_API int hqmc_set_net_interval(hqmc_config* cfg, int k);
+/* Arithmetic of the net's inference layers (hqmc_net_apply, the learned guess and
+ * flexible CG): on = 1 (default) stores the 16-channel activations in BF16 and
+ * runs the layers that read them (16 -> 16 and 16 -> 1) on tensor cores: BF16
+ * activations times BF16 weights with FP32 accumulation (warp-level mma, 16
+ * output channels x 8 sites per product), the transport phases applied to the
+ * FP32 products.  on = 0 keeps every layer and activation in FP32 on CUDA cores.
+ * Training stays in FP32.  Host-only; HQMC_EINVAL unless on is 0 or 1. */
+HQMC_API int hqmc_set_net_tensor_cores(hqmc_config* cfg, int on);
 
 /* Chronological initial guess of the solves inside hqmc_leapfrog and
  * hqmc_trajectory (Brower, Ivanenko, Levi and Orginos, "Chronological inversion

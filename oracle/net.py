@@ -42,6 +42,17 @@ def transport(theta: np.ndarray, h: np.ndarray, mu: int) -> np.ndarray:
     return sign * np.roll(h, 1, axis=0)
 
 
+def round_bf16(a: np.ndarray) -> np.ndarray:
+    """Nearest bfloat16 value (8-bit significand, ties to even) of each real entry,
+    taken through float32 and returned as float64: the upper 16 bits of the
+    float32 pattern after adding half an ulp of bfloat16 (0x7FFF plus the lowest
+    kept bit, which breaks ties towards an even significand)."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32)
+    u = (u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
+    return u.view(np.float32).astype(np.float64)
+
+
 def layer(theta: np.ndarray, h: np.ndarray, W: np.ndarray) -> np.ndarray:
     """One layer: sum over directions of the transported field times W[mu]^T."""
     out = None
@@ -51,11 +62,17 @@ def layer(theta: np.ndarray, h: np.ndarray, W: np.ndarray) -> np.ndarray:
     return out
 
 
-def apply(theta: np.ndarray, r: np.ndarray, weights) -> np.ndarray:
-    """K(theta) r for r of shape (Ntau, L, L)."""
+def apply(theta: np.ndarray, r: np.ndarray, weights, tensor_cores: bool = False) -> np.ndarray:
+    """K(theta) r for r of shape (Ntau, L, L).  tensor_cores: every 16-channel
+    activation is stored in bfloat16 (real and imaginary parts rounded to the
+    nearest bfloat16) before the next layer reads it, the precision of layers that
+    contract BF16 activations with BF16 weights in a wide accumulator; all
+    arithmetic stays FP64."""
     h = r[..., None].astype(np.complex128)
     for W in weights:
         h = layer(theta, h, np.asarray(W, dtype=np.float64))
+        if tensor_cores and h.shape[-1] == 16:
+            h = round_bf16(h.real) + 1j * round_bf16(h.imag)
     return h[..., 0]
 
 

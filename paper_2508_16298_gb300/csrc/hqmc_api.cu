@@ -117,6 +117,7 @@ struct hqmc_config {
   float2* r_old32 = nullptr;                                           // flexible CG: residual before the update
   double *part_fz = nullptr, *part_fx = nullptr;                       // flexible CG: <r, z>, <r_old, z> partials
   int net_interval = 1;                                                // flexible CG: net on iterations c % k == 0
+  int net_tc = 1;                                                      // inference 16 -> 16 layers on tensor cores
   // chronological initial guess of leapfrog solves (hqmc_set_guess_history): the
   // last guess_k solutions of the current integration and an orthonormal basis
   double2* hist = nullptr;                                             // guess_k vectors, contiguous
@@ -467,7 +468,7 @@ int net_forward(hqmc_config* cfg, hqmc_net* net, const double2* r, double2* z, c
   for (int l = 0; l < kNetLayers; ++l) {
     if (host_weights)
       LK(1, launch_net_layer_host_weights(cfg->g, cfg->th32, net->hw.data() + net->off[l], net->cin[l], net->cout[l],
-                                          cfg->net_h[l], cfg->net_h[l + 1], nullptr, s));
+                                          cfg->net_h[l], cfg->net_h[l + 1], nullptr, s, cfg->net_tc != 0));
     else
       LK(1, launch_net_layer(cfg->g, cfg->th32, (const char*)net->wb + 2 * (size_t)net->off[l], net->cin[l],
                              net->cout[l], cfg->net_h[l], cfg->net_h[l + 1], s));
@@ -484,7 +485,7 @@ int net_forward32(hqmc_config* cfg, hqmc_net* net, const float2* r, float2* z, c
   for (int l = 0; l < kNetLayers; ++l) {
     float2* out = l == kNetLayers - 1 ? z : cfg->net_h[l + 1];
     LK(1, launch_net_layer_host_weights(cfg->g, cfg->th32, net->hw.data() + net->off[l], net->cin[l], net->cout[l],
-                                        in, out, cfg->st, s));
+                                        in, out, cfg->st, s, cfg->net_tc != 0));
     in = out;
   }
   return HQMC_OK;
@@ -2917,6 +2918,16 @@ int hqmc_set_net_interval(hqmc_config* cfg, int k) {
   if (!cfg || k < 1) return HQMC_EINVAL;
   if (k == cfg->net_interval) return HQMC_OK;
   cfg->net_interval = k;
+  CK(cudaDeviceSynchronize());  // no cached loop graph may still be running
+  for (auto& g : cfg->graphs) cudaGraphExecDestroy(g.exec);
+  cfg->graphs.clear();
+  return HQMC_OK;
+}
+
+int hqmc_set_net_tensor_cores(hqmc_config* cfg, int on) {
+  if (!cfg || (on != 0 && on != 1)) return HQMC_EINVAL;
+  if (on == cfg->net_tc) return HQMC_OK;
+  cfg->net_tc = on;
   CK(cudaDeviceSynchronize());  // no cached loop graph may still be running
   for (auto& g : cfg->graphs) cudaGraphExecDestroy(g.exec);
   cfg->graphs.clear();

@@ -373,8 +373,14 @@ cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, in
 // Inference layer with the weights passed by value from host memory ([7][cout][cin] FP32 values of
 // the BF16 weights): the same arithmetic as launch_net_layer.
 // st (nullable): skip the launch unless the solve is running (flexible CG).
+// tensor_cores: the 16-channel activations are BF16 in the chunk layout (net.cu);
+// 1 -> 16 runs on CUDA cores and rounds its output, 16 -> 16 and 16 -> 1 are
+// BF16 mma.sync products with FP32 accumulation.  Otherwise every layer is FP32
+// on CUDA cores with channel-planar activations.  Every layer of one pass must
+// use the same setting.
 cudaError_t launch_net_layer_host_weights(const Geo& g, const float2* th32, const float* w, int cin, int cout,
-                                         const float2* in, float2* out, const CgState* st, cudaStream_t s);
+                                         const float2* in, float2* out, const CgState* st, cudaStream_t s,
+                                         bool tensor_cores = false);
 cudaError_t launch_net_wgrad(const Geo& g, const float2* th32, int cin, int cout, const float2* d, const float2* h,
                              double* partials, int nchunks, cudaStream_t s);
 cudaError_t launch_net_loss(const float2* h, const double2* x, const double* xx, float2* d, double* part, int nblocks,

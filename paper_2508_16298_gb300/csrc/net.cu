@@ -24,6 +24,25 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// BF16 activations of the tensor-core inference path ("chunk layout"): site i
+// holds its 16 complex channels in 64 bytes, four 16-byte chunks; chunk q packs
+//   re(2q) re(2q+1) | re(2q+8) re(2q+9) | im(2q) im(2q+1) | im(2q+8) im(2q+9)
+// (BF16 pairs, lower channel in the low half).  Chunk q of a site is exactly the
+// B fragment of mma.m16n8k16 that lane (g, q) needs for column g (its real part
+// in .x .y, its imaginary part in .z .w), and a warp's 16-byte loads of chunks
+// 0..3 of 8 consecutive sites cover 512 contiguous bytes.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+__device__ __forceinline__ void store_bf16_chunks(uint4* __restrict__ dst, const float2 (&acc)[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    dst[q] = make_uint4(pack_bf16x2(acc[2 * q].x, acc[2 * q + 1].x), pack_bf16x2(acc[2 * q + 8].x, acc[2 * q + 9].x),
+                        pack_bf16x2(acc[2 * q].y, acc[2 * q + 1].y), pack_bf16x2(acc[2 * q + 8].y, acc[2 * q + 9].y));
+}
+
 // Transport factor and neighbour index of direction mu at global site i.
 __device__ __forceinline__ void net_neighbour(const Geo& g, const float2* __restrict__ th32, long long i, int mu,
                                               long long& j, float2& ph) {
@@ -194,7 +213,9 @@ struct NetLayerW {
   float w[7][CIN][COUT];
 };
 
-template <int CIN, int COUT>
+// OUT_BF16 (1 -> 16 layer of the tensor-core path): the output is rounded to BF16
+// and written in the chunk layout instead of channel-planar FP32.
+template <int CIN, int COUT, bool OUT_BF16>
 __global__ void __launch_bounds__(256) net_layer_cw_kernel(Geo g, const float2* __restrict__ th32,
                                                            const __grid_constant__ NetLayerW<CIN, COUT> W,
                                                            const float2* __restrict__ in, float2* __restrict__ out,
@@ -248,19 +269,148 @@ __global__ void __launch_bounds__(256) net_layer_cw_kernel(Geo g, const float2* 
         }
       }
     }
+    if constexpr (OUT_BF16 && COUT == 16) {
+      store_bf16_chunks(reinterpret_cast<uint4*>(out) + (size_t)i * 4, acc);
+    } else {
 #pragma unroll
-    for (int c = 0; c < COUT; ++c) out[(size_t)c * n + i] = acc[c];
+      for (int c = 0; c < COUT; ++c) out[(size_t)c * n + i] = acc[c];
+    }
   }
 }
 
-template <int CIN, int COUT>
+// Tensor-core inference layer with 16 input channels (16 or 1 output channels),
+// BF16 activations in the chunk layout.  The phase of a transport is the same
+// for every channel, so it factors out of the channel contraction:
+//   sum_c' W[mu][c][c'] (T_mu h)(x, c') = ph_mu(x) (W[mu] h(x + mu))(c).
+// Per group of 8 consecutive sites and direction mu a warp forms the products
+// U = W[mu] (16 x 16) H (16 x 8) of the raw neighbour activations, once for the
+// real and once for the imaginary parts: mma.sync.m16n8k16 with BF16 operands and
+// FP32 accumulation, the weight fragments of all seven directions held in
+// registers (rows g, g+8, columns 2q, 2q+1, 2q+8, 2q+9 of W[mu] in lane (g, q)).
+// The centre and +-tau terms have real phases (1, or the boundary sign, applied
+// exactly to the BF16 operand) and accumulate in place; the +-x and +-y products
+// are multiplied by their sites' phases in FP32 and added.  Lane (g, q) loads
+// chunk q of site g's neighbour (its B fragment, 16 bytes) and owns output
+// channels g and g+8 of sites 2q and 2q+1.  COUT = 16: two lanes swap half of
+// their results so that each writes one 16-byte chunk (512 contiguous bytes per
+// warp); COUT = 1 (weight rows 1..15 zero): lanes g = 0 write the FP32 output.
+struct NetLayerBf16 {
+  uint32_t w[7 * 16 * 8];  // [mu][c][c'/2]: BF16 pairs (even c' in the low half); rows c >= COUT zero
+};
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(256, 4) net_layer_tc_kernel(Geo g, const float2* __restrict__ th32,
+                                                           const __grid_constant__ NetLayerBf16 W,
+                                                           const uint4* __restrict__ in, void* __restrict__ out,
+                                                           int n, const CgState* st) {
+  if (st && *(volatile const int*)&st->done != CG_RUNNING) return;  // flexible CG: the solve has stopped
+  // weights in shared memory, rows padded to 12 words: the fragment reads of a warp
+  // (rows g, columns 2q..) hit 32 distinct banks, and no registers hold them
+  __shared__ uint32_t ws[7 * 16 * 12];
+  for (int k = threadIdx.x; k < 7 * 16 * 8; k += blockDim.x) ws[(k >> 3) * 12 + (k & 7)] = W.w[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  auto frag = [&](int mu) {
+    const uint32_t* r0 = ws + (mu * 16 + gq) * 12 + tq;
+    const uint32_t* r8 = r0 + 8 * 12;
+    return make_uint4(r0[0], r8[0], r0[4], r8[4]);  // rows g, g+8 x columns 2q.., 2q+8..
+  };
+  const int V = g.V, L = g.L, N = g.Ntau;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int srcA = (2 * tq) << 2, srcB = (2 * tq + 1) << 2;  // lanes whose column is site 2q / 2q+1
+  for (int i0 = warp * 8; i0 < n; i0 += nwarps * 8) {  // n is a multiple of 8 (L even)
+    const int i = i0 + gq;  // this lane's column (B operand)
+    const int tau = i / V, s = i - tau * V, y = s / L, x = s - y * L;
+    const int base = tau * V;
+    const int tp = tau + 1 == N ? 0 : tau + 1, tm = tau == 0 ? N - 1 : tau - 1;
+    // the seven neighbours (centre, +x, -x, +y, -y, +tau, -tau) and the four link
+    // angles, all requested before any product so that their latencies overlap
+    int j[7];
+    j[0] = i;
+    j[1] = base + y * L + (x + 1 == L ? 0 : x + 1);
+    j[2] = base + y * L + (x == 0 ? L - 1 : x - 1);
+    j[3] = base + (y + 1 == L ? 0 : y + 1) * L + x;
+    j[4] = base + (y == 0 ? L - 1 : y - 1) * L + x;
+    j[5] = tp * V + s;
+    j[6] = tm * V + s;
+    uint4 b[7];
+#pragma unroll
+    for (int mu = 0; mu < 7; ++mu) b[mu] = __ldg(in + (size_t)j[mu] * 4 + tq);
+    const float thx_p = __ldg(th32 + i).x, thx_m = __ldg(th32 + j[2]).x;
+    const float thy_p = __ldg(th32 + i).y, thy_m = __ldg(th32 + j[4]).y;
+    // accumulators: [0] (channel g, site 2q), [1] (g, 2q+1), [2] (g+8, 2q), [3] (g+8, 2q+1)
+    float dr[4] = {0.f, 0.f, 0.f, 0.f}, di[4] = {0.f, 0.f, 0.f, 0.f};
+    // centre and +-tau: real phases; the antiperiodic sign flips the BF16 sign bits (exact)
+    const uint32_t s5 = tp == 0 ? 0x80008000u : 0u, s6 = tau == 0 ? 0x80008000u : 0u;
+#pragma unroll
+    for (int mu = 0; mu < 7; mu += (mu == 0 ? 5 : 1)) {  // 0, 5, 6
+      const uint4 f = frag(mu);
+      const uint32_t a4[4] = {f.x, f.y, f.z, f.w};
+      const uint32_t sg = mu == 5 ? s5 : mu == 6 ? s6 : 0u;
+      mma_bf16_16816(dr, a4, b[mu].x ^ sg, b[mu].y ^ sg);
+      mma_bf16_16816(di, a4, b[mu].z ^ sg, b[mu].w ^ sg);
+    }
+    // +-x, +-y: the products times their sites' phases (ph = e^{+i theta} forward,
+    // e^{-i theta(neighbour)} backward), the phases from the lanes owning the sites
+#pragma unroll
+    for (int mu = 1; mu <= 4; ++mu) {
+      float sn, cs;
+      __sincosf(mu == 1 ? thx_p : mu == 2 ? thx_m : mu == 3 ? thy_p : thy_m, &sn, &cs);
+      const float phx = cs, phy = (mu & 1) ? sn : -sn;
+      float ur[4] = {0.f, 0.f, 0.f, 0.f}, ui[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint4 f = frag(mu);
+      const uint32_t a4[4] = {f.x, f.y, f.z, f.w};
+      mma_bf16_16816(ur, a4, b[mu].x, b[mu].y);
+      mma_bf16_16816(ui, a4, b[mu].z, b[mu].w);
+      const float ax = __shfl_sync(0xffffffffu, phx, srcA), ay = __shfl_sync(0xffffffffu, phy, srcA);
+      const float bx = __shfl_sync(0xffffffffu, phx, srcB), by = __shfl_sync(0xffffffffu, phy, srcB);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float px = (e & 1) ? bx : ax, py = (e & 1) ? by : ay;
+        dr[e] = fmaf(px, ur[e], fmaf(-py, ui[e], dr[e]));
+        di[e] = fmaf(px, ui[e], fmaf(py, ur[e], di[e]));
+      }
+    }
+    if constexpr (COUT == 16) {
+      // lane (g, q) keeps site 2q + (g & 1) and swaps the other site's values with lane g ^ 1
+      const bool odd = gq & 1;
+      const uint32_t keep_r = odd ? pack_bf16x2(dr[1], dr[3]) : pack_bf16x2(dr[0], dr[2]);  // channels g, g+8
+      const uint32_t keep_i = odd ? pack_bf16x2(di[1], di[3]) : pack_bf16x2(di[0], di[2]);
+      const uint32_t send_r = odd ? pack_bf16x2(dr[0], dr[2]) : pack_bf16x2(dr[1], dr[3]);
+      const uint32_t send_i = odd ? pack_bf16x2(di[0], di[2]) : pack_bf16x2(di[1], di[3]);
+      const uint32_t recv_r = __shfl_xor_sync(0xffffffffu, send_r, 4);
+      const uint32_t recv_i = __shfl_xor_sync(0xffffffffu, send_i, 4);
+      // chunk g/2 of the kept site: channels 2c, 2c+1 (lo/hi) from the even and odd lane
+      const uint32_t lo_r = odd ? recv_r : keep_r, hi_r = odd ? keep_r : recv_r;
+      const uint32_t lo_i = odd ? recv_i : keep_i, hi_i = odd ? keep_i : recv_i;
+      const uint4 c = make_uint4((lo_r & 0xffffu) | (hi_r << 16), (lo_r >> 16) | (hi_r & 0xffff0000u),
+                                 (lo_i & 0xffffu) | (hi_i << 16), (lo_i >> 16) | (hi_i & 0xffff0000u));
+      reinterpret_cast<uint4*>(out)[(size_t)(i0 + 2 * tq + (odd ? 1 : 0)) * 4 + (gq >> 1)] = c;
+    } else {
+      if (gq == 0)
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(out) + i0 + 2 * tq) =
+            make_float4(dr[0], di[0], dr[1], di[1]);
+    }
+  }
+}
+
+template <int CIN, int COUT, bool OUT_BF16 = false>
 static cudaError_t layer_cw(const Geo& g, const float2* th32, const float* w, const float2* in, float2* out,
                             int n, int nb, const CgState* st, cudaStream_t s) {
   NetLayerW<CIN, COUT> W;
   for (int mu = 0; mu < 7; ++mu)
     for (int c = 0; c < COUT; ++c)
       for (int cp = 0; cp < CIN; ++cp) W.w[mu][cp][c] = w[(mu * COUT + c) * CIN + cp];
-  net_layer_cw_kernel<CIN, COUT><<<nb, 256, 0, s>>>(g, th32, W, in, out, n, st);
+  net_layer_cw_kernel<CIN, COUT, OUT_BF16><<<nb, 256, 0, s>>>(g, th32, W, in, out, n, st);
   return cudaGetLastError();
 }
 
@@ -428,9 +578,28 @@ cudaError_t launch_net_layer(const Geo& g, const float2* th32, const void* W, in
 }
 
 cudaError_t launch_net_layer_host_weights(const Geo& g, const float2* th32, const float* w, int cin, int cout,
-                                         const float2* in, float2* out, const CgState* st, cudaStream_t s) {
+                                         const float2* in, float2* out, const CgState* st, cudaStream_t s,
+                                         bool tensor_cores) {
   const int n = g.V * g.Ntau;
   const int nb = blocks_for(n, 256);
+  if (tensor_cores) {  // 16-channel activations in BF16 chunks: in (16 -> *) / out (* -> 16)
+    if (n % 8 != 0) return cudaErrorInvalidValue;
+    if (cin == 1 && cout == 16) return layer_cw<1, 16, true>(g, th32, w, in, out, n, nb, st, s);
+    if (cin != 16 || (cout != 16 && cout != 1)) return cudaErrorInvalidValue;
+    NetLayerBf16 W{};  // the weights are BF16 values: the conversion is exact; rows >= cout stay zero
+    for (int mu = 0; mu < 7; ++mu)
+      for (int c = 0; c < cout; ++c)
+        for (int p = 0; p < 8; ++p) {
+          const float* wr = w + ((size_t)mu * cout + c) * 16;
+          const __nv_bfloat162 v = __floats2bfloat162_rn(wr[2 * p], wr[2 * p + 1]);
+          W.w[(mu * 16 + c) * 8 + p] = *reinterpret_cast<const uint32_t*>(&v);
+        }
+    const int groups = n / 8;  // one warp per group of 8 sites, 8 warps per block
+    const uint4* in4 = reinterpret_cast<const uint4*>(in);
+    if (cout == 16) net_layer_tc_kernel<16><<<blocks_for(groups, 8), 256, 0, s>>>(g, th32, W, in4, out, n, st);
+    else net_layer_tc_kernel<1><<<blocks_for(groups, 8), 256, 0, s>>>(g, th32, W, in4, out, n, st);
+    return cudaGetLastError();
+  }
   if (cin == 1 && cout == 16) return layer_cw<1, 16>(g, th32, w, in, out, n, nb, st, s);
   if (cin == 16 && cout == 16) return layer_cw<16, 16>(g, th32, w, in, out, n, nb, st, s);
   if (cin == 16 && cout == 1) return layer_cw<16, 1>(g, th32, w, in, out, n, nb, st, s);

@@ -45,7 +45,7 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_batch_set_solver", "hqmc_batch_launch_shape",
            "hqmc_net_create", "hqmc_net_free", "hqmc_net_num_weights", "hqmc_net_get_weights",
            "hqmc_net_set_weights", "hqmc_net_apply", "hqmc_net_train_step", "hqmc_set_preconditioner",
-           "hqmc_set_net_interval", "hqmc_set_guess_history", "hqmc_checkpoint_write", "hqmc_checkpoint_read")
+           "hqmc_set_net_interval", "hqmc_set_net_tensor_cores", "hqmc_set_guess_history", "hqmc_checkpoint_write", "hqmc_checkpoint_read")
 
 
 class Params(ctypes.Structure):
@@ -138,6 +138,7 @@ _sig = {
     "hqmc_net_train_step": ([_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_set_preconditioner": ([_vp, _vp], _i),
     "hqmc_set_net_interval": ([_vp, _i], _i),
+    "hqmc_set_net_tensor_cores": ([_vp, _i], _i),
     "hqmc_set_guess_history": ([_vp, _i], _i),
     "hqmc_checkpoint_write": ([ctypes.c_char_p, ctypes.POINTER(Checkpoint), _vp, _vp], _i),
     "hqmc_checkpoint_read": ([ctypes.c_char_p, ctypes.POINTER(Checkpoint), _vp, _vp], _i),
@@ -596,6 +597,12 @@ def set_net_interval(cfg: Config, k: int):
     """Flexible CG ("flearned"): the net preconditions every k-th iteration, the
     tau-line preconditioner the others."""
     cfg.check(_lib.hqmc_set_net_interval(cfg.handle, int(k)))
+
+
+def set_net_tensor_cores(cfg: Config, on: bool):
+    """Inference 16 -> 16 layers on tensor cores (BF16 operands, FP32 accumulation;
+    the default) or in FP32 on CUDA cores."""
+    cfg.check(_lib.hqmc_set_net_tensor_cores(cfg.handle, 1 if on else 0))
 
 
 def save_checkpoint(path: str, theta, seed: int, traj_counter: int, dt: float, nsteps: int, solver="cg64",
