@@ -361,6 +361,43 @@ def thermalize(hqmc, cfg, theta, wl, seed):
     return dt_prod, report
 
 
+def train_net_streamed(hqmc, inputs, cfg, wl, theta, dt, seed, dev):
+    """Online training on wl["train_triples"] sampler triples that are never stored:
+    the chain advances one trajectory at the production dt, then `stream_sources`
+    sources phi = M^dagger R on that field are solved (preconditioned mixed CG,
+    FP64 residual 1e-8) and each (theta, phi, x) takes one Adam step as soon as it
+    exists.  Device memory stays that of one triple, whatever the count.  Returns
+    the net and a report with the mean loss over each block of 100 triples."""
+    import torch
+    L, N = wl["L"], wl["Ntau"]
+    total, per = wl["train_triples"], wl["stream_sources"]
+    kw = dict(nsteps=wl["nsteps"], dt=dt, tol=wl["tol"], solver="pmixed")
+    net = hqmc.Net(seed=seed)
+    hqmc.set_preconditioner(cfg, net)
+    losses, curve = [], []
+    t_sample = t_train = 0.0
+    k = 0
+    while len(losses) < total:
+        t0 = time.perf_counter()
+        hqmc.trajectory(cfg, theta, seed=seed, traj_counter=TRIPLE_COUNTER + k, **kw)
+        for m in range(min(per, total - len(losses))):
+            R = torch.from_numpy(inputs.complex_gaussian(L, N, seed * 7919 + 97 * k + m)).to(dev)
+            phi = hqmc.apply_M(cfg, theta, R, dagger=True)
+            x, _ = hqmc.cg_solve(cfg, theta, phi, tol=wl["tol"], solver="pmixed")
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            t_sample += t1 - t0
+            losses.append(net.train_step(cfg, theta, phi, x, lr=wl["lr"]))
+            t0 = time.perf_counter()
+            t_train += t0 - t1
+            if len(losses) % 100 == 0:
+                curve.append(round(statistics.mean(losses[-100:]), 4))
+        k += 1
+    return net, {"triples": len(losses), "stored": 0, "trajectories": k, "sources_per_trajectory": per,
+                 "epochs": 1, "sampler_s": round(t_sample, 2), "train_s": round(t_train, 2),
+                 "loss_per_100_triples": curve, "loss": "||K(theta) phi - x||^2 / ||x||^2"}
+
+
 def train_net(hqmc, inputs, cfg, wl, theta, dt, seed, dev):
     """Untimed set-up of the learned solver: `triple_trajs` trajectories of the chain at the
     production dt; after each, `rhs_per_traj` sources phi = M^dagger R with fresh Gaussian R
@@ -465,7 +502,8 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     learned = None
     net = None
     if wl["solver"] in ("learned", "plearned"):
-        net, learned = train_net(hqmc, inputs, cfg, wl, theta, dt, seed, dev)
+        trainer = train_net_streamed if wl.get("train_triples") else train_net
+        net, learned = trainer(hqmc, inputs, cfg, wl, theta, dt, seed, dev)
 
     for k in range(args.warmup):
         hqmc.trajectory(cfg, theta, seed=seed, traj_counter=k, **kw)
@@ -854,6 +892,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--profile", action="store_true", help="run the short ncu capture case and exit")
+    ap.add_argument("--train-triples", type=int, default=0,
+                    help="learned workloads: train online on this many sampler triples (none stored) "
+                         "instead of epochs over the stored set")
     args = ap.parse_args()
     if args.profile:
         run_profile_case(WORKLOADS[args.workload])
@@ -862,6 +903,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
+    if args.train_triples:
+        wl = dict(wl, train_triples=args.train_triples, stream_sources=20)
     if world > 1 and args.impl == "ours":
         import torch
         import torch.distributed as dist
