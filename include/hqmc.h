@@ -69,10 +69,12 @@ enum {
     HQMC_SOLVER_MIXED = 1,   /* CG with M^dagger M in FP32 (complex float) and FP64 reliable
                                 residual updates every params.reliable_interval iterations */
     HQMC_SOLVER_LEARNED = 2, /* the attached net (hqmc_set_preconditioner) corrects the initial
-                                guess, x <- x + K(theta)(phi - O x) with phi - O x from the FP32
-                                apply (the net's input precision), kept only if its FP64 residual
-                                is below that one; then the mixed solver, whose FP64 true residual
-                                judges convergence */
+                                guess, x <- x + z with z = K(theta) r0, r0 = phi - O x, kept only if
+                                ||r0 - O z|| < ||r0|| (both from the FP32 apply: they only decide);
+                                then the mixed solver, whose FP64 true residual judges convergence.
+                                Inside hqmc_leapfrog / hqmc_trajectory with the chronological guess
+                                (hqmc_set_guess_history), the net is not tried again in that
+                                integration after two consecutive rejections */
     /* The same three with the tau-line preconditioner Otilde^{-1} of hqmc_apply_precond in the
      * preconditioned CG of Methods Eq. (pCG): directions from z = Otilde^{-1} r, step lengths
      * from <r, z>; convergence is still judged on ||r|| and the FP64 true residual. */
@@ -139,6 +141,8 @@ typedef struct hqmc_traj_info {
     double H0, H1, dH;     /* Hamiltonian at start and end, dH = H1 - H0 */
     double u;              /* the uniform number used by the Metropolis test */
     double max_true_residual;
+    int net_guesses_tried; /* learned solvers: solves that applied the net to their initial residual */
+    int net_guesses_used;  /* ... and kept its correction */
 } hqmc_traj_info;
 
 /* ---- configuration ----------------------------------------------------- */

@@ -118,6 +118,9 @@ struct hqmc_config {
   double *part_fz = nullptr, *part_fx = nullptr;                       // flexible CG: <r, z>, <r_old, z> partials
   int net_interval = 1;                                                // flexible CG: net on iterations c % k == 0
   int net_tc = 1;                                                      // inference 16 -> 16 layers on tensor cores
+  // learned guess inside a leapfrog integration with the chronological guess:
+  // consecutive rejections of the net's correction, and whether the last solve tried it
+  int net_adaptive = 0, net_rejects = 0, net_tried = 0;
   // chronological initial guess of leapfrog solves (hqmc_set_guess_history): the
   // last guess_k solutions of the current integration and an orthonormal basis
   double2* hist = nullptr;                                             // guess_k vectors, contiguous
@@ -718,43 +721,48 @@ bool hermitian_solve(int k, std::vector<double>& A, std::vector<double>& b) {
 // HQMC_SOLVER_LEARNED: x <- x + K(theta)(phi - O x) from the attached net, kept
 // only if it lowers the FP64 residual, then the mixed solver (plain CG with its
 // FP64 true residual stays the judge and the fallback).
+// After this many consecutive rejections within one leapfrog integration that has
+// the chronological guess, the learned guess is not tried again in that integration.
+constexpr int kNetMaxRejects = 2;
+
 int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
           hqmc_solve_info* info, cudaStream_t s) {
   NvtxRange nv("hqmc cg solve");
   int net_used = 0;
   const bool pc = solver_pc(solver);
-  bool started = false;  // the FP64 residual that starts the recurrence is already in place
+  cfg->net_tried = 0;
   if (solver_base(solver) == HQMC_SOLVER_LEARNED) {
-    // candidate x1 = x + K r0 with r0 = phi - O x; the CG workspace is free here.
-    // r0 comes from the FP32 fused apply: the net reads it in FP32, and ||r0|| only
-    // decides whether the candidate is kept.  The FP64 residual of x1 is computed as
-    // the start of the mixed recurrence, so a kept candidate costs no FP64 residual
-    // beyond the one any solve starts with; a rejected one restores x and starts again.
     if (!solver_fcg(solver)) solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
-    LK(1, launch_net_convert(x, cfg->xh32, 1, 1.0, cfg->n, s));  // x as float (xh32 is free until the loop)
-    {
+    // Inside a leapfrog integration with the chronological guess, the net is not
+    // tried again after kNetMaxRejects consecutive rejections (reset per integration).
+    if (!(cfg->net_adaptive && cfg->net_rejects >= kNetMaxRejects)) {
+      // candidate x + z with z = K r0, r0 = phi - O x.  Both residual norms come from
+      // the FP32 fused apply (r1 = r0 - O z): they only decide whether z is kept, and
+      // a rejected z then costs no FP64 residual and no copy of x.  The FP64 residual
+      // that starts the recurrence is computed afterwards, as for any solve.
+      cfg->net_tried = 1;
       MdagmArgs<float> a = mdagm_args<float, MODE_APPLY>(cfg);
       a.U = cfg->U32;
       a.x = cfg->xh32;
       a.y = cfg->q32;
+      LK(1, launch_net_convert(x, cfg->xh32, 1, 1.0, cfg->n, s));  // x as float (xh32 is free until the loop)
       LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
-    }
-    LK(1, launch_resid_from_fp32(cfg->n, phi, cfg->q32, cfg->vscratch, s));
-    LK(2, launch_cdot(cfg->n, cfg->vscratch, cfg->vscratch, cfg->act_grid, cfg->part_act, cfg->report, s));
-    RET(read_state(cfg, s));
-    const double rr0 = cfg->report_h[0];
-    RET(net_forward(cfg, cfg->net, cfg->vscratch, cfg->p64[1], s));                       // z = K r0
-    CK(cudaMemcpyAsync(cfg->p64[0], x, sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));  // keep x
-    LK(1, launch_kick(2 * cfg->n, (double*)x, (const double*)cfg->p64[1], 1.0, s));          // x += z
-    RET(residual(cfg, phi, x, cfg->r32, true, FIN_START, tol, maxit, GATE_ALWAYS, s));
-    RET(read_state(cfg, s));
-    if (cfg->report_h[0] < rr0) {
-      net_used = 1;
-      started = true;
-    } else {
-      CK(cudaMemcpyAsync(x, cfg->p64[0], sizeof(double2) * cfg->n, cudaMemcpyDeviceToDevice, s));
+      LK(1, launch_resid_from_fp32(cfg->n, phi, cfg->q32, cfg->vscratch, s));  // r0
+      LK(2, launch_cdot(cfg->n, cfg->vscratch, cfg->vscratch, cfg->act_grid, cfg->part_act, cfg->report, s));
+      RET(net_forward(cfg, cfg->net, cfg->vscratch, cfg->p64[1], s));  // z = K r0 (reads the host weights first)
+      LK(1, launch_net_convert(cfg->p64[1], cfg->xh32, 1, 1.0, cfg->n, s));
+      LK(1, (launch_fused<float, MODE_APPLY>(cfg, a, s)));
+      LK(1, launch_resid_from_fp32(cfg->n, cfg->vscratch, cfg->q32, cfg->r64, s));  // r1 = r0 - O z (r64 free here)
+      LK(2, launch_cdot(cfg->n, cfg->r64, cfg->r64, cfg->act_grid, cfg->part_act, cfg->report + 1, s));
+      RET(read_state(cfg, s));
+      if (cfg->report_h[1] < cfg->report_h[0]) {
+        net_used = 1;
+        LK(1, launch_kick(2 * cfg->n, (double*)x, (const double*)cfg->p64[1], 1.0, s));  // x += z
+      }
+      cfg->net_rejects = net_used ? 0 : cfg->net_rejects + 1;
     }
   }
+  const bool started = false;
   const bool mixed = solver_fp32(solver);
   hqmc_solve_info inf{};
   if (!started)
@@ -942,13 +950,26 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
   hqmc_solve_info si;
   int status = HQMC_OK;
   cfg->hist_n = cfg->hist_next = 0;  // a new integration: no earlier solutions
+  // the learned guess gives way to the chronological one after repeated rejections
+  // (only within this integration: the guard clears the gate on every exit)
+  struct AdaptiveGate {
+    hqmc_config* c;
+    ~AdaptiveGate() { c->net_adaptive = 0; }
+  } gate{cfg};
+  cfg->net_adaptive = (chrono && learned) ? 1 : 0;
+  cfg->net_rejects = 0;
+  auto account = [&]() {
+    ti->cg_solves++;
+    ti->cg_iterations += si.iterations;
+    ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+    ti->net_guesses_tried += cfg->net_tried;
+    ti->net_guesses_used += si.net_guess_used;
+  };
   RET(links(cfg, theta, true, mixed, s, false, learned));
   int rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
   if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
   status = merge_status(status, rc);
-  ti->cg_solves++;
-  ti->cg_iterations += si.iterations;
-  ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+  account();
   RET(chrono_push(cfg, X, s));
   RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
   for (int n = 0; n < nsteps; ++n) {
@@ -958,9 +979,7 @@ int leapfrog(hqmc_config* cfg, double* theta, double* p, const double2* phi, dou
     rc = solve(cfg, phi, X, tol, maxit, solver, &si, s);
     if (rc != HQMC_OK && rc != HQMC_ENOTCONV) return rc;
     status = merge_status(status, rc);
-    ti->cg_solves++;
-    ti->cg_iterations += si.iterations;
-    ti->max_true_residual = std::fmax(ti->max_true_residual, si.true_residual);
+    account();
     RET(chrono_push(cfg, X, s));
     RET(force(cfg, theta, X, cfg->F, cfg->dSf, s));
     LK(1, launch_kick(nb, p, cfg->F, dt / 2, s));

@@ -68,7 +68,8 @@ class SolveInfo(ctypes.Structure):
 class TrajInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("accepted", ctypes.c_int), ("cg_solves", ctypes.c_int),
                 ("cg_iterations", ctypes.c_int), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
-                ("dH", ctypes.c_double), ("u", ctypes.c_double), ("max_true_residual", ctypes.c_double)]
+                ("dH", ctypes.c_double), ("u", ctypes.c_double), ("max_true_residual", ctypes.c_double),
+                ("net_guesses_tried", ctypes.c_int), ("net_guesses_used", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -76,3 +76,39 @@ def test_guess_history_arguments(hq):
         hq.set_guess_history(cfg, 3)
         hq.set_guess_history(cfg, 2)  # smaller: no new allocation
         hq.set_guess_history(cfg, 0)
+
+
+def test_learned_guess_gives_way_to_the_chronological_guess(hq):
+    """A net equal to minus the identity is rejected on every solve (||r0 - O z|| =
+    ||r0 + O r0|| > ||r0||).  With the chronological guess the learned solver stops
+    trying it after two consecutive rejections in an integration; without it, it tries
+    every solve.  Either way the trajectory is the oracle's."""
+    from oracle import net as onet
+    L, N, nsteps, dt = 8, 16, 6, 0.02
+    lat = oracle.Lattice(L, N)
+    th0 = inputs.theta_hot(L, N, 81)
+    p0 = inputs.momenta(L, N, 82)
+    R = inputs.complex_gaussian(L, N, 83)
+    ref = oracle.trajectory(lat, th0, p0, R, u=0.5, nsteps=nsteps, dt=dt, tol=1e-12)
+    ws = onet.identity_weights(onet.LAYERS)
+    ws[0] = -ws[0]
+    flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
+    with hq.Config(L, N) as cfg:
+        net = hq.Net(seed=0)
+        net.set_weights(flat)
+        hq.set_preconditioner(cfg, net)
+        out = {}
+        for k in (0, 4):
+            hq.set_guess_history(cfg, k)
+            th = cuda(th0)
+            out[k] = hq.trajectory(cfg, th, p_in=cuda(p0), R_in=cuda(R), u_in=0.5, nsteps=nsteps, dt=dt, tol=1e-10,
+                                   solver="plearned"), th.cpu().numpy()
+        hq.set_preconditioner(cfg, None)
+        net.close()
+    for k, (info, th) in out.items():
+        assert info["status"] == 0 and info["max_true_residual"] <= 1e-10
+        assert info["net_guesses_used"] == 0
+        assert info["net_guesses_tried"] == (2 if k else nsteps + 1), (k, info["net_guesses_tried"])
+        assert abs(info["dH"] - ref["dH"]) < 1e-7 and bool(info["accepted"]) == ref["accepted"]
+        want = ref["theta"] if ref["accepted"] else th0
+        assert np.max(np.abs(th - want)) < 1e-8
