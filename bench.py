@@ -672,6 +672,9 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
                               (1 - statistics.mean(i["accepted"] for i in infos)) / len(infos)) ** 0.5,
         "dt": dt,
         "cg_iterations_per_traj": its_per_traj,
+        "net_guesses_per_traj": {"tried": statistics.mean(i["net_guesses_tried"] for i in infos),
+                                 "kept": statistics.mean(i["net_guesses_used"] for i in infos),
+                                 "solves": statistics.mean(i["cg_solves"] for i in infos)},
         "dH": [round(i["dH"], 6) for i in infos],
         "max_true_residual": max(i["max_true_residual"] for i in infos),
         "step_ms": [round(s, 3) for s in step_ms],

@@ -74,7 +74,8 @@ enum {
                                 then the mixed solver, whose FP64 true residual judges convergence.
                                 Inside hqmc_leapfrog / hqmc_trajectory with the chronological guess
                                 (hqmc_set_guess_history), the net is not tried again in that
-                                integration after two consecutive rejections */
+                                integration after two consecutive tries that did not cut the
+                                residual norm at least in half (kept or not) */
     /* The same three with the tau-line preconditioner Otilde^{-1} of hqmc_apply_precond in the
      * preconditioned CG of Methods Eq. (pCG): directions from z = Otilde^{-1} r, step lengths
      * from <r, z>; convergence is still judged on ||r|| and the FP64 true residual. */

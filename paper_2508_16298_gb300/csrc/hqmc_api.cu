@@ -119,7 +119,7 @@ struct hqmc_config {
   int net_interval = 1;                                                // flexible CG: net on iterations c % k == 0
   int net_tc = 1;                                                      // inference 16 -> 16 layers on tensor cores
   // learned guess inside a leapfrog integration with the chronological guess:
-  // consecutive rejections of the net's correction, and whether the last solve tried it
+  // consecutive tries that did not halve the residual, and whether the last solve tried it
   int net_adaptive = 0, net_rejects = 0, net_tried = 0;
   // chronological initial guess of leapfrog solves (hqmc_set_guess_history): the
   // last guess_k solutions of the current integration and an orthonormal basis
@@ -721,9 +721,13 @@ bool hermitian_solve(int k, std::vector<double>& A, std::vector<double>& b) {
 // HQMC_SOLVER_LEARNED: x <- x + K(theta)(phi - O x) from the attached net, kept
 // only if it lowers the FP64 residual, then the mixed solver (plain CG with its
 // FP64 true residual stays the judge and the fallback).
-// After this many consecutive rejections within one leapfrog integration that has
-// the chronological guess, the learned guess is not tried again in that integration.
+// Within one leapfrog integration that has the chronological guess, the learned
+// guess is not tried again after kNetMaxRejects consecutive tries that did not cut
+// the residual norm at least in half (||r1||^2 >= kNetGainMin ||r0||^2).  A net apply
+// costs about as much as eight CG iterations at L = 66, and CG takes about 28
+// iterations per decade of residual there, so a try pays only above a 2x cut.
 constexpr int kNetMaxRejects = 2;
+constexpr double kNetGainMin = 0.25;
 
 int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxit, int solver,
           hqmc_solve_info* info, cudaStream_t s) {
@@ -734,7 +738,8 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
   if (solver_base(solver) == HQMC_SOLVER_LEARNED) {
     if (!solver_fcg(solver)) solver = pc ? HQMC_SOLVER_PMIXED : HQMC_SOLVER_MIXED;
     // Inside a leapfrog integration with the chronological guess, the net is not
-    // tried again after kNetMaxRejects consecutive rejections (reset per integration).
+    // tried again after kNetMaxRejects consecutive tries below the 2x cut (reset per
+    // integration).
     if (!(cfg->net_adaptive && cfg->net_rejects >= kNetMaxRejects)) {
       // candidate x + z with z = K r0, r0 = phi - O x.  Both residual norms come from
       // the FP32 fused apply (r1 = r0 - O z): they only decide whether z is kept, and
@@ -759,7 +764,7 @@ int solve(hqmc_config* cfg, const double2* phi, double2* x, double tol, int maxi
         net_used = 1;
         LK(1, launch_kick(2 * cfg->n, (double*)x, (const double*)cfg->p64[1], 1.0, s));  // x += z
       }
-      cfg->net_rejects = net_used ? 0 : cfg->net_rejects + 1;
+      cfg->net_rejects = (cfg->report_h[1] < kNetGainMin * cfg->report_h[0]) ? 0 : cfg->net_rejects + 1;
     }
   }
   const bool started = false;

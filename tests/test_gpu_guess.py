@@ -81,8 +81,8 @@ def test_guess_history_arguments(hq):
 def test_learned_guess_gives_way_to_the_chronological_guess(hq):
     """A net equal to minus the identity is rejected on every solve (||r0 - O z|| =
     ||r0 + O r0|| > ||r0||).  With the chronological guess the learned solver stops
-    trying it after two consecutive rejections in an integration; without it, it tries
-    every solve.  Either way the trajectory is the oracle's."""
+    trying it after two consecutive tries that do not halve the residual; without it,
+    it tries every solve.  Either way the trajectory is the oracle's."""
     from oracle import net as onet
     L, N, nsteps, dt = 8, 16, 6, 0.02
     lat = oracle.Lattice(L, N)
