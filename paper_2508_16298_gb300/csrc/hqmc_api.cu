@@ -300,11 +300,14 @@ int residual(hqmc_config* cfg, const double2* b, const double2* x, void* r_out, 
   a.part_out = cfg->part_resid;
   a.st = cfg->st;
   a.gate = gate;
+  // the autotuned FP64 shape where it is the generic kernel (the residual mode
+  // exists only there), else the default generic shape
+  const SliceLaunch& rs = (cfg->fused64.nby == 0 && cfg->fused64.mb == cfg->sl.mb) ? cfg->fused64 : cfg->sl;
   int slot;
   RET(timer_begin(cfg, HQMC_TIMER_MDAGM, s, &slot));
-  LK(1, (launch_mdagm<double, MODE_RESID>(cfg->sl, a, s)));
+  LK(1, (launch_mdagm<double, MODE_RESID>(rs, a, s)));
   RET(timer_end(cfg, HQMC_TIMER_MDAGM, s, slot));
-  LK(1, launch_resid_finalize(cfg->part_resid, cfg->sl.grid, fin_mode, tol, maxit, cfg->part_ew, cfg->n_part_ew,
+  LK(1, launch_resid_finalize(cfg->part_resid, rs.grid, fin_mode, tol, maxit, cfg->part_ew, cfg->n_part_ew,
                            cfg->st, cfg->report, gate, s));
   return HQMC_OK;
 }
