@@ -142,6 +142,26 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
     ok = ok && mbar_wait_bounded(&bar, parity);
     parity ^= 1;
     if (ok) {
+      if (MODE == MODE_CGDIR && (!first || j + 1 < te)) {
+        // p = r + beta p_old of slice j + 1, formed once in place in the stage in
+        // slice order (16-byte, conflict-free), and written out where this block
+        // owns the slice; the strip copies below then read p from the stage
+        float4* pn = reinterpret_cast<float4*>(p_new + (size_t)wrap(j + 1) * V);
+        float4* r4 = reinterpret_cast<float4*>(Sv0);
+        const float4* o4 = reinterpret_cast<const float4*>(Sv1);
+        for (int e = threadIdx.x; e < (V >> 1); e += blockDim.x) {
+          float4 v = r4[e];
+          if (!first) {
+            const float4 o = o4[e];
+            v = make_float4(fmaf(beta, o.x, v.x), fmaf(beta, o.y, v.y), fmaf(beta, o.z, v.z), fmaf(beta, o.w, v.w));
+            r4[e] = v;
+          }
+          if (j + 1 < te) pn[e] = v;
+        }
+      }
+    }
+    if (MODE == MODE_CGDIR) __syncthreads();  // p complete in the stage
+    if (ok) {
       load_strip_links_smem<NBY>(sg, Sth, t1, t2, lk);
 #pragma unroll
       for (int r = 0; r < H; ++r) {
@@ -149,24 +169,7 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int s = y * L + (c ? sg.x1 : sg.x0);
-          T xv = Sv0[s];
-          if (MODE == MODE_CGDIR && !first) xv = caxpy(xv, beta, Sv1[s]);
-          X1[(2 * r + c) * blockDim.x + threadIdx.x] = xv;
-        }
-      }
-      if (MODE == MODE_CGDIR && j + 1 < te) {
-        // p of the slice this block owns, written from the stage in slice order:
-        // contiguous 16-byte stores (the same arithmetic as the strip copies above)
-        float4* pn = reinterpret_cast<float4*>(p_new + (size_t)wrap(j + 1) * V);
-        const float4* r4 = reinterpret_cast<const float4*>(Sv0);
-        const float4* o4 = reinterpret_cast<const float4*>(Sv1);
-        for (int e = threadIdx.x; e < (V >> 1); e += blockDim.x) {
-          float4 v = r4[e];
-          if (!first) {
-            const float4 o = o4[e];
-            v = make_float4(fmaf(beta, o.x, v.x), fmaf(beta, o.y, v.y), fmaf(beta, o.z, v.z), fmaf(beta, o.w, v.w));
-          }
-          pn[e] = v;
+          X1[(2 * r + c) * blockDim.x + threadIdx.x] = Sv0[s];
         }
       }
     }
