@@ -138,40 +138,41 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
 
   uint32_t parity = 0;
   bool ok = true;
+  // The stage is copied out cooperatively in slice order: thread (jj, i) of the
+  // Lh x S block takes the 16-byte pair of columns (2i, 2i+1) in rows jj + m S
+  // (m < H), conflict-free, and writes each site into the X1 slot of its owner:
+  // column 2i is column x1 of thread i - 1 (of thread Lh - 1 for i = 0), column
+  // 2i + 1 is column x0 of thread i, and row y is D row r of strip jo with
+  // y - 1 = jo H + r (mod L).  In CG-direction mode the pass forms p = r + beta p_old
+  // and writes p_new for the block's own slices.
   for (int j = tb - 1; j < te; ++j) {
     ok = ok && mbar_wait_bounded(&bar, parity);
     parity ^= 1;
+    __syncthreads();  // every thread has read its X1 slots of the previous step
     if (ok) {
-      if (MODE == MODE_CGDIR && (!first || j + 1 < te)) {
-        // p = r + beta p_old of slice j + 1, formed once in place in the stage in
-        // slice order (16-byte, conflict-free), and written out where this block
-        // owns the slice; the strip copies below then read p from the stage
-        float4* pn = reinterpret_cast<float4*>(p_new + (size_t)wrap(j + 1) * V);
-        float4* r4 = reinterpret_cast<float4*>(Sv0);
-        const float4* o4 = reinterpret_cast<const float4*>(Sv1);
-        for (int e = threadIdx.x; e < (V >> 1); e += blockDim.x) {
-          float4 v = r4[e];
+      float4* pn = reinterpret_cast<float4*>(p_new + (size_t)wrap(j + 1) * V);
+      const float4* r4 = reinterpret_cast<const float4*>(Sv0);
+      const float4* o4 = reinterpret_cast<const float4*>(Sv1);
+      const bool own = j + 1 < te;
+      const int Lh = sg.Lh, S = L / H, y0 = sg.base / H;  // this thread: column pair sg.i of rows y0 + m S
+#pragma unroll 1
+      for (int m = 0; m < H; ++m) {
+        const int y = y0 + m * S;
+        const int e = y * Lh + sg.i;
+        float4 v = r4[e];
+        if (MODE == MODE_CGDIR) {
           if (!first) {
             const float4 o = o4[e];
             v = make_float4(fmaf(beta, o.x, v.x), fmaf(beta, o.y, v.y), fmaf(beta, o.z, v.z), fmaf(beta, o.w, v.w));
-            r4[e] = v;
           }
-          if (j + 1 < te) pn[e] = v;
+          if (own) pn[e] = v;
         }
+        const int yp = (y == 0) ? L - 1 : y - 1;
+        const int jo = yp / H, r = yp - jo * H;
+        X1[(2 * r + 1) * blockDim.x + jo * Lh + sg.il] = make_float2(v.x, v.y);  // column 2i
+        X1[(2 * r) * blockDim.x + jo * Lh + sg.i] = make_float2(v.z, v.w);       // column 2i + 1
       }
-    }
-    if (MODE == MODE_CGDIR) __syncthreads();  // p complete in the stage
-    if (ok) {
       load_strip_links_smem<NBY>(sg, Sth, t1, t2, lk);
-#pragma unroll
-      for (int r = 0; r < H; ++r) {
-        const int y = drow(sg, r, H);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int s = y * L + (c ? sg.x1 : sg.x0);
-          X1[(2 * r + c) * blockDim.x + threadIdx.x] = Sv0[s];
-        }
-      }
     }
     if (!__syncthreads_and(ok)) {  // uniform: every thread leaves together
       ok = false;
