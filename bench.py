@@ -95,7 +95,7 @@ MDAGM_BYTES_PER_SITE = {"cg64": 96, "pcg64": 96, "mixed": 40, "learned": 40, "pm
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu capture of the τ-walking
 # FP32 kernel at L = 66 (cold caches; writes still in L2 at the kernel's end are not counted there).
 # Valid for the kernel as captured; set to None when the kernel changes.
-NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 79.156736e6 + 9.892608e6}
+NCU_TRAFFIC_BYTES = {"hmc_learned_fp32_L66_Nt660": 79.50208e6 + 9.959936e6}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
