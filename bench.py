@@ -208,6 +208,7 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
     t_traj = its_per_traj * t_iter + (wl["nsteps"] + 1) * t_force
     kind = "preconditioned CG" if pc else "CG"
     return {"traj_s": t_traj, "t_iter_s": t_iter, "t_force_s": t_force, "cores": oracle.num_threads(),
+            "sample_s": t2 - t0,
             "sample": f"{it} oracle {kind} iterations + 1 force at L={wl['L']}, Ntau={wl['Ntau']}, "
                       f"scaled to {its_per_traj:.0f} iterations and {wl['nsteps'] + 1} forces per trajectory"}
 
@@ -216,7 +217,7 @@ def oracle_sample(wl: dict, its_per_traj: float, theta, phi, max_iters: int = 10
 # available (the reference arm); measured on the GPU with the same algorithm.
 ITS_PER_TRAJ_HINT = {"hmc_fp64_L24_Nt240": 11000.0, "hmc_fp64_L8_Nt40": 6000.0, "hmc_mixed_L48_Nt480": 16500.0,
                      "batched_32chains_L12-24": 11000.0, "batched_32chains_L12-24_pcg64": 1800.0,
-                     "hmc_learned_fp32_L66_Nt660": 2640.0,
+                     "hmc_learned_fp32_L66_Nt660": 2950.0,
                      "estimate_L66_Nt660_40rv": 250.0}
 # oracle CG iterations per bounded sample (the largest lattices take about a second per iteration on the host)
 ORACLE_SAMPLE_ITERS = {"hmc_learned_fp32_L66_Nt660": 4, "hmc_mixed_L48_Nt480": 6, "estimate_L66_Nt660_40rv": 4}
@@ -244,8 +245,14 @@ def run_reference(args, wl_name, wl, rank, world):
     samples = [oracle_sample(wl, its, theta, phi, max_iters=n_it) for _ in range(args.steps)]
     t = statistics.median(s["traj_s"] for s in samples)
     value = 1.0 / t
+    # a step is one bounded sample: ms_per_step is its wall time, and the rate is the
+    # fraction of a trajectory it covers over that time (= 1 / extrapolated seconds per trajectory)
+    sample_s = statistics.median(s["sample_s"] for s in samples)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample_s,
+            "work_per_step": {"fraction_of_unit": sample_s / t, "extrapolated_s_per_unit": t,
+                              "value": "fraction_of_unit / (ms_per_step / 1000)"},
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(wl_name, WORKLOADS[wl_name]),
             "cpu_baseline": {"value": value, "unit": unit, "cores": samples[0]["cores"], "kind": "oracle",
@@ -270,9 +277,11 @@ SOLVER_TEXT = {
     "pcg64": "pcg64: FP64 CG preconditioned with the tau-line preconditioner",
     "mixed": "mixed: FP32 M^dagger M in CG, FP64 reliable updates every 50 iterations",
     "pmixed": "pmixed: the mixed solver preconditioned with the tau-line preconditioner (FP32)",
-    "learned": "learned: net-corrected initial guess (kept if its FP64 residual is below the FP32 residual of the guess it corrects), then the mixed solver",
-    "plearned": "plearned: net-corrected initial guess (kept if its FP64 residual is below the FP32 residual of the guess it corrects), then the mixed "
-                "solver preconditioned with the tau-line preconditioner (FP32)",
+    "learned": "learned: net-corrected initial guess (kept if it lowers the FP32 residual norm; with the chronological guess "
+               "tried until two tries in an integration fail to halve it), then the mixed solver",
+    "plearned": "plearned: net-corrected initial guess (kept if it lowers the FP32 residual norm; with the chronological guess "
+                "tried until two tries in an integration fail to halve it), then the mixed solver preconditioned with the "
+                "tau-line preconditioner (FP32)",
     "flearned": "flearned: net-corrected initial guess, then flexible CG (Polak-Ribiere beta) with the net as preconditioner "
                 "every iteration, FP32 recurrence with FP64 reliable updates, tau-line pmixed as the fallback",
 }
