@@ -74,5 +74,26 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     assert capsys.readouterr().out == ""
 
 
+def test_reference_line_is_consistent_with_its_own_clock(capsys):
+    """ms_per_step is the wall time of one bounded oracle sample, and value is the
+    fraction of a trajectory that sample covers over that time."""
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+
+    class Args:
+        steps, warmup, gpus = 2, 1, 1
+
+    name = "hmc_fp64_L8_Nt40"
+    bench.run_reference(Args(), name, bench.WORKLOADS[name], rank=0, world=1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    w = line["work_per_step"]
+    assert line["impl"] == "reference" and line["unit"] == "traj/s"
+    assert 0 < w["fraction_of_unit"] < 1
+    assert abs(line["value"] - w["fraction_of_unit"] / (line["ms_per_step"] / 1e3)) <= 1e-9 * line["value"]
+    assert abs(line["value"] * w["extrapolated_s_per_unit"] - 1.0) < 1e-12
+
+
 if __name__ == "__main__":
     sys.exit(pytest.main([__file__, "-q"]))
