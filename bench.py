@@ -557,6 +557,11 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     n_md, md_ms = hqmc.get_timing(cfg, hqmc.TIMER_MDAGM32 if fp32 else hqmc.TIMER_MDAGM)
     n_up, up_ms = hqmc.get_timing(cfg, hqmc.TIMER_CG_UPDATE)
     n_pc, pc_ms = hqmc.get_timing(cfg, hqmc.TIMER_PRECOND)
+    # per-launch times: a loop body's launches after its solve converged exit at once, so
+    # the median (not the mean) is the time of a launch that does the work
+    md_us = hqmc.get_timing_samples(cfg, hqmc.TIMER_MDAGM32 if fp32 else hqmc.TIMER_MDAGM)
+    up_us = hqmc.get_timing_samples(cfg, hqmc.TIMER_CG_UPDATE)
+    pc_us = hqmc.get_timing_samples(cfg, hqmc.TIMER_PRECOND)
     hqmc.set_timing(cfg, False)
     total_ms = max_over_ranks(total_ms, world, dev)
     value = job_rate(args.steps, world, total_ms / 1e3)
@@ -632,8 +637,11 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
     its = [i["cg_iterations"] for i in infos]
     its_per_traj = statistics.mean(its)
     md_avg_ms = md_ms / max(n_md, 1)
-    achieved_tflops = MDAGM_FLOPS_PER_SITE * sites / (md_avg_ms * 1e-3) / 1e12
-    achieved_gbs = MDAGM_BYTES_PER_SITE[wl["solver"]] * sites / (md_avg_ms * 1e-3) / 1e9
+    md_med_ms = statistics.median(md_us) / 1e3 if md_us else md_avg_ms
+    achieved_tflops = MDAGM_FLOPS_PER_SITE * sites / (md_med_ms * 1e-3) / 1e12
+    achieved_gbs = MDAGM_BYTES_PER_SITE[wl["solver"]] * sites / (md_med_ms * 1e-3) / 1e9
+    med_up = statistics.median(up_us) if up_us else None
+    med_pc = statistics.median(pc_us) if pc_us else None
     shape = cfg.launch_shape(hqmc.FP32 if fp32 else hqmc.FP64)
     kname = kernel_name(shape, "float" if fp32 else "double")
     if fp32:  # the FP32 fused kernel is bounded by HBM bandwidth
@@ -643,9 +651,11 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
                     "traffic_note": "DRAM read + write bytes per launch, ncu (profiles/)" if traffic else None,
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "bytes_per_site": MDAGM_BYTES_PER_SITE[wl["solver"]], "sites_per_launch": sites,
-                    "tflops_algorithmic": achieved_tflops, "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms,
-                    "cg_update_avg_us": 1e3 * up_ms / max(n_up, 1),
-                    "precond_avg_us": 1e3 * pc_ms / n_pc if n_pc else None,
+                    "tflops_algorithmic": achieved_tflops, "launches": n_md,
+                    "median_launch_us": 1e3 * md_med_ms, "mean_launch_us_all": 1e3 * md_avg_ms,
+                    "launch_time": "median of the per-launch CUDA-event times over one trajectory (launches after "
+                                   "a solve converged exit at once; the mean over all launches counts them)",
+                    "cg_update_median_us": med_up, "precond_median_us": med_pc,
                     "precond_shape": hqmc.get_precond_shape(cfg, hqmc.FP32)}
     else:
         roofline = {"kernel": kname, "bound": "alu", "achieved": achieved_tflops,
@@ -654,8 +664,8 @@ def run_ours(args, wl_name, wl, rank, world, local_rank):
                     "peak_note": "FP64 FMA rate measured on this GPU by hqmc_probe_fp64_rate",
                     "flops_per_site": MDAGM_FLOPS_PER_SITE, "sites_per_launch": sites,
                     "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / hbm,
-                    "launches": n_md, "avg_launch_us": 1e3 * md_avg_ms, "cg_update_avg_us": 1e3 * up_ms / max(n_up, 1),
-                    "precond_avg_us": 1e3 * pc_ms / n_pc if n_pc else None}
+                    "launches": n_md, "median_launch_us": 1e3 * md_med_ms, "mean_launch_us_all": 1e3 * md_avg_ms,
+                    "cg_update_median_us": med_up, "precond_median_us": med_pc}
 
     # ---- oracle on the host cores: bounded sample --------------------------
     import oracle
@@ -840,6 +850,61 @@ def run_estimate(args, wl_name, wl, rank, world, local_rank):
                  "speedup_over_sequential": (sum(ms) / sum(pms)),
                  "estimate_g": [[round(g.real, 6), round(g.imag, 6)] for g in pgs],
                  "method": "each solve starts from the Galerkin projection onto the earlier solutions of the set"}
+    # the same vectors with the systems solved together (hqmc_estimate_multi): per CG iteration one
+    # tau-walking M^dagger M launch, one update launch and one preconditioner launch for all nrv systems
+    hqmc.set_multi_rhs(cfg, nrv)
+    shape = hqmc.multi_launch_shape(cfg, nrv)
+    for k in range(args.warmup):
+        hqmc.estimate(cfg, theta, nrv, seed=seed, counter=nrv * k, tol=wl["tol"], solver=wl["solver"], together=True)
+    torch.cuda.synchronize()
+    tms, tits, tgs = [], [], []
+    l1 = cfg.launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g, infos, _, _ = hqmc.estimate(cfg, theta, nrv, seed=seed, counter=nrv * (args.warmup + k), tol=wl["tol"],
+                                       solver=wl["solver"], together=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tms.append(a.elapsed_time(b))
+        tgs.append(g)
+        tits.append(sum(i["iterations"] for i in infos))
+    # the multi-system walk launch: CUDA events around every launch of one more estimate (host-driven
+    # loop bodies); the median per-launch time (launches after every system converged exit at once)
+    hqmc.set_timing(cfg, True)
+    hqmc.estimate(cfg, theta, nrv, seed=seed, counter=nrv * (args.warmup + args.steps), tol=wl["tol"],
+                  solver=wl["solver"], together=True)
+    w_us = hqmc.get_timing_samples(cfg, hqmc.TIMER_MDAGM32)
+    u_us = hqmc.get_timing_samples(cfg, hqmc.TIMER_CG_UPDATE)
+    p_us = hqmc.get_timing_samples(cfg, hqmc.TIMER_PRECOND)
+    hqmc.set_timing(cfg, False)
+    sites = L * L * N
+    w_med = statistics.median(w_us)
+    w_bytes = (32 * nrv + 8) * sites  # per system r/z, p_old, p_new, q (8 B each); theta as float once
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    w_gbs = w_bytes / (w_med * 1e-6) / 1e9
+    roofline = {"kernel": "hqmc::mdagm_walk_kernel<2, nby, multi> (FP32 M†M, CG direction, %d systems)" % nrv,
+                "bound": "hbm", "achieved": w_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": w_gbs / hbm if hbm else None, "traffic": None,
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_launch": w_bytes, "bytes_note": "(32 nrv + 8) B per site: per system r or z, p_old, "
+                "p_new, q in FP32 complex; theta as float once for all systems",
+                "median_launch_us": w_med, "launches": len(w_us),
+                "per_system_us": w_med / nrv,
+                "cg_update_median_us": statistics.median(u_us) if u_us else None,
+                "precond_median_us": statistics.median(p_us) if p_us else None}
+    together = {"vectors_per_s": args.steps * nrv / (sum(tms) / 1e3),
+                "iterations_per_vector": statistics.mean(tits) / nrv,
+                "speedup_over_sequential": sum(ms) / sum(tms), "ms_per_step": sum(tms) / args.steps,
+                "gpu_launches": int(cfg.launch_count() - l1),
+                "walk_launch": shape,
+                "estimate_g": [[round(g.real, 6), round(g.imag, 6)] for g in tgs],
+                "step_ms": [round(m, 3) for m in tms],
+                "method": "the nrv systems advance together from X = 0: one tau-walking M^dagger M launch "
+                          "(CTA b: system b % nrv, slice range b / nrv), one update and one preconditioner "
+                          "launch per CG iteration for all systems, one FP64 reliable-update launch per 50"}
+    hqmc.set_multi_rhs(cfg, 0)
     line = {"metric": METRIC, "value": value, "unit": "random vectors/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -854,18 +919,23 @@ def run_estimate(args, wl_name, wl, rank, world, local_rank):
             "exact_re_g": 0.5,
             "iterations_per_vector": statistics.mean(its) / nrv,
             "step_ms": [round(m, 3) for m in ms],
-            "projected": projected}
+            "projected": projected,
+            "together": together,
+            "roofline": roofline}
     print(json.dumps(line), flush=True)
 
 
-def run_profile_case(wl):
+def run_profile_case(wl, nrv=None):
     """A short, fixed sequence for ncu captures at the workload's size, with the CG
     loop driven from the host (kernels inside a graph with conditional nodes cannot
     be profiled one by one) and the default launch shapes (an autotuner timed under
     a profiler would not pick the bench's shapes): three fused M^dagger M applies in
     the workload's precision, then one trajectory of 4 leapfrog steps with the
     workload's solver, initial-guess history and first dt (the learned one with a
-    freshly initialised net; its cost does not depend on the weights).  Prints no JSON."""
+    freshly initialised net; its cost does not depend on the weights).  For the
+    estimate workload: one estimate of nrv vectors (default the workload's) with the
+    systems solved together.  Prints no JSON."""
+    nrv = nrv or wl.get("nrv")
     import numpy as np
     import torch
 
@@ -874,6 +944,18 @@ def run_profile_case(wl):
     from paper_2508_16298_gb300 import hqmc, inputs
 
     L, N = wl["L"], wl["Ntau"]
+    if wl.get("estimate"):  # one estimate with the systems solved together, nrv of them
+        with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"]) as cfg:
+            hqmc.set_timing(cfg, True)
+            hqmc.set_multi_rhs(cfg, nrv)
+            theta = torch.from_numpy(start_theta(wl, wl["seed"])).cuda()
+            g, infos, _, _ = hqmc.estimate(cfg, theta, nrv, seed=wl["seed"], tol=wl["tol"], solver=wl["solver"],
+                                           together=True)
+            torch.cuda.synchronize()
+            print("systems:", nrv, "walk launch:", hqmc.multi_launch_shape(cfg, nrv), "iterations per vector:",
+                  sum(i["iterations"] for i in infos) / nrv, file=sys.stderr)
+        print("profile case done", flush=True)
+        return
     with hqmc.Config(L, N, dtau=wl["dtau"], t=wl["t"], J=wl["J"]) as cfg:
         hqmc.set_timing(cfg, True)
         theta = torch.from_numpy(start_theta(wl, wl["seed"])).cuda()
@@ -904,12 +986,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--profile", action="store_true", help="run the short ncu capture case and exit")
+    ap.add_argument("--profile-nrv", type=int, default=0,
+                    help="estimate workload with --profile: vectors of the estimate (default the workload's)")
     ap.add_argument("--train-triples", type=int, default=0,
                     help="learned workloads: train online on this many sampler triples (none stored) "
                          "instead of epochs over the stored set")
     args = ap.parse_args()
     if args.profile:
-        run_profile_case(WORKLOADS[args.workload])
+        run_profile_case(WORKLOADS[args.workload], args.profile_nrv or None)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -308,6 +308,60 @@ HQMC_API int hqmc_estimate_projected(hqmc_config* cfg, const double* theta, uint
                                      int nrv, double tol, int maxit, int solver, void* Gxi, void* xi,
                                      double* g_host, hqmc_solve_info* infos, void* stream);
 
+/* ---- systems solved together on one field ------------------------------
+ * Methods, "Stochastic estimation of fermionic observables": the N_rv systems
+ * (M^dagger M) X_k = R_k of an estimate share theta.  Solved together, one
+ * CG iteration of all of them is one tau-walking M^dagger M launch (CTA b walks
+ * slice range b / nrhs of system b % nrhs, so the CTAs resident together read
+ * the same theta slices, and each walks a longer range than a one-system launch
+ * could give it), one update launch and (PMIXED) one preconditioner launch; each
+ * loop body ends with one FP64 reliable-update launch for all systems.  Every
+ * system keeps its own scalars, CG state and convergence test on its own FP64
+ * true residual. */
+
+/* Allocates the workspace of up to nmax systems on this config (about 96 bytes
+ * per site and system: six FP32 and three FP64 vectors) and their descriptor
+ * tables; nmax = 0 frees it, a smaller nmax keeps the larger workspace.  The only
+ * call of this group that allocates.  Needs the tau-walking FP32 kernel (every
+ * even L that fits one slice per CTA; not with params.variant 1 or 2).
+ * Synchronises the device.  Errors: HQMC_EINVAL (nmax outside [0, 1024]),
+ * HQMC_EUNSUPPORTED (no tau-walking shape), HQMC_ENOMEM. */
+HQMC_API int hqmc_set_multi_rhs(hqmc_config* cfg, int nmax);
+
+/* Solves (M^dagger M) x_k = phi_k for k < nrhs on one theta.  phi and x are
+ * device arrays of nrhs complex double vectors back to back (nrhs x Ntau x L x L);
+ * x holds the guesses on entry and the solutions on exit.  solver is
+ * HQMC_SOLVER_MIXED or HQMC_SOLVER_PMIXED (otherwise HQMC_EUNSUPPORTED).  A system
+ * stops when its FP64 true residual ||phi_k - O x_k|| <= tol ||phi_k||; a system
+ * whose FP32 recurrence breaks down or stalls is finished alone by the solver of
+ * hqmc_cg_solve from its current iterate.  infos (host, nullable) receives nrhs
+ * solve infos.  Needs hqmc_set_multi_rhs(cfg, >= nrhs) (HQMC_EINVAL otherwise).
+ * Returns the first failure of hqmc_cg_solve's kinds over the systems;
+ * synchronises the stream. */
+HQMC_API int hqmc_cg_solve_multi(hqmc_config* cfg, const double* theta, int nrhs, const void* phi, void* x,
+                                 double tol, int maxit, int solver, hqmc_solve_info* infos, void* stream);
+
+/* hqmc_estimate with its systems solved together in groups of up to the
+ * workspace's nmax (hqmc_set_multi_rhs), each from X = 0: the same draws xi_k,
+ * R_k = M^dagger xi_k and estimate; outputs, errors and synchronisation as
+ * hqmc_estimate; solver as hqmc_cg_solve_multi. */
+HQMC_API int hqmc_estimate_multi(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv,
+                                 double tol, int maxit, int solver, void* Gxi, void* xi, double* g_host,
+                                 hqmc_solve_info* infos, void* stream);
+
+/* Fixes the slice ranges per system of the multi-system walk launch (each
+ * system's Ntau slices split into `ranges` contiguous ranges, one CTA each);
+ * 0 restores the default, the ranges with the fewest rounds of sweeps the device
+ * needs: about ceil(nrhs ranges / resident CTAs) x (2 ceil(Ntau / ranges) + 1).
+ * Results do not depend on it beyond FP32 rounding of the partial sums.
+ * HQMC_EINVAL outside [0, Ntau].  Host only. */
+HQMC_API int hqmc_set_multi_ranges(hqmc_config* cfg, int ranges);
+
+/* Launch shape of a multi-system solve of nrhs systems: slice ranges per system
+ * (*ranges), block size and strip height of the tau-walking kernel.
+ * HQMC_EUNSUPPORTED without a tau-walking shape.  Host only. */
+HQMC_API int hqmc_multi_launch_shape(const hqmc_config* cfg, int nrhs, int* ranges, int* threads, int* nby);
+
 /* ---- force (Supplement SI, Eqs. (force&CG) and (fermion_force)) -------- */
 
 /* Given X = (M^dagger M)^{-1} phi (complex double), writes the total force
@@ -525,6 +579,13 @@ HQMC_API int hqmc_set_timing(hqmc_config* cfg, int enable);
 /* Synchronises the device and returns, for one kernel class, the number of
  * timed launches and their summed duration in milliseconds. */
 HQMC_API int hqmc_get_timing(hqmc_config* cfg, int timer, long long* launches, double* total_ms);
+
+/* Synchronises the device and writes the durations (microseconds) of the first
+ * min(max_n, launches) timed launches of one kernel class, in launch order, to
+ * us (host); *n_out (nullable) receives the number of timed launches.  Launches
+ * that found their solve finished (the rest of a loop body after convergence)
+ * are among them: a median over the samples is the time of a launch that works. */
+HQMC_API int hqmc_get_timing_samples(hqmc_config* cfg, int timer, float* us, int max_n, int* n_out);
 
 /* Measures the device's FP64 fused-multiply-add throughput (TFLOP/s, 2 flops
  * per FMA) with a short kernel of independent FMA chains on the default

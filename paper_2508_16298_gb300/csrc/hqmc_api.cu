@@ -31,6 +31,7 @@ struct NvtxRange {
 
 constexpr int kMaxL = 68;             // 3 complex-double slices must fit in 227 KB of shared memory
 constexpr int kBodyIters64 = 16;      // FP64 CG iterations per loop body
+constexpr int kMaxMultiRhs = 1024;  // systems of one multi-system workspace (hqmc_set_multi_rhs)
 constexpr int kDefaultReliable = 50;  // mixed solver residual-update period (iterations per body)
 constexpr int kMaxBreakdowns = 8;     // mixed solver: FP32 breakdown restarts before the FP64 fallback
 constexpr size_t kMaxLineSmem = 227 * 1024;  // tau-line preconditioner tile: opt-in shared memory per block
@@ -51,6 +52,45 @@ struct SolveGraph {
   long long net_version;  // flexible CG: the net weights captured by value in the body
   int body_kernels;  // kernels per body, including the loop-condition kernel
   cudaGraphExec_t exec;
+};
+
+// Systems solved together on one field (hqmc_set_multi_rhs): `cap` systems stored
+// back to back, system k at offset k n of every vector, k pstride of part_w,
+// part_ew and part_rz, k rstride of part_res, 2 k of report.
+struct MultiWs {
+  int cap = 0;
+  int pstride = 0;  // doubles per system: walk partials (<= Ntau), update partials, preconditioner partials
+  int rstride = 0;  // doubles per system of the FP64 residual partials (two sums per slot)
+  int nlt = 0;      // preconditioner tiles per system
+  int ublocks = 0;  // blocks per system of the batched update (= its partials of <r, r>)
+  int rC = 1;       // cluster size (slices per tile) of the batched FP64 residual
+  int rnt = 0;      // FP64 residual tiles per system
+  int rslots = 0;   // FP64 residual partial slots per system (rnt rC)
+  float2 *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *z = nullptr, *xh = nullptr;
+  double2 *eta = nullptr, *xw = nullptr, *xiw = nullptr;  // estimate: R_k, X_k and xi_k when the caller keeps none
+  double *part_w = nullptr, *part_ew = nullptr, *part_rz = nullptr, *part_res = nullptr, *report = nullptr;
+  CgState* st = nullptr;
+  CgState** d_states = nullptr;
+  UpdArgs<float>* d_upd = nullptr;     // per call (n_pq follows the walk launch's ranges)
+  int2* d_ublocks = nullptr;           // (system, block) of the batched update
+  int* d_unblocks = nullptr;
+  LineBatchDesc<float>* d_line = nullptr;
+  int4* d_ltiles = nullptr;            // (system, bx, by) of the batched preconditioner
+  MdagmArgs<double>* d_res = nullptr;  // per call: [0, cap) start residuals, [cap, 2 cap) reliable updates
+  FinArgs* d_fin = nullptr;
+  int2* d_rtiles = nullptr;            // (system, slice) of the FP64 residual
+  CgState* st_h = nullptr;             // pinned mirrors
+  double* report_h = nullptr;
+  void* h_stage = nullptr;             // pinned staging of the per-call descriptors
+  size_t stage_bytes = 0;
+  std::vector<void*> allocs;           // device buffers above (freed when the workspace grows)
+  struct Graph {
+    int nsys, pc, granges;
+    void* x;
+    int body_kernels;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
 };
 
 }  // namespace
@@ -129,6 +169,9 @@ struct hqmc_config {
   int hist_n = 0, hist_next = 0;                                       // stored solutions, next ring slot
   double* net_scal = nullptr;                                          // device scalars (norms)
 
+  MultiWs mw;  // systems solved together on one field (hqmc_set_multi_rhs)
+  int multi_ranges = 0;  // slice ranges per system of their walk launch (0: the launch-time model)
+
   int timing = 0;
   long long launches = 0;  // kernels enqueued by this config
   int capturing = 0;       // inside a stream capture: launches are counted when the graph runs
@@ -196,7 +239,19 @@ int dalloc(hqmc_config* cfg, T** ptr, size_t count) {
   return HQMC_OK;
 }
 
+void multi_release(MultiWs& m) {
+  for (auto& g : m.graphs) cudaGraphExecDestroy(g.exec);
+  m.graphs.clear();
+  for (void* p : m.allocs) cudaFree(p);
+  m.allocs.clear();
+  if (m.st_h) cudaFreeHost(m.st_h);
+  if (m.report_h) cudaFreeHost(m.report_h);
+  if (m.h_stage) cudaFreeHost(m.h_stage);
+  m = MultiWs{};
+}
+
 void release(hqmc_config* cfg) {
+  multi_release(cfg->mw);
   for (void* p : cfg->allocs) cudaFree(p);
   cfg->allocs.clear();
   if (cfg->st_h) cudaFreeHost(cfg->st_h);
@@ -1754,6 +1809,410 @@ int estimate_impl(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Systems solved together on one field (the N_rv right-hand sides of the
+// stochastic estimation, Methods "Stochastic estimation of fermionic
+// observables"): mixed-precision CG of Eq. (pCG) on every system at once, with
+// per iteration one tau-walking M^dagger M launch, one update launch and (PMIXED)
+// one preconditioner launch for all of them, and per loop body the FP64
+// reliable updates of all of them in one launch.  Every system keeps its own
+// scalars, state and convergence test; the systems share theta and its tables.
+
+// The tau-walking shape of a multi-system launch (walk = 0: none).
+SliceLaunch multi_walk_shape(const hqmc_config* cfg) {
+  return cfg->fused32.walk ? cfg->fused32 : cfg->slw32;
+}
+
+// Slice ranges per system of a launch over nsys systems: CTAs of one system walk
+// ranges of about Ntau / G slices at 2 sweeps per slice plus one halo sweep, and
+// the device holds R of them at a time, so the launch takes about
+// ceil(nsys G / R) rounds of (2 ceil(Ntau / G) + 1) sweeps; the G with the fewest
+// (the largest G among equals: more, shorter CTAs balance better) is taken.
+int multi_granges(const hqmc_config* cfg, int nsys) {
+  const SliceLaunch w = multi_walk_shape(cfg);
+  const int N = cfg->p.Ntau;
+  if (cfg->multi_ranges > 0) return std::min(cfg->multi_ranges, N);
+  const long long R = (long long)std::max(1, cfg->num_sms) * std::max(1, mdagm_walk_multi_blocks_per_sm(w));
+  long long best = -1;
+  int bestG = 1;
+  for (int G = 1; G <= N; ++G) {
+    const long long rounds = ((long long)nsys * G + R - 1) / R;
+    const long long cost = rounds * (2LL * ((N + G - 1) / G) + 1);
+    if (best < 0 || cost <= best) {
+      best = cost;
+      bestG = G;
+    }
+  }
+  return bestG;
+}
+
+// Shared memory of the systems' FP64 residual (the batched generic kernel: links
+// from the FP64 table, clusters of consecutive slices).
+size_t multi_res_smem(const hqmc_config* cfg) { return (size_t)3 * cfg->g.V * sizeof(double2); }
+
+template <class T>
+int mdalloc(hqmc_config* cfg, T** ptr, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(cfg, HQMC_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  cfg->mw.allocs.push_back(p);
+  *ptr = (T*)p;
+  return HQMC_OK;
+}
+
+// Allocates the workspace of `cap` systems and the descriptor tables that do not
+// depend on the operands of a call.
+int multi_setup(hqmc_config* cfg, int cap) {
+  MultiWs& m = cfg->mw;
+  const size_t n = (size_t)cfg->n;
+  const int N = cfg->p.Ntau;
+  const LineLaunch& ll = cfg->ll32;
+  m.cap = cap;
+  // update: about two resident waves of 256-thread blocks over all systems, so each
+  // block streams enough of its vector to hide the latency of its head (state and
+  // partial sums); at most the one-system grid
+  m.ublocks = (int)std::max(8LL, std::min((long long)cfg->ew_grid, (2LL * cfg->num_sms * 8 + cap - 1) / cap));
+  m.pstride = std::max(N, std::max(m.ublocks, ll.gx * ll.gy));
+  m.nlt = ll.gx * ll.gy;
+  // FP64 residual: the cluster size of the one-system residual where the batched
+  // generic kernel can co-schedule it (a cluster of C slices does 2C + 1 sweeps)
+  {
+    const SliceLaunch& rs = (cfg->fused64.nby == 0 && cfg->fused64.mb == cfg->sl.mb) ? cfg->fused64 : cfg->sl;
+    m.rC = std::max(1, std::min(rs.cluster, N));
+    if (m.rC > 1 && mdagm_batch_max_active_clusters(m.rC, cfg->sl.threads, multi_res_smem(cfg)) <= 0) m.rC = 1;
+    m.rnt = (N + m.rC - 1) / m.rC;
+    m.rslots = m.rnt * m.rC;
+    m.rstride = 2 * m.rslots;
+  }
+  const size_t vc = (size_t)cap * n;
+  RET(mdalloc(cfg, &m.r, vc));
+  RET(mdalloc(cfg, &m.p0, vc));
+  RET(mdalloc(cfg, &m.p1, vc));
+  RET(mdalloc(cfg, &m.q, vc));
+  RET(mdalloc(cfg, &m.z, vc));
+  RET(mdalloc(cfg, &m.xh, vc));
+  RET(mdalloc(cfg, &m.eta, vc));
+  RET(mdalloc(cfg, &m.xw, vc));
+  RET(mdalloc(cfg, &m.xiw, vc));
+  RET(mdalloc(cfg, &m.part_w, (size_t)cap * m.pstride));
+  RET(mdalloc(cfg, &m.part_ew, (size_t)cap * m.pstride));
+  RET(mdalloc(cfg, &m.part_rz, (size_t)cap * m.pstride));
+  RET(mdalloc(cfg, &m.part_res, (size_t)cap * m.rstride));
+  RET(mdalloc(cfg, &m.report, 2 * (size_t)cap));
+  RET(mdalloc(cfg, &m.st, (size_t)cap));
+  RET(mdalloc(cfg, &m.d_states, (size_t)cap));
+  RET(mdalloc(cfg, &m.d_upd, (size_t)cap));
+  RET(mdalloc(cfg, &m.d_ublocks, (size_t)cap * m.ublocks));
+  RET(mdalloc(cfg, &m.d_unblocks, (size_t)cap));
+  RET(mdalloc(cfg, &m.d_line, (size_t)cap));
+  RET(mdalloc(cfg, &m.d_ltiles, (size_t)cap * m.nlt));
+  RET(mdalloc(cfg, &m.d_res, 2 * (size_t)cap));
+  RET(mdalloc(cfg, &m.d_fin, (size_t)cap));
+  RET(mdalloc(cfg, &m.d_rtiles, (size_t)cap * m.rnt));
+  CK(cudaMallocHost((void**)&m.st_h, (size_t)cap * sizeof(CgState)));
+  CK(cudaMallocHost((void**)&m.report_h, 2 * (size_t)cap * sizeof(double)));
+  m.stage_bytes = (size_t)cap * (2 * sizeof(MdagmArgs<double>) + sizeof(FinArgs) + sizeof(UpdArgs<float>));
+  CK(cudaMallocHost(&m.h_stage, m.stage_bytes));
+  CK(cudaMemset(m.st, 0, (size_t)cap * sizeof(CgState)));
+  CK(cudaMemset(m.part_w, 0, (size_t)cap * m.pstride * sizeof(double)));
+  CK(cudaMemset(m.part_ew, 0, (size_t)cap * m.pstride * sizeof(double)));
+  CK(cudaMemset(m.part_rz, 0, (size_t)cap * m.pstride * sizeof(double)));
+  // fixed tables, system-major (the first nsys systems' entries are a prefix)
+  std::vector<CgState*> states(cap);
+  std::vector<int2> ublocks, rtiles;
+  std::vector<int> unblocks(cap, m.ublocks);
+  std::vector<LineBatchDesc<float>> line(cap);
+  std::vector<int4> ltiles;
+  for (int k = 0; k < cap; ++k) {
+    states[k] = m.st + k;
+    for (int j = 0; j < m.ublocks; ++j) ublocks.push_back(make_int2(k, j));
+    for (int t = 0; t < N; t += m.rC) rtiles.push_back(make_int2(k, t));
+    line[k] = LineBatchDesc<float>{cfg->g, cfg->lc, m.r + k * n, m.z + k * n, m.part_rz + (size_t)k * m.pstride,
+                                   m.st + k, ll.gx, ll.chunk};
+    for (int by = 0; by < ll.gy; ++by)
+      for (int bx = 0; bx < ll.gx; ++bx) ltiles.push_back(make_int4(k, bx, by, 0));
+  }
+  CK(cudaMemcpy(m.d_states, states.data(), cap * sizeof(CgState*), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m.d_ublocks, ublocks.data(), ublocks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m.d_unblocks, unblocks.data(), cap * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m.d_line, line.data(), cap * sizeof(LineBatchDesc<float>), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m.d_ltiles, ltiles.data(), ltiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m.d_rtiles, rtiles.data(), rtiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  if (prepare_mdagm_walk_multi(multi_walk_shape(cfg)) != cudaSuccess ||
+      prepare_line_precond_batch32(cfg->lc.W, ll.chunk) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(cfg, HQMC_EUNSUPPORTED, "cannot configure the multi-system kernels for L=%d", cfg->p.L);
+  }
+  return HQMC_OK;
+}
+
+// One loop body over nsys systems: `reliable` mixed iterations, then the FP64
+// reliable update of every active system and (PMIXED) its preconditioned residual.
+int multi_body(hqmc_config* cfg, int nsys, bool pc, const SliceLaunch& wl, double2* x, cudaStream_t s, int* nk) {
+  MultiWs& m = cfg->mw;
+  MdagmArgs<float> a = mdagm_args<float, MODE_CGDIR>(cfg);
+  a.U = cfg->U32;
+  a.y = m.q;
+  a.r = pc ? m.z : m.r;
+  a.pbuf[0] = m.p0;
+  a.pbuf[1] = m.p1;
+  a.part_in = m.part_ew;
+  a.n_part_in = m.ublocks;
+  if (pc) {
+    a.part_rz = m.part_rz;
+    a.n_part_rz = m.nlt;
+  }
+  a.part_out = m.part_w;
+  a.st = m.st;
+  const MultiStride ms{nsys, cfg->n, m.pstride};
+  const int iters = cfg->reliable;
+  int slot;
+  for (int c = 0; c < iters; ++c) {
+    RET(timer_begin(cfg, HQMC_TIMER_MDAGM32, s, &slot));
+    CK(launch_mdagm_walk_multi(wl, a, ms, s));
+    RET(timer_end(cfg, HQMC_TIMER_MDAGM32, s, slot));
+    RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
+    CK(launch_cg_update_batch32(m.d_upd, m.d_ublocks, m.d_unblocks, nsys * m.ublocks, s));
+    RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
+    if (pc) {
+      RET(timer_begin(cfg, HQMC_TIMER_PRECOND, s, &slot));
+      CK(launch_line_precond_batch(m.d_line, m.d_ltiles, nsys * m.nlt, cfg->lc.W, cfg->ll32.chunk, s));
+      RET(timer_end(cfg, HQMC_TIMER_PRECOND, s, slot));
+    }
+  }
+  CK(launch_accumulate_correction_multi(cfg->n, nsys, x, m.xh, m.st, GATE_ACTIVE, s));
+  CK((launch_mdagm_batch<double, MODE_RESID>(m.d_res + m.cap, m.d_rtiles, nsys * m.rnt, m.rC, cfg->sl.threads,
+                                             multi_res_smem(cfg), s)));
+  CK(launch_resid_finalize_batch(m.d_fin, nsys, FIN_RELIABLE, 0.0, 0, GATE_ACTIVE, s));
+  if (pc) CK(launch_line_precond_batch(m.d_line, m.d_ltiles, nsys * m.nlt, cfg->lc.W, cfg->ll32.chunk, s));
+  *nk = (pc ? 3 : 2) * iters + 3 + (pc ? 1 : 0);
+  return HQMC_OK;
+}
+
+// The WHILE-node graph of multi_body for (nsys, solver, ranges, x), built once.
+int multi_graph(hqmc_config* cfg, int nsys, bool pc, const SliceLaunch& wl, double2* x, MultiWs::Graph** out) {
+  MultiWs& m = cfg->mw;
+  for (auto& g : m.graphs)
+    if (g.nsys == nsys && g.pc == (int)pc && g.granges == wl.grid && g.x == x) {
+      *out = &g;
+      return HQMC_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(cfg, HQMC_ECUDA, "conditional graph node: %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(cfg->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cfg->capturing = 1;
+  int nk = 0;
+  int rc = multi_body(cfg, nsys, pc, wl, x, cfg->cap, &nk);
+  if (rc == HQMC_OK) {
+    cudaError_t le = launch_loop_condition_batch(m.d_states, nsys, handle, cfg->cap);
+    if (le != cudaSuccess) rc = fail(cfg, HQMC_ECUDA, "loop condition launch: %s", cudaGetErrorString(le));
+  }
+  cfg->capturing = 0;
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cfg->cap, &captured);
+  if (rc == HQMC_OK && e != cudaSuccess) rc = fail(cfg, HQMC_ECUDA, "end capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  if (rc == HQMC_OK) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) rc = fail(cfg, HQMC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(graph);
+  if (rc != HQMC_OK) {
+    cudaGetLastError();
+    return rc;
+  }
+  if (m.graphs.size() >= 4) {
+    cudaGraphExecDestroy(m.graphs.front().exec);
+    m.graphs.erase(m.graphs.begin());
+  }
+  m.graphs.push_back(MultiWs::Graph{nsys, (int)pc, wl.grid, x, nk + 1, exec});
+  *out = &m.graphs.back();
+  return HQMC_OK;
+}
+
+// Solves (M^dagger M) x_k = phi_k, k < nsys <= cap, on the field whose tables are
+// built (FP64 links and theta as float).  x holds the guesses on entry.  A system
+// the joint loop leaves unconverged (breakdown, stagnation or a non-finite value
+// of its FP32 recurrence) is finished alone by solve() from its current iterate,
+// with that solver's restarts and FP64 fallback.
+int solve_multi(hqmc_config* cfg, int nsys, const double2* phi, double2* x, double tol, int maxit, int solver,
+                hqmc_solve_info* infos, cudaStream_t s) {
+  NvtxRange nv("hqmc multi-system cg solve");
+  MultiWs& m = cfg->mw;
+  const bool pc = solver_pc(solver);
+  const size_t n = (size_t)cfg->n;
+  SliceLaunch wl = multi_walk_shape(cfg);
+  wl.grid = multi_granges(cfg, nsys);
+  // per-call descriptors: FP64 residuals (start, reliable update), their
+  // bookkeeping and the updates (n_pq follows the walk launch's ranges)
+  std::vector<MdagmArgs<double>> res(2 * (size_t)nsys);
+  std::vector<FinArgs> fin(nsys);
+  std::vector<UpdArgs<float>> upd(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    MdagmArgs<double> r = mdagm_args<double, MODE_RESID>(cfg);
+    r.U = cfg->U64;
+    r.x = x + k * n;
+    r.b = phi + k * n;
+    r.r_out = m.r + k * n;
+    r.r_out_fp32 = 1;
+    r.part_out = m.part_res + (size_t)k * m.rstride;
+    r.st = m.st + k;
+    r.teff = cfg->sl.threads;
+    r.gate = GATE_ALWAYS;
+    res[k] = r;
+    r.gate = GATE_ACTIVE;
+    res[nsys + k] = r;
+    fin[k] = FinArgs{m.part_res + (size_t)k * m.rstride, m.rslots, m.part_ew + (size_t)k * m.pstride,
+                     m.ublocks, m.st + k, m.report + 2 * k};
+    upd[k] = UpdArgs<float>{cfg->n,        m.xh + k * n, 0, m.r + k * n, m.p0 + k * n, m.p1 + k * n, m.q + k * n,
+                            m.part_w + (size_t)k * m.pstride, wl.grid, m.part_ew + (size_t)k * m.pstride,
+                            m.st + k};
+  }
+  // staged through pinned memory (the previous call synchronised, so its copies are done)
+  char* hs = (char*)m.h_stage;
+  std::memcpy(hs, res.data(), 2 * (size_t)nsys * sizeof(MdagmArgs<double>));
+  char* hf = hs + 2 * (size_t)m.cap * sizeof(MdagmArgs<double>);
+  std::memcpy(hf, fin.data(), nsys * sizeof(FinArgs));
+  char* hu = hf + (size_t)m.cap * sizeof(FinArgs);
+  std::memcpy(hu, upd.data(), nsys * sizeof(UpdArgs<float>));
+  CK(cudaMemcpyAsync(m.d_res, hs, nsys * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m.d_res + m.cap, hs + nsys * sizeof(MdagmArgs<double>), nsys * sizeof(MdagmArgs<double>),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m.d_fin, hf, nsys * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m.d_upd, hu, nsys * sizeof(UpdArgs<float>), cudaMemcpyHostToDevice, s));
+  // start: r_k = phi_k - O x_k in FP64 (stored as float), states, corrections zero, z_k
+  LK(1, (launch_mdagm_batch<double, MODE_RESID>(m.d_res, m.d_rtiles, nsys * m.rnt, m.rC, cfg->sl.threads,
+                                                multi_res_smem(cfg), s)));
+  LK(1, launch_resid_finalize_batch(m.d_fin, nsys, FIN_START, tol, maxit, GATE_ALWAYS, s));
+  CK(cudaMemsetAsync(m.xh, 0, (size_t)nsys * n * sizeof(float2), s));
+  if (pc) LK(1, launch_line_precond_batch(m.d_line, m.d_ltiles, nsys * m.nlt, cfg->lc.W, cfg->ll32.chunk, s));
+  auto read_states = [&]() -> int {
+    CK(cudaMemcpyAsync(m.st_h, m.st, nsys * sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(m.report_h, m.report, 2 * (size_t)nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HQMC_OK;
+  };
+  if (!cfg->timing) {  // the device-side loop
+    MultiWs::Graph* gr = nullptr;
+    RET(multi_graph(cfg, nsys, pc, wl, x, &gr));
+    CK(cudaGraphLaunch(gr->exec, s));
+    RET(read_states());
+    cfg->launches += (long long)m.st_h[0].loops * gr->body_kernels;
+  } else {  // event timing around every launch: bodies enqueued from the host
+    const long long cap_bodies = 2LL * maxit / std::max(1, cfg->reliable) + 64;
+    for (long long b = 0;; ++b) {
+      RET(read_states());
+      bool run = false;
+      for (int k = 0; k < nsys; ++k) run = run || m.st_h[k].done == CG_RUNNING || m.st_h[k].done == CG_REC_CONVERGED;
+      if (!run || b >= cap_bodies) break;
+      int nk = 0;
+      RET(multi_body(cfg, nsys, pc, wl, x, s, &nk));
+      cfg->launches += nk;
+    }
+  }
+  int worst = HQMC_OK;
+  for (int k = 0; k < nsys; ++k) {
+    const CgState st = m.st_h[k];
+    hqmc_solve_info inf{};
+    inf.iterations = st.k;
+    inf.reliable_updates = st.n_rel;
+    int status = HQMC_OK;
+    if (st.bb == 0.0) {  // phi_k = 0: the solution is zero whatever the guess
+      CK(cudaMemsetAsync(x + k * n, 0, n * sizeof(double2), s));
+    } else if (st.done == CG_CONVERGED) {
+      inf.true_residual = std::sqrt(m.report_h[2 * k] / st.bb);
+      const double rr_rec = (pc && st.k > st.seg_start) ? st.rr_rec : st.rr[st.k & 1];
+      inf.recursive_residual = std::sqrt(rr_rec / st.bb);
+    } else {
+      // fold in the correction the joint loop left, then finish this system alone
+      LK(1, launch_accumulate_correction(cfg->n, x + k * n, m.xh + k * n, nullptr, GATE_ALWAYS, s));
+      hqmc_solve_info si{};
+      status = solve(cfg, phi + k * n, x + k * n, tol, std::max(0, maxit - st.k), solver, &si, s);
+      if (status != HQMC_OK && status != HQMC_ENOTCONV && status != HQMC_EBREAKDOWN && status != HQMC_ENONFINITE &&
+          status != HQMC_ETIMEOUT)
+        return status;
+      inf = si;
+      inf.iterations += st.k;
+      inf.reliable_updates += st.n_rel;
+      inf.restarts += 1;
+    }
+    inf.status = status;
+    if (status == HQMC_OK && !(inf.true_residual <= tol)) status = inf.status = HQMC_ENOTCONV;
+    if (infos) infos[k] = inf;
+    worst = merge_status(worst, status);
+  }
+  return worst;
+}
+
+int check_multi(hqmc_config* cfg, int nsys, int solver, double tol, int maxit) {
+  if (cfg->mw.cap < 1) return fail(cfg, HQMC_EINVAL, "no multi-system workspace: call hqmc_set_multi_rhs first");
+  if (solver != HQMC_SOLVER_MIXED && solver != HQMC_SOLVER_PMIXED)
+    return fail(cfg, HQMC_EUNSUPPORTED, "systems solved together take HQMC_SOLVER_MIXED or HQMC_SOLVER_PMIXED");
+  if (!(tol > 0) || maxit < 0) return fail(cfg, HQMC_EINVAL, "tol must be > 0 and maxit >= 0");
+  if (nsys < 1) return fail(cfg, HQMC_EINVAL, "at least one system is needed");
+  return HQMC_OK;
+}
+
+// The estimate of hqmc_estimate with its right-hand sides solved in groups of up
+// to cap systems (solve_multi), each from X = 0.  The draws, R_k and the traces
+// are those of hqmc_estimate.
+int estimate_multi(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
+                   int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos,
+                   cudaStream_t s) {
+  NvtxRange nv("hqmc estimate (systems together)");
+  MultiWs& m = cfg->mw;
+  const size_t n = (size_t)cfg->n;
+  RET(links(cfg, theta, true, true, s, false, true));
+  double sum_re = 0.0, sum_im = 0.0;
+  int status = HQMC_OK;
+  for (int g0 = 0; g0 < nrv; g0 += m.cap) {
+    const int ns = std::min(m.cap, nrv - g0);
+    double2* X = Gxi ? (double2*)Gxi + (size_t)g0 * n : m.xw;
+    for (int k = 0; k < ns; ++k) {
+      double2* v = xi ? (double2*)xi + (size_t)(g0 + k) * n : m.xiw + k * n;
+      LK(1, launch_draw_vector(cfg->n, seed, 3u, counter + (uint64_t)(g0 + k), v, s));
+      LK(1, launch_apply_M<double>(cfg->sl1, cfg->cB, cfg->U64, v, m.eta + k * n, 1, s));  // R = M^dagger xi
+    }
+    CK(cudaMemsetAsync(X, 0, (size_t)ns * n * sizeof(double2), s));
+    const int rc = solve_multi(cfg, ns, m.eta, X, tol, maxit, solver, infos ? infos + g0 : nullptr, s);
+    if (rc != HQMC_OK && rc != HQMC_ENOTCONV && rc != HQMC_EBREAKDOWN && rc != HQMC_ENONFINITE) return rc;
+    status = merge_status(status, rc);
+    for (int k = 0; k < ns; ++k) {
+      const double2* v = xi ? (double2*)xi + (size_t)(g0 + k) * n : m.xiw + k * n;
+      LK(2, launch_cdot(cfg->n, v, X + k * n, cfg->act_grid, cfg->part_act, cfg->terms + 4, s));
+      CK(cudaMemcpyAsync(cfg->terms_h + 4, cfg->terms + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      sum_re += cfg->terms_h[4];
+      sum_im += cfg->terms_h[5];
+    }
+  }
+  if (g_host) {
+    const double norm = 1.0 / ((double)nrv * (double)cfg->n);
+    g_host[0] = sum_re * norm;
+    g_host[1] = sum_im * norm;
+  }
+  return status;
+}
+
 int check_estimate(hqmc_config* cfg, const double* theta, int nrv, double tol, int maxit, int solver, void* Gxi,
                    void* xi) {
   if (!aligned16(theta) || (Gxi && !aligned16(Gxi)) || (xi && !aligned16(xi)))
@@ -1786,6 +2245,63 @@ int hqmc_estimate_projected(hqmc_config* cfg, const double* theta, uint64_t seed
   RET(check_estimate(cfg, theta, nrv, tol, maxit, solver, Gxi, xi));
   return estimate_impl(cfg, theta, seed, counter, nrv, tol, maxit, solver, Gxi, xi, g_host, infos, true,
                        (cudaStream_t)stream);
+}
+
+int hqmc_set_multi_rhs(hqmc_config* cfg, int nmax) {
+  if (!cfg) return HQMC_EINVAL;
+  if (nmax < 0 || nmax > kMaxMultiRhs) return fail(cfg, HQMC_EINVAL, "nmax must be in [0, %d]", kMaxMultiRhs);
+  RET(check_device(cfg));
+  if (nmax > 0 && nmax <= cfg->mw.cap) return HQMC_OK;
+  if (nmax > 0 && !multi_walk_shape(cfg).walk)
+    return fail(cfg, HQMC_EUNSUPPORTED, "no tau-walking shape for L=%d (or variant %d)", cfg->p.L, cfg->p.variant);
+  CK(cudaDeviceSynchronize());  // no graph over the old workspace may still run
+  multi_release(cfg->mw);
+  if (nmax == 0) return HQMC_OK;
+  const int rc = multi_setup(cfg, nmax);
+  if (rc != HQMC_OK) multi_release(cfg->mw);
+  return rc;
+}
+
+int hqmc_set_multi_ranges(hqmc_config* cfg, int ranges) {
+  if (!cfg) return HQMC_EINVAL;
+  if (ranges < 0 || ranges > cfg->p.Ntau) return fail(cfg, HQMC_EINVAL, "ranges must be in [0, Ntau]");
+  cfg->multi_ranges = ranges;
+  return HQMC_OK;
+}
+
+int hqmc_multi_launch_shape(const hqmc_config* cfg, int nrhs, int* ranges, int* threads, int* nby) {
+  if (!cfg || nrhs < 1) return HQMC_EINVAL;
+  const SliceLaunch w = multi_walk_shape(cfg);
+  if (!w.walk) return HQMC_EUNSUPPORTED;
+  if (ranges) *ranges = multi_granges(cfg, nrhs);
+  if (threads) *threads = w.threads;
+  if (nby) *nby = w.nby;
+  return HQMC_OK;
+}
+
+int hqmc_cg_solve_multi(hqmc_config* cfg, const double* theta, int nrhs, const void* phi, void* x, double tol,
+                        int maxit, int solver, hqmc_solve_info* infos, void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  if (!aligned16(theta) || !aligned16(phi) || !aligned16(x)) return fail(cfg, HQMC_EINVAL, "NULL or misaligned pointer");
+  RET(check_multi(cfg, nrhs, solver, tol, maxit));
+  if (nrhs > cfg->mw.cap)
+    return fail(cfg, HQMC_EINVAL, "%d systems exceed the %d of hqmc_set_multi_rhs", nrhs, cfg->mw.cap);
+  const size_t vb = (size_t)cfg->n * sizeof(double2) * (size_t)nrhs;
+  if (overlap(phi, vb, x, vb)) return fail(cfg, HQMC_EINVAL, "phi and x overlap");
+  RET(check_device(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  RET(links(cfg, theta, true, true, s, false, true));
+  return solve_multi(cfg, nrhs, (const double2*)phi, (double2*)x, tol, maxit, solver, infos, s);
+}
+
+int hqmc_estimate_multi(hqmc_config* cfg, const double* theta, uint64_t seed, uint64_t counter, int nrv, double tol,
+                        int maxit, int solver, void* Gxi, void* xi, double* g_host, hqmc_solve_info* infos,
+                        void* stream) {
+  if (!cfg) return HQMC_EINVAL;
+  RET(check_estimate(cfg, theta, nrv, tol, maxit, solver, Gxi, xi));
+  RET(check_multi(cfg, nrv, solver, tol, maxit));
+  return estimate_multi(cfg, theta, seed, counter, nrv, tol, maxit, solver, Gxi, xi, g_host, infos,
+                        (cudaStream_t)stream);
 }
 
 int hqmc_force(hqmc_config* cfg, const double* theta, const void* X, double* F, double* dSf, void* stream) {
@@ -1953,6 +2469,20 @@ int hqmc_get_timing(hqmc_config* cfg, int timer, long long* launches, double* to
   }
   if (launches) *launches = (long long)tc.used;
   if (total_ms) *total_ms = sum;
+  return HQMC_OK;
+}
+
+int hqmc_get_timing_samples(hqmc_config* cfg, int timer, float* us, int max_n, int* n_out) {
+  if (!cfg || timer < 0 || timer >= HQMC_TIMER_COUNT || max_n < 0 || (max_n > 0 && !us)) return HQMC_EINVAL;
+  CK(cudaDeviceSynchronize());
+  const TimerClass& tc = cfg->timers[timer];
+  const int n = (int)std::min(tc.used, (size_t)max_n);
+  for (int i = 0; i < n; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, tc.pairs[i].first, tc.pairs[i].second));
+    us[i] = 1e3f * ms;
+  }
+  if (n_out) *n_out = (int)tc.used;
   return HQMC_OK;
 }
 

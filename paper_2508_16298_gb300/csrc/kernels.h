@@ -78,11 +78,31 @@ __device__ __forceinline__ double head_sum(const double* p, int n) {
   return warp_sum_partials(p, n);
 }
 
+// Where the head finds the CG state and the partial arrays: the launch's own
+// (HeadOwn, read from the arguments where they are used) or those of one system
+// of a multi-system launch (HeadAt).
 template <class R>
-__device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, int& s_flags, R& s_beta,
-                                           int& s_k) {
+struct HeadOwn {
+  const MdagmArgs<R>& a;
+  __device__ __forceinline__ CgState* st() const { return a.st; }
+  __device__ __forceinline__ const double* part_in() const { return a.part_in; }
+  __device__ __forceinline__ const double* part_rz() const { return a.part_rz; }
+  __device__ __forceinline__ const double* part_cross() const { return a.part_cross; }
+};
+struct HeadAt {
+  CgState* s;
+  const double *pin, *prz, *pcr;
+  __device__ __forceinline__ CgState* st() const { return s; }
+  __device__ __forceinline__ const double* part_in() const { return pin; }
+  __device__ __forceinline__ const double* part_rz() const { return prz; }
+  __device__ __forceinline__ const double* part_cross() const { return pcr; }
+};
+
+template <class R, class P>
+__device__ __forceinline__ void cgdir_head_impl(const MdagmArgs<R>& a, const P& ptr, bool writer, int& s_flags,
+                                                R& s_beta, int& s_k) {
   if (threadIdx.x < 32) {
-    CgState* st = a.st;
+    CgState* st = ptr.st();
     const int lane = threadIdx.x;
     const int done = *(volatile int*)&st->done;
     const int k = *(volatile int*)&st->k;
@@ -97,8 +117,8 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
       new_done = CG_MAXIT;
     } else if (k == seg) {
       flags = 2;
-      if (a.part_rz) {
-        const double rz = head_sum<R>(a.part_rz, a.n_part_rz);
+      if (ptr.part_rz()) {
+        const double rz = head_sum<R>(ptr.part_rz(), a.n_part_rz);
         if (!isfinite(rz) || !(rz > 0.0)) {
           flags = 1;
           new_done = isfinite(rz) ? CG_BREAKDOWN : CG_NONFINITE;
@@ -107,10 +127,10 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
         }
       }
     } else {
-      const double rr = head_sum<R>(a.part_in, a.n_part_in);
-      const double rz = a.part_rz ? head_sum<R>(a.part_rz, a.n_part_rz) : rr;
+      const double rr = head_sum<R>(ptr.part_in(), a.n_part_in);
+      const double rz = ptr.part_rz() ? head_sum<R>(ptr.part_rz(), a.n_part_rz) : rr;
       // flexible CG: beta = Re<z_k, r_k - r_{k-1}> / Re<z_{k-1}, r_{k-1}> (Polak-Ribiere)
-      const double cross = a.part_cross ? head_sum<R>(a.part_cross, a.n_part_rz) : 0.0;
+      const double cross = ptr.part_cross() ? head_sum<R>(ptr.part_cross(), a.n_part_rz) : 0.0;
       if (!isfinite(rr) || !isfinite(rz) || !isfinite(cross)) {
         flags = 1;
         new_done = CG_NONFINITE;
@@ -124,7 +144,7 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
         beta = (rz - cross) / st->rr[(k - 1) & 1];
       }
       if (writer && lane == 0) {
-        if (!a.part_rz) {
+        if (!ptr.part_rz()) {
           st->rr[k & 1] = rr;
         } else {
           st->rr_rec = rr;
@@ -143,6 +163,20 @@ __device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, i
     }
   }
   __syncthreads();
+}
+
+template <class R>
+__device__ __forceinline__ void cgdir_head(const MdagmArgs<R>& a, bool writer, int& s_flags, R& s_beta,
+                                           int& s_k) {
+  cgdir_head_impl<R>(a, HeadOwn<R>{a}, writer, s_flags, s_beta, s_k);
+}
+
+// The head of one system of a multi-system launch (its state and partials given).
+template <class R>
+__device__ __forceinline__ void cgdir_head_at(const MdagmArgs<R>& a, bool writer, int& s_flags, R& s_beta,
+                                              int& s_k, CgState* st, const double* part_in, const double* part_rz,
+                                              const double* part_cross) {
+  cgdir_head_impl<R>(a, HeadAt{st, part_in, part_rz, part_cross}, writer, s_flags, s_beta, s_k);
 }
 
 // Fused M^dagger M (three modes).
@@ -171,6 +205,20 @@ cudaError_t prepare_mdagm_walk(const SliceLaunch& sl);
 int walk_thread_cap(int nby);
 size_t walk_smem_bytes(const Geo& g, int mode);
 int mdagm_walk_blocks_per_sm(const SliceLaunch& sl);
+// Multi-system tau-walking launch: nsys systems on one field; CTA b serves system
+// b % nsys and slice range b / nsys.  System k's vectors (r or z, pbuf, y) start
+// vstride elements after system k - 1's, its CG state is a.st[k], and its partial
+// arrays (part_in, part_rz, part_out) start pstride doubles after system k - 1's.
+struct MultiStride {
+  int nsys;
+  long long vstride;
+  int pstride;
+};
+// CG-direction mode: sl.grid slice ranges per system, sl.grid * ms.nsys CTAs.
+cudaError_t launch_mdagm_walk_multi(const SliceLaunch& sl, const MdagmArgs<float>& a, const MultiStride& ms,
+                                    cudaStream_t s);
+cudaError_t prepare_mdagm_walk_multi(const SliceLaunch& sl);
+int mdagm_walk_multi_blocks_per_sm(const SliceLaunch& sl);
 
 // Tau-line preconditioner (precond.cu): z = (rho/b) F_W^dagger F_W r per site.
 struct LineCoef {
@@ -213,6 +261,10 @@ struct LineBatchDesc {
 cudaError_t launch_line_precond_batch(const LineBatchDesc<double>* descs, const int4* tiles, int ntiles, int W,
                                      int tc, cudaStream_t s);
 cudaError_t prepare_line_precond_batch(int W, int tc);
+// The same in FP32 (the systems of a multi-system mixed solve).
+cudaError_t launch_line_precond_batch(const LineBatchDesc<float>* descs, const int4* tiles, int ntiles, int W,
+                                     int tc, cudaStream_t s);
+cudaError_t prepare_line_precond_batch32(int W, int tc);
 
 // Preconditioned CG: the vector update fused with the preconditioner (precond.cu).
 template <class R>
@@ -295,11 +347,15 @@ struct FinArgs {
 // blocks[b] = (chain, local block), nblocks[chain].
 cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
                                    cudaStream_t s);
+// The same in FP32 (descs: device array of UpdArgs<float>).
+cudaError_t launch_cg_update_batch32(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
+                                     cudaStream_t s);
 
 enum { FIN_START = 0, FIN_RESTART = 1, FIN_RELIABLE = 2, FIN_REPORT = 3 };
 
 
-// Batched finalize (START or RESTART), one block per chain; descs: device array of FinArgs.
+// Batched finalize (every FIN_* mode, as resid_finalize), one block per chain;
+// descs: device array of FinArgs.
 cudaError_t launch_resid_finalize_batch(const void* descs, int nchains, int mode, double tol, int maxit, int gate,
                                         cudaStream_t s);
 // bodies (nullable): device counter of loop bodies, incremented once per body.
@@ -318,6 +374,9 @@ cudaError_t launch_fcg_dots(long long n, const float2* r, const float2* r_old, c
 // x64 += xh32; xh32 = 0 (gated on st->done unless st is NULL).
 cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, const CgState* st, int gate,
                                          cudaStream_t s);
+// The same for nsys systems stored back to back (system k: x + k n, xh + k n, st + k).
+cudaError_t launch_accumulate_correction_multi(long long n, int nsys, double2* x, float2* xh, const CgState* st,
+                                               int gate, cudaStream_t s);
 
 // Ends a device-side CG loop body: counts it and sets the WHILE condition to
 // "still running", forcing CG_MAXIT once loop_cap bodies have run.

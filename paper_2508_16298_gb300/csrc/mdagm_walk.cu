@@ -46,8 +46,13 @@ size_t walk_smem_bytes(const Geo& g, int mode) {
   return (size_t)(1 + nv + 1 + 2) * g.V * sizeof(float2);
 }
 
-template <int MODE, int NBY>
-__global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(const MdagmArgs<float> a) {
+// MULTI: one launch over ms.nsys systems that share theta (launch_mdagm_walk_multi):
+// CTA b walks slice range b / nsys of system b % nsys, so the CTAs resident at one
+// time read the same theta slices, and each system's ranges are longer than in a
+// one-system launch of the same grid (fewer halo sweeps per slice).
+template <int MODE, int NBY, bool MULTI>
+__global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(const MdagmArgs<float> a,
+                                                                                    const MultiStride ms) {
   using T = float2;
   constexpr int H = 2 * NBY;
   constexpr int NV = MODE == MODE_CGDIR ? 2 : 1;
@@ -65,21 +70,29 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
   __shared__ float s_beta;
   __shared__ int s_k;
 
+  // This CTA's system and slice range (MULTI), else the launch's only system.
+  const int sys = MULTI ? (int)(blockIdx.x % (unsigned)ms.nsys) : 0;
+  const int rng = MULTI ? (int)(blockIdx.x / (unsigned)ms.nsys) : (int)blockIdx.x;
+  const int G = MULTI ? (int)(gridDim.x / (unsigned)ms.nsys) : gridDim.x;
+  const size_t voff = MULTI ? (size_t)sys * (size_t)ms.vstride : 0;
+  const size_t poff = MULTI ? (size_t)sys * (size_t)ms.pstride : 0;
+  CgState* const st = MULTI ? a.st + sys : a.st;
+#define WALK_Y (MULTI ? a.y + voff : a.y)
+
   // The direction buffers follow the iteration count k, which no kernel changes
   // while this one runs (the update kernel advances it): iteration k reads
   // pbuf[k & 1] and writes pbuf[(k + 1) & 1].  Read here, before the head.
-  const int k0 = MODE == MODE_CGDIR ? *(volatile const int*)&a.st->k : 0;
+  const int k0 = MODE == MODE_CGDIR ? *(volatile const int*)&st->k : 0;
   const T* p_old = nullptr;
   T* p_new = nullptr;
   if (MODE == MODE_CGDIR) {
-    p_old = (k0 & 1) ? a.pbuf[1] : a.pbuf[0];
-    p_new = (k0 & 1) ? a.pbuf[0] : a.pbuf[1];
+    p_old = ((k0 & 1) ? a.pbuf[1] : a.pbuf[0]) + voff;
+    p_new = ((k0 & 1) ? a.pbuf[0] : a.pbuf[1]) + voff;
   }
-  const T* vsrc = MODE == MODE_CGDIR ? a.r : a.x;
+  const T* vsrc = (MODE == MODE_CGDIR ? a.r : a.x) + voff;
 
-  const int G = gridDim.x;
-  const int tb = (int)((long long)blockIdx.x * N / G);
-  const int te = (int)((long long)(blockIdx.x + 1) * N / G);
+  const int tb = MULTI ? (int)((long long)rng * N / G) : (int)((long long)blockIdx.x * N / G);
+  const int te = MULTI ? (int)((long long)(rng + 1) * N / G) : (int)((long long)(blockIdx.x + 1) * N / G);
   auto wrap = [N](int j) { return j < 0 ? j + N : (j >= N ? j - N : j); };
 
   // The stage always carries p_old in CG-direction mode (ignored on the first
@@ -115,7 +128,8 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
     }
   }
   if (MODE == MODE_CGDIR) {
-    cgdir_head<float>(a, blockIdx.x == 0, s_flags, s_beta, s_k);
+    cgdir_head_at<float>(a, rng == 0, s_flags, s_beta, s_k, st, a.part_in + poff,
+                         a.part_rz ? a.part_rz + poff : nullptr, a.part_cross ? a.part_cross + poff : nullptr);
     if (s_flags & 1) {  // uniform over the grid; the stage in flight lands before the block exits
       if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0);
       return;
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int s = y * L + (c ? sg.x1 : sg.x0);
-        a.y[bj + s] = caxpy(t[r][c], cB, v[r][c]);
+        WALK_Y[bj + s] = caxpy(t[r][c], cB, v[r][c]);
         t[r][c] = tn[r][c];
         v[r][c] = X1[(2 * r + c) * blockDim.x + threadIdx.x];
       }
@@ -237,27 +251,30 @@ __global__ void __launch_bounds__(WalkThreads<NBY>::max, 1) mdagm_walk_kernel(co
     // non-finite result, then give the copy in flight a bounded chance to land.
     const T nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
     for (int j = tb; j < te; ++j)
-      for (int s = threadIdx.x; s < V; s += blockDim.x) a.y[(size_t)j * V + s] = nan2;
+      for (int s = threadIdx.x; s < V; s += blockDim.x) WALK_Y[(size_t)j * V + s] = nan2;
     acc = __longlong_as_double(0x7ff8000000000000ll);
     if (a.err && threadIdx.x == 0) atomicExch(a.err, 1);  // the host reports HQMC_ETIMEOUT
     mbar_wait_bounded(&bar, parity ^ 1);
   }
   if (MODE == MODE_CGDIR) {
     const double tot = block_sum(acc, red);
-    if (threadIdx.x == 0) a.part_out[blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.part_out[poff + rng] = tot;
   }
+#undef WALK_Y
 }
 
-template <int MODE, int NBY>
-static cudaError_t walk_launch(const SliceLaunch& sl, const MdagmArgs<float>& a, cudaStream_t s) {
+template <int MODE, int NBY, bool MULTI = false>
+static cudaError_t walk_launch(const SliceLaunch& sl, const MdagmArgs<float>& a, cudaStream_t s,
+                               const MultiStride ms = MultiStride{1, 0, 0}) {
   const size_t smem = walk_smem_bytes(sl.g, MODE);
-  mdagm_walk_kernel<MODE, NBY><<<sl.grid, sl.threads, smem, s>>>(a);
+  const int grid = MULTI ? sl.grid * ms.nsys : sl.grid;
+  mdagm_walk_kernel<MODE, NBY, MULTI><<<grid, sl.threads, smem, s>>>(a, ms);
   return cudaGetLastError();
 }
 
-template <int MODE, int NBY>
+template <int MODE, int NBY, bool MULTI = false>
 static cudaError_t walk_prepare(const SliceLaunch& sl) {
-  return raise_smem_limit(mdagm_walk_kernel<MODE, NBY>, walk_smem_bytes(sl.g, MODE));
+  return raise_smem_limit(mdagm_walk_kernel<MODE, NBY, MULTI>, walk_smem_bytes(sl.g, MODE));
 }
 
 template <int MODE>
@@ -287,9 +304,49 @@ int mdagm_walk_blocks_per_sm(const SliceLaunch& sl) {
   cudaError_t e = cudaErrorInvalidValue;
   const size_t smem = walk_smem_bytes(sl.g, MODE_CGDIR);
   switch (sl.nby) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 1>, sl.threads, smem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 2>, sl.threads, smem); break;
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 3>, sl.threads, smem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 1, false>, sl.threads, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 2, false>, sl.threads, smem); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 3, false>, sl.threads, smem); break;
+    default: break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// Multi-system CG-direction launch: sl.grid slice ranges per system, a.nsys systems.
+cudaError_t launch_mdagm_walk_multi(const SliceLaunch& sl, const MdagmArgs<float>& a, const MultiStride& ms,
+                                    cudaStream_t s) {
+  if (sl.grid < 1 || sl.grid > sl.g.Ntau || ms.nsys < 1 || (long long)sl.grid * ms.nsys > (1ll << 30))
+    return cudaErrorInvalidValue;
+  switch (sl.nby) {
+    case 1: return walk_launch<MODE_CGDIR, 1, true>(sl, a, s, ms);
+    case 2: return walk_launch<MODE_CGDIR, 2, true>(sl, a, s, ms);
+    case 3: return walk_launch<MODE_CGDIR, 3, true>(sl, a, s, ms);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t prepare_mdagm_walk_multi(const SliceLaunch& sl) {
+  switch (sl.nby) {
+    case 1: return walk_prepare<MODE_CGDIR, 1, true>(sl);
+    case 2: return walk_prepare<MODE_CGDIR, 2, true>(sl);
+    case 3: return walk_prepare<MODE_CGDIR, 3, true>(sl);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// CTAs of the multi-system kernel the device keeps resident per SM (0: none fit).
+int mdagm_walk_multi_blocks_per_sm(const SliceLaunch& sl) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  const size_t smem = walk_smem_bytes(sl.g, MODE_CGDIR);
+  switch (sl.nby) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 1, true>, sl.threads, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 2, true>, sl.threads, smem); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mdagm_walk_kernel<MODE_CGDIR, 3, true>, sl.threads, smem); break;
     default: break;
   }
   if (e != cudaSuccess) {

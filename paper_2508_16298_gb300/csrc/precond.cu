@@ -555,6 +555,16 @@ cudaError_t prepare_line_precond_batch(int W, int tc) {
   return raise_smem_limit(line_precond_batch_kernel<double>, line_smem_bytes(8, W, tc));
 }
 
+cudaError_t launch_line_precond_batch(const LineBatchDesc<float>* descs, const int4* tiles, int ntiles, int W,
+                                     int tc, cudaStream_t s) {
+  line_precond_batch_kernel<float><<<ntiles, kLineSites * kLineWarps, line_smem_bytes(4, W, tc), s>>>(descs, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_line_precond_batch32(int W, int tc) {
+  return raise_smem_limit(line_precond_batch_kernel<float>, line_smem_bytes(4, W, tc));
+}
+
 template cudaError_t launch_line_precond<double>(const Geo&, const LineCoef&, const LineLaunch&, const double2*,
                                                  double2*, double*, const CgState*, cudaStream_t);
 template cudaError_t launch_line_precond<float>(const Geo&, const LineCoef&, const LineLaunch&, const float2*,

@@ -159,6 +159,12 @@ cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const 
   cg_update_batch_kernel<double><<<total_blocks, 256, 0, s>>>((const UpdArgs<double>*)descs, blocks, nblocks);
   return cudaGetLastError();
 }
+
+cudaError_t launch_cg_update_batch32(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
+                                     cudaStream_t s) {
+  cg_update_batch_kernel<float><<<total_blocks, 256, 0, s>>>((const UpdArgs<float>*)descs, blocks, nblocks);
+  return cudaGetLastError();
+}
 template cudaError_t launch_cg_update<double>(long long, int, void*, int, double2*, double2* const[2],
                                               const double2*, const double*, int, double*, CgState*,
                                               cudaStream_t);
@@ -248,6 +254,8 @@ __global__ void resid_finalize_batch_kernel(const FinArgs* __restrict__ descs, i
   if (!s_open) return;
   const double rr = warp_sum_partials(f.part, f.n);
   const double bb = warp_sum_partials(f.part + f.n, f.n);
+  if (mode == FIN_RELIABLE)
+    for (int k = 1 + threadIdx.x; k < f.n_rr_out; k += blockDim.x) f.part_rr_out[k] = 0.0;
   if (threadIdx.x != 0) return;
   CgState* st = f.st;
   if (f.report) {
@@ -279,6 +287,18 @@ __global__ void resid_finalize_batch_kernel(const FinArgs* __restrict__ descs, i
     if (!isfinite(rr)) st->done = CG_NONFINITE;
     else if (rr <= st->tol2bb) st->done = CG_CONVERGED;
     else if (k >= st->maxit) st->done = CG_MAXIT;
+    else st->done = CG_RUNNING;
+  } else if (mode == FIN_RELIABLE) {  // mixed solver: as resid_finalize_kernel
+    const int k = st->k;
+    f.part_rr_out[0] = rr;
+    const int nr = st->n_rel;
+    const bool stalled = nr >= 8 && rr > 0.25 * st->rr_rel[nr & 7];
+    st->rr_rel[nr & 7] = rr;
+    st->n_rel = nr + 1;
+    if (!isfinite(rr)) st->done = CG_NONFINITE;
+    else if (rr <= st->tol2bb) st->done = CG_CONVERGED;
+    else if (k >= st->maxit) st->done = CG_MAXIT;
+    else if (stalled) st->done = CG_STAGNATED;
     else st->done = CG_RUNNING;
   }
 }
@@ -374,6 +394,28 @@ __global__ void accumulate_correction_kernel(long long n, double2* __restrict__ 
 cudaError_t launch_accumulate_correction(long long n, double2* x, float2* xh, const CgState* st, int gate,
                                          cudaStream_t s) {
   accumulate_correction_kernel<<<ew_blocks(n, 256, 4096), 256, 0, s>>>(n, x, xh, st, gate);
+  return cudaGetLastError();
+}
+
+// nsys systems back to back: blockIdx.y is the system.
+__global__ void accumulate_correction_multi_kernel(long long n, double2* __restrict__ x, float2* __restrict__ xh,
+                                                   const CgState* st, int gate) {
+  const size_t off = (size_t)blockIdx.y * (size_t)n;
+  if (st && !gate_open(gate, *(volatile const int*)&st[blockIdx.y].done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 d = xh[off + i];
+    const double2 xv = x[off + i];
+    x[off + i] = make_double2(xv.x + (double)d.x, xv.y + (double)d.y);
+    xh[off + i] = make_float2(0.f, 0.f);
+  }
+}
+
+cudaError_t launch_accumulate_correction_multi(long long n, int nsys, double2* x, float2* xh, const CgState* st,
+                                               int gate, cudaStream_t s) {
+  if (nsys < 1 || nsys > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)ew_blocks(n, 256, 1024), (unsigned)nsys);
+  accumulate_correction_multi_kernel<<<grid, 256, 0, s>>>(n, x, xh, st, gate);
   return cudaGetLastError();
 }
 

@@ -37,9 +37,10 @@ EXPORTS = ("hqmc_make_config", "hqmc_free_config", "hqmc_strerror", "hqmc_last_e
            "hqmc_launch_count", "hqmc_get_launch_shape",
            "hqmc_apply_M", "hqmc_apply_MdagM", "hqmc_apply_precond", "hqmc_get_precond", "hqmc_get_precond_shape",
            "hqmc_set_precond_fused", "hqmc_cg_solve",
-           "hqmc_estimate", "hqmc_estimate_projected",
+           "hqmc_estimate", "hqmc_estimate_projected", "hqmc_set_multi_rhs", "hqmc_set_multi_ranges", "hqmc_multi_launch_shape",
+           "hqmc_cg_solve_multi", "hqmc_estimate_multi",
            "hqmc_force", "hqmc_action_terms",
-           "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing",
+           "hqmc_draw", "hqmc_leapfrog", "hqmc_trajectory", "hqmc_set_timing", "hqmc_get_timing", "hqmc_get_timing_samples",
            "hqmc_probe_fp64_rate", "hqmc_apply_MdagM_static", "hqmc_make_batch", "hqmc_free_batch",
            "hqmc_batch_last_error", "hqmc_batch_launch_count", "hqmc_batch_cg_solve", "hqmc_batch_trajectory",
            "hqmc_batch_set_solver", "hqmc_batch_launch_shape",
@@ -109,6 +110,12 @@ _sig = {
                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_estimate_projected": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _i, _d, _i, _i, _vp, _vp,
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), _vp], _i),
+    "hqmc_set_multi_rhs": ([_vp, _i], _i),
+    "hqmc_set_multi_ranges": ([_vp, _i], _i),
+    "hqmc_multi_launch_shape": ([_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "hqmc_cg_solve_multi": ([_vp, _vp, _i, _vp, _vp, _d, _i, _i, ctypes.POINTER(SolveInfo), _vp], _i),
+    "hqmc_estimate_multi": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _i, _d, _i, _i, _vp, _vp,
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), _vp], _i),
     "hqmc_force": ([_vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hqmc_action_terms": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
     "hqmc_draw": ([_vp, _u64, _u64, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp], _i),
@@ -117,6 +124,7 @@ _sig = {
                          ctypes.POINTER(TrajInfo), _vp], _i),
     "hqmc_set_timing": ([_vp, _i], _i),
     "hqmc_get_timing": ([_vp, _i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _i),
+    "hqmc_get_timing_samples": ([_vp, _i, ctypes.POINTER(ctypes.c_float), _i, ctypes.POINTER(_i)], _i),
     "hqmc_probe_fp64_rate": ([_vp, ctypes.POINTER(ctypes.c_double)], _i),
     "hqmc_apply_MdagM_static": ([ctypes.POINTER(Params), _vp, _vp, _vp, _vp], _i),
     "hqmc_make_batch": ([ctypes.POINTER(Params), _i, ctypes.POINTER(_vp)], _i),
@@ -325,14 +333,55 @@ def cg_solve(cfg: Config, theta, phi, x=None, tol: float = 1e-8, maxit: int = 10
     return x, info.as_dict()
 
 
+def set_multi_rhs(cfg: Config, nmax: int):
+    """Workspace for up to nmax systems solved together on one field (hqmc_set_multi_rhs;
+    0 frees it)."""
+    cfg.check(_lib.hqmc_set_multi_rhs(cfg.handle, nmax))
+
+
+def set_multi_ranges(cfg: Config, ranges: int):
+    """Slice ranges per system of the multi-system walk launch (0: the default model)."""
+    cfg.check(_lib.hqmc_set_multi_ranges(cfg.handle, ranges))
+
+
+def multi_launch_shape(cfg: Config, nrhs: int) -> dict:
+    """Slice ranges per system, block size and strip height of a multi-system solve."""
+    r, t, b = _i(), _i(), _i()
+    cfg.check(_lib.hqmc_multi_launch_shape(cfg.handle, nrhs, ctypes.byref(r), ctypes.byref(t), ctypes.byref(b)))
+    return {"ranges": r.value, "threads": t.value, "nby": b.value}
+
+
+def cg_solve_multi(cfg: Config, theta, phi, x=None, tol: float = 1e-8, maxit: int = 100000, solver="pmixed",
+                   raise_on_fail: bool = True):
+    """Solve (M^dagger M) x_k = phi_k for the nrhs systems of phi (shape (nrhs, Ntau, L, L))
+    together (hqmc_cg_solve_multi; needs set_multi_rhs(cfg, >= nrhs)).  Returns (x, infos)."""
+    cfg._bonds(theta, "theta")
+    if phi.dim() != 4 or tuple(phi.shape[1:]) != (cfg.Ntau, cfg.L, cfg.L) or phi.dtype != torch.complex128 \
+            or not phi.is_contiguous():
+        raise ValueError("phi must be a contiguous complex128 tensor of shape (nrhs, Ntau, L, L)")
+    x = torch.zeros_like(phi) if x is None else x
+    if x.shape != phi.shape or x.dtype != phi.dtype or not x.is_contiguous():
+        raise ValueError("x must match phi")
+    nrhs = phi.shape[0]
+    infos = (SolveInfo * nrhs)()
+    rc = _lib.hqmc_cg_solve_multi(cfg.handle, _ptr(theta), nrhs, _ptr(phi), _ptr(x), tol, maxit, _solver(solver),
+                                  infos, _stream())
+    if raise_on_fail:
+        cfg.check(rc)
+    return x, [i.as_dict() for i in infos]
+
+
 def estimate(cfg: Config, theta, nrv: int, seed: int = 0, counter: int = 0, tol: float = 1e-8,
              maxit: int = 100000, solver="cg64", want_vectors: bool = False, raise_on_fail: bool = True,
-             projected: bool = False, Gxi=None):
-    """Stochastic estimation with nrv CN(0, 1) vectors (hqmc_estimate, or with
+             projected: bool = False, Gxi=None, together: bool = False):
+    """Stochastic estimation with nrv CN(0, 1) vectors (hqmc_estimate; with
     projected=True hqmc_estimate_projected, which needs the solutions: Gxi is then
-    allocated here unless given).  Returns (g, infos, Gxi, xi): g the complex estimate
-    of the mean diagonal of M^{-1}, the per-vector solve infos, and (if want_vectors)
-    M^{-1} xi_k and xi_k as tensors of shape (nrv, Ntau, L, L)."""
+    allocated here unless given; with together=True hqmc_estimate_multi, the systems
+    solved together, which needs set_multi_rhs).  Returns (g, infos, Gxi, xi): g the
+    complex estimate of the mean diagonal of M^{-1}, the per-vector solve infos, and
+    (if want_vectors) M^{-1} xi_k and xi_k as tensors of shape (nrv, Ntau, L, L)."""
+    if projected and together:
+        raise ValueError("projected and together are different estimates")
     cfg._bonds(theta, "theta")
     xi = None
     if Gxi is None and (want_vectors or projected):
@@ -341,7 +390,7 @@ def estimate(cfg: Config, theta, nrv: int, seed: int = 0, counter: int = 0, tol:
         xi = torch.empty_like(Gxi)
     g = (ctypes.c_double * 2)()
     infos = (SolveInfo * nrv)()
-    fn = _lib.hqmc_estimate_projected if projected else _lib.hqmc_estimate
+    fn = _lib.hqmc_estimate_projected if projected else _lib.hqmc_estimate_multi if together else _lib.hqmc_estimate
     rc = fn(cfg.handle, _ptr(theta), seed, counter, nrv, tol, maxit, _solver(solver), _ptr(Gxi), _ptr(xi), g, infos,
             _stream())
     if raise_on_fail:
@@ -419,6 +468,15 @@ def get_timing(cfg: Config, timer: int):
     n, ms = ctypes.c_longlong(), ctypes.c_double()
     cfg.check(_lib.hqmc_get_timing(cfg.handle, timer, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def get_timing_samples(cfg: Config, timer: int) -> list:
+    """Per-launch durations (microseconds) of one kernel class since set_timing, in launch order."""
+    n = _i()
+    cfg.check(_lib.hqmc_get_timing_samples(cfg.handle, timer, None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_float * max(n.value, 1))()
+    cfg.check(_lib.hqmc_get_timing_samples(cfg.handle, timer, buf, n.value, ctypes.byref(n)))
+    return list(buf[:n.value])
 
 
 def probe_fp64_rate(cfg: Config) -> float:

@@ -53,13 +53,17 @@ def test_host_only_setters_reject_null_handles(lib_path):
     lib = ctypes.CDLL(lib_path)
     vp, i = ctypes.c_void_p, ctypes.c_int
     for name, args in [("hqmc_set_net_tensor_cores", [vp, i]), ("hqmc_set_net_interval", [vp, i]),
-                       ("hqmc_set_guess_history", [vp, i]), ("hqmc_batch_set_solver", [vp, i])]:
+                       ("hqmc_set_guess_history", [vp, i]), ("hqmc_batch_set_solver", [vp, i]),
+                       ("hqmc_set_multi_rhs", [vp, i]), ("hqmc_set_multi_ranges", [vp, i])]:
         f = getattr(lib, name)
         f.argtypes, f.restype = args, i
         assert f(None, 1) == 1, name
     f = lib.hqmc_batch_launch_shape
     f.argtypes, f.restype = [vp, vp, vp, vp, vp], i
     assert f(None, None, None, None, None) == 1
+    f = lib.hqmc_multi_launch_shape
+    f.argtypes, f.restype = [vp, i, vp, vp, vp], i
+    assert f(None, 4, None, None, None) == 1
 
 
 def test_params_struct_layout_matches_header(lib_path, tmp_path):
