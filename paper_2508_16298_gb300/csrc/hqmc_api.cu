@@ -71,9 +71,6 @@ struct MultiWs {
   double *part_w = nullptr, *part_ew = nullptr, *part_rz = nullptr, *part_res = nullptr, *report = nullptr;
   CgState* st = nullptr;
   CgState** d_states = nullptr;
-  UpdArgs<float>* d_upd = nullptr;     // per call (n_pq follows the walk launch's ranges)
-  int2* d_ublocks = nullptr;           // (system, block) of the batched update
-  int* d_unblocks = nullptr;
   LineBatchDesc<float>* d_line = nullptr;
   int4* d_ltiles = nullptr;            // (system, bx, by) of the batched preconditioner
   MdagmArgs<double>* d_res = nullptr;  // per call: [0, cap) start residuals, [cap, 2 cap) reliable updates
@@ -1874,7 +1871,10 @@ int multi_setup(hqmc_config* cfg, int cap) {
   // update: about two resident waves of 256-thread blocks over all systems, so each
   // block streams enough of its vector to hide the latency of its head (state and
   // partial sums); at most the one-system grid
-  m.ublocks = (int)std::max(8LL, std::min((long long)cfg->ew_grid, (2LL * cfg->num_sms * 8 + cap - 1) / cap));
+  {
+    const long long resident = (long long)cfg->num_sms * std::max(1, cg_update_multi_blocks_per_sm());
+    m.ublocks = (int)std::max(8LL, std::min((long long)cfg->ew_grid, 2 * resident / cap));
+  }
   m.pstride = std::max(N, std::max(m.ublocks, ll.gx * ll.gy));
   m.nlt = ll.gx * ll.gy;
   // FP64 residual: the cluster size of the one-system residual where the batched
@@ -1904,9 +1904,6 @@ int multi_setup(hqmc_config* cfg, int cap) {
   RET(mdalloc(cfg, &m.report, 2 * (size_t)cap));
   RET(mdalloc(cfg, &m.st, (size_t)cap));
   RET(mdalloc(cfg, &m.d_states, (size_t)cap));
-  RET(mdalloc(cfg, &m.d_upd, (size_t)cap));
-  RET(mdalloc(cfg, &m.d_ublocks, (size_t)cap * m.ublocks));
-  RET(mdalloc(cfg, &m.d_unblocks, (size_t)cap));
   RET(mdalloc(cfg, &m.d_line, (size_t)cap));
   RET(mdalloc(cfg, &m.d_ltiles, (size_t)cap * m.nlt));
   RET(mdalloc(cfg, &m.d_res, 2 * (size_t)cap));
@@ -1914,7 +1911,7 @@ int multi_setup(hqmc_config* cfg, int cap) {
   RET(mdalloc(cfg, &m.d_rtiles, (size_t)cap * m.rnt));
   CK(cudaMallocHost((void**)&m.st_h, (size_t)cap * sizeof(CgState)));
   CK(cudaMallocHost((void**)&m.report_h, 2 * (size_t)cap * sizeof(double)));
-  m.stage_bytes = (size_t)cap * (2 * sizeof(MdagmArgs<double>) + sizeof(FinArgs) + sizeof(UpdArgs<float>));
+  m.stage_bytes = (size_t)cap * (2 * sizeof(MdagmArgs<double>) + sizeof(FinArgs));
   CK(cudaMallocHost(&m.h_stage, m.stage_bytes));
   CK(cudaMemset(m.st, 0, (size_t)cap * sizeof(CgState)));
   CK(cudaMemset(m.part_w, 0, (size_t)cap * m.pstride * sizeof(double)));
@@ -1922,13 +1919,11 @@ int multi_setup(hqmc_config* cfg, int cap) {
   CK(cudaMemset(m.part_rz, 0, (size_t)cap * m.pstride * sizeof(double)));
   // fixed tables, system-major (the first nsys systems' entries are a prefix)
   std::vector<CgState*> states(cap);
-  std::vector<int2> ublocks, rtiles;
-  std::vector<int> unblocks(cap, m.ublocks);
+  std::vector<int2> rtiles;
   std::vector<LineBatchDesc<float>> line(cap);
   std::vector<int4> ltiles;
   for (int k = 0; k < cap; ++k) {
     states[k] = m.st + k;
-    for (int j = 0; j < m.ublocks; ++j) ublocks.push_back(make_int2(k, j));
     for (int t = 0; t < N; t += m.rC) rtiles.push_back(make_int2(k, t));
     line[k] = LineBatchDesc<float>{cfg->g, cfg->lc, m.r + k * n, m.z + k * n, m.part_rz + (size_t)k * m.pstride,
                                    m.st + k, ll.gx, ll.chunk};
@@ -1936,8 +1931,6 @@ int multi_setup(hqmc_config* cfg, int cap) {
       for (int bx = 0; bx < ll.gx; ++bx) ltiles.push_back(make_int4(k, bx, by, 0));
   }
   CK(cudaMemcpy(m.d_states, states.data(), cap * sizeof(CgState*), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(m.d_ublocks, ublocks.data(), ublocks.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(m.d_unblocks, unblocks.data(), cap * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m.d_line, line.data(), cap * sizeof(LineBatchDesc<float>), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m.d_ltiles, ltiles.data(), ltiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m.d_rtiles, rtiles.data(), rtiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -1968,6 +1961,7 @@ int multi_body(hqmc_config* cfg, int nsys, bool pc, const SliceLaunch& wl, doubl
   a.part_out = m.part_w;
   a.st = m.st;
   const MultiStride ms{nsys, cfg->n, m.pstride};
+  const UpdArgs<float> upd{cfg->n, m.xh, 0, m.r, m.p0, m.p1, m.q, m.part_w, wl.grid, m.part_ew, m.st};
   const int iters = cfg->reliable;
   int slot;
   for (int c = 0; c < iters; ++c) {
@@ -1975,7 +1969,7 @@ int multi_body(hqmc_config* cfg, int nsys, bool pc, const SliceLaunch& wl, doubl
     CK(launch_mdagm_walk_multi(wl, a, ms, s));
     RET(timer_end(cfg, HQMC_TIMER_MDAGM32, s, slot));
     RET(timer_begin(cfg, HQMC_TIMER_CG_UPDATE, s, &slot));
-    CK(launch_cg_update_batch32(m.d_upd, m.d_ublocks, m.d_unblocks, nsys * m.ublocks, s));
+    CK(launch_cg_update_multi(upd, cfg->n, m.pstride, nsys, m.ublocks, s));
     RET(timer_end(cfg, HQMC_TIMER_CG_UPDATE, s, slot));
     if (pc) {
       RET(timer_begin(cfg, HQMC_TIMER_PRECOND, s, &slot));
@@ -2062,11 +2056,9 @@ int solve_multi(hqmc_config* cfg, int nsys, const double2* phi, double2* x, doub
   const size_t n = (size_t)cfg->n;
   SliceLaunch wl = multi_walk_shape(cfg);
   wl.grid = multi_granges(cfg, nsys);
-  // per-call descriptors: FP64 residuals (start, reliable update), their
-  // bookkeeping and the updates (n_pq follows the walk launch's ranges)
+  // per-call descriptors: FP64 residuals (start, reliable update) and their bookkeeping
   std::vector<MdagmArgs<double>> res(2 * (size_t)nsys);
   std::vector<FinArgs> fin(nsys);
-  std::vector<UpdArgs<float>> upd(nsys);
   for (int k = 0; k < nsys; ++k) {
     MdagmArgs<double> r = mdagm_args<double, MODE_RESID>(cfg);
     r.U = cfg->U64;
@@ -2083,22 +2075,16 @@ int solve_multi(hqmc_config* cfg, int nsys, const double2* phi, double2* x, doub
     res[nsys + k] = r;
     fin[k] = FinArgs{m.part_res + (size_t)k * m.rstride, m.rslots, m.part_ew + (size_t)k * m.pstride,
                      m.ublocks, m.st + k, m.report + 2 * k};
-    upd[k] = UpdArgs<float>{cfg->n,        m.xh + k * n, 0, m.r + k * n, m.p0 + k * n, m.p1 + k * n, m.q + k * n,
-                            m.part_w + (size_t)k * m.pstride, wl.grid, m.part_ew + (size_t)k * m.pstride,
-                            m.st + k};
   }
   // staged through pinned memory (the previous call synchronised, so its copies are done)
   char* hs = (char*)m.h_stage;
   std::memcpy(hs, res.data(), 2 * (size_t)nsys * sizeof(MdagmArgs<double>));
   char* hf = hs + 2 * (size_t)m.cap * sizeof(MdagmArgs<double>);
   std::memcpy(hf, fin.data(), nsys * sizeof(FinArgs));
-  char* hu = hf + (size_t)m.cap * sizeof(FinArgs);
-  std::memcpy(hu, upd.data(), nsys * sizeof(UpdArgs<float>));
   CK(cudaMemcpyAsync(m.d_res, hs, nsys * sizeof(MdagmArgs<double>), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(m.d_res + m.cap, hs + nsys * sizeof(MdagmArgs<double>), nsys * sizeof(MdagmArgs<double>),
                      cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(m.d_fin, hf, nsys * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(m.d_upd, hu, nsys * sizeof(UpdArgs<float>), cudaMemcpyHostToDevice, s));
   // start: r_k = phi_k - O x_k in FP64 (stored as float), states, corrections zero, z_k
   LK(1, (launch_mdagm_batch<double, MODE_RESID>(m.d_res, m.d_rtiles, nsys * m.rnt, m.rC, cfg->sl.threads,
                                                 multi_res_smem(cfg), s)));

@@ -347,9 +347,12 @@ struct FinArgs {
 // blocks[b] = (chain, local block), nblocks[chain].
 cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
                                    cudaStream_t s);
-// The same in FP32 (descs: device array of UpdArgs<float>).
-cudaError_t launch_cg_update_batch32(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
-                                     cudaStream_t s);
+// FP32 update of nsys systems stored back to back (base: system 0's arguments, a FP32
+// correction x; system k's vectors at k vstride elements, its partials at k pstride,
+// its state at base.st + k), blocks_per_system blocks each (= partials of <r, r>).
+cudaError_t launch_cg_update_multi(const UpdArgs<float>& base, long long vstride, int pstride, int nsys,
+                                   int blocks_per_system, cudaStream_t s);
+int cg_update_multi_blocks_per_sm();
 
 enum { FIN_START = 0, FIN_RESTART = 1, FIN_RELIABLE = 2, FIN_REPORT = 3 };
 

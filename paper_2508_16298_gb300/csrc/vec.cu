@@ -70,8 +70,11 @@ cudaError_t launch_links(const Geo& g, const double* theta, double t1, double t2
 // ---------------------------------------------------------------------------
 // CG update: alpha = <r,r>/<p,Op>; x += alpha p; r -= alpha Op; partial <r,r>.
 // Body of the CG update for block j of nblocks serving one chain.
+// voff: element offset added to every vector access (one system of several stored
+// back to back; 0 otherwise).
 template <class R>
-__device__ __forceinline__ void cg_update_body(const UpdArgs<R>& u, const int j, const int nblocks) {
+__device__ __forceinline__ void cg_update_body(const UpdArgs<R>& u, const int j, const int nblocks,
+                                               const size_t voff = 0) {
   __shared__ double red[32];
   __shared__ int s_stop;
   __shared__ double s_alpha;
@@ -111,15 +114,15 @@ __device__ __forceinline__ void cg_update_body(const UpdArgs<R>& u, const int j,
   const C2<R>* __restrict__ p = ((s_k + 1) & 1) ? u.p1 : u.p0;
   R acc = 0;  // FP32: a thread's few terms in float (cdot_re_own)
   for (long long i = j * (long long)blockDim.x + threadIdx.x; i < u.n; i += (long long)nblocks * blockDim.x) {
-    const C2<R> pv = p[i];
-    C2<R> rv = caxpy(u.r[i], -alpha, u.q[i]);
-    u.r[i] = rv;
+    const C2<R> pv = p[voff + i];
+    C2<R> rv = caxpy(u.r[voff + i], -alpha, u.q[voff + i]);
+    u.r[voff + i] = rv;
     if (u.x_is_double) {
       double2* xd = reinterpret_cast<double2*>(u.x);
-      xd[i] = caxpy(xd[i], (double)alpha, make_double2(pv.x, pv.y));
+      xd[voff + i] = caxpy(xd[voff + i], (double)alpha, make_double2(pv.x, pv.y));
     } else {
       float2* xf = reinterpret_cast<float2*>(u.x);
-      xf[i] = caxpy(xf[i], (float)alpha, make_float2(pv.x, pv.y));
+      xf[voff + i] = caxpy(xf[voff + i], (float)alpha, make_float2(pv.x, pv.y));
     }
     acc += cdot_re_own(rv, rv);
   }
@@ -160,10 +163,35 @@ cudaError_t launch_cg_update_batch(const void* descs, const int2* blocks, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_batch32(const void* descs, const int2* blocks, const int* nblocks, int total_blocks,
-                                     cudaStream_t s) {
-  cg_update_batch_kernel<float><<<total_blocks, 256, 0, s>>>((const UpdArgs<float>*)descs, blocks, nblocks);
+// Systems stored back to back (FP32 mixed solve): block (j, k) is block j of system
+// k, whose vectors start k vstride elements, partials k pstride doubles and state k
+// states after system 0's.  The vector pointers stay system 0's (kernel parameters)
+// with the offset added at each access, so the element loop reads no descriptor and
+// holds no extra pointers.
+__global__ void __launch_bounds__(256) cg_update_multi_kernel(const UpdArgs<float> base, long long vstride,
+                                                              int pstride) {
+  const size_t k = blockIdx.y;
+  UpdArgs<float> u = base;
+  u.part_pq = base.part_pq + k * pstride;
+  u.part_rr = base.part_rr + k * pstride;
+  u.st = base.st + k;
+  cg_update_body<float>(u, blockIdx.x, gridDim.x, k * (size_t)vstride);
+}
+
+cudaError_t launch_cg_update_multi(const UpdArgs<float>& base, long long vstride, int pstride, int nsys,
+                                   int blocks_per_system, cudaStream_t s) {
+  if (nsys < 1 || nsys > 65535 || blocks_per_system < 1 || base.x_is_double) return cudaErrorInvalidValue;
+  cg_update_multi_kernel<<<dim3(blocks_per_system, nsys), 256, 0, s>>>(base, vstride, pstride);
   return cudaGetLastError();
+}
+
+int cg_update_multi_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cg_update_multi_kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 template cudaError_t launch_cg_update<double>(long long, int, void*, int, double2*, double2* const[2],
                                               const double2*, const double*, int, double*, CgState*,
