@@ -15,6 +15,7 @@
 
 #include "hqmc.h"
 #include "kernels.h"
+#include "multi_shape.h"
 
 using namespace hqmc;
 
@@ -1820,27 +1821,14 @@ SliceLaunch multi_walk_shape(const hqmc_config* cfg) {
   return cfg->fused32.walk ? cfg->fused32 : cfg->slw32;
 }
 
-// Slice ranges per system of a launch over nsys systems: CTAs of one system walk
-// ranges of about Ntau / G slices at 2 sweeps per slice plus one halo sweep, and
-// the device holds R of them at a time, so the launch takes about
-// ceil(nsys G / R) rounds of (2 ceil(Ntau / G) + 1) sweeps; the G with the fewest
-// (the largest G among equals: more, shorter CTAs balance better) is taken.
+// Slice ranges per system of a launch over nsys systems (multi_shape.h), unless
+// hqmc_set_multi_ranges fixed them.
 int multi_granges(const hqmc_config* cfg, int nsys) {
   const SliceLaunch w = multi_walk_shape(cfg);
   const int N = cfg->p.Ntau;
   if (cfg->multi_ranges > 0) return std::min(cfg->multi_ranges, N);
   const long long R = (long long)std::max(1, cfg->num_sms) * std::max(1, mdagm_walk_multi_blocks_per_sm(w));
-  long long best = -1;
-  int bestG = 1;
-  for (int G = 1; G <= N; ++G) {
-    const long long rounds = ((long long)nsys * G + R - 1) / R;
-    const long long cost = rounds * (2LL * ((N + G - 1) / G) + 1);
-    if (best < 0 || cost <= best) {
-      best = cost;
-      bestG = G;
-    }
-  }
-  return bestG;
+  return multi_ranges_model(N, nsys, R);
 }
 
 // Shared memory of the systems' FP64 residual (the batched generic kernel: links
