@@ -289,6 +289,26 @@ def test_leapfrog_reversible(hq):
         assert (pt.cpu().numpy() + p).__abs__().max() < 1e-9
 
 
+def test_leapfrog_reversible_to_1e10(hq):
+    """The reversibility check as the oracle pins it: CG to a true residual of 1e-12
+    and theta, p back to 1e-10 (L = 8, Ntau = 16: kappa small enough for FP64 CG to
+    reach 1e-12)."""
+    L, N = 8, 16
+    th = inputs.theta_warm(L, N, seed=171)
+    p = inputs.momenta(L, N, seed=172)
+    R = inputs.complex_gaussian(L, N, seed=173)
+    with hq.Config(L, N) as cfg:
+        tht, pt = cuda(th), cuda(p)
+        phi = hq.apply_M(cfg, tht, cuda(R), dagger=True)
+        X = torch.zeros_like(phi)
+        i1 = hq.leapfrog(cfg, tht, pt, phi, X, nsteps=3, dt=0.02, tol=1e-12)
+        pt.neg_()
+        i2 = hq.leapfrog(cfg, tht, pt, phi, X, nsteps=3, dt=0.02, tol=1e-12)
+        assert i1["status"] == 0 and i2["status"] == 0
+        assert (tht.cpu().numpy() - th).__abs__().max() <= 1e-10
+        assert (pt.cpu().numpy() + p).__abs__().max() <= 1e-10
+
+
 def test_energy_conservation_at_config2_size(hq):
     """At L = 24, Ntau = 240 from a cold start: dH shrinks ~4x when dt halves at fixed
     trajectory length (leapfrog error O(dt^2))."""
