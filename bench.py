@@ -29,6 +29,12 @@ let the pseudofermion force drive the leapfrog into singular configurations.
 The step keeps |dH| below 1 at this volume (|dH| grows like volume * dt^2 from
 a cold start: 125 at dt = 0.01, 31 at dt = 0.005, measured).
 
+Workload estimate_L66_Nt660_40rv (stochastic estimation): a step is one estimate
+of diag M^{-1} with 40 CN(0, 1) vectors on one L = 66 field (pmixed to 1e-8),
+solved one after another (the line's value), with projected initial guesses
+(`projected`) and with the 40 systems advancing together (`together`, whose
+multi-system walk launch is the line's roofline).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 Prints one JSON line on rank 0.  Under torchrun every rank runs an independent
